@@ -1,0 +1,259 @@
+"""Pins the FP64 CPU oracle to results fixed by the paper and by mathematics.
+
+Each test below checks the oracle against something that is not the oracle:
+counts printed in the paper, closed-form solutions of special cases, exact
+invariants of the equations, and a dense matrix exponential of the generator.
+A dropped term, a wrong sign or a swapped site index anywhere in the
+right-hand side fails at least one of them.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.linalg import expm
+
+import oracle
+from paper_1012_4382_gb300 import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+C_CM_PER_FS = 2.99792458e-5
+KB = 0.6950348004  # cm^-1 / K
+W = 2.0 * math.pi * C_CM_PER_FS  # cm^-1 -> rad/fs
+
+
+def _load_table(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([float(x) for x in line.split()])
+    return np.array(rows)
+
+
+# ----------------------------------------------------------------------------
+# Hierarchy size and structure (App. B: N_tot = (N+N_max)!/(N! N_max!))
+# ----------------------------------------------------------------------------
+
+def test_node_counts_match_paper_table():
+    for N, K, nodes in _load_table("table2_node_counts.txt").astype(int):
+        assert oracle.num_nodes(N, K) == nodes
+        assert math.comb(N + K, K) == nodes
+
+
+@pytest.mark.parametrize("N,K", [(1, 0), (1, 5), (2, 4), (3, 3), (4, 2), (5, 0)])
+def test_multi_indices_brute_force(N, K):
+    got = oracle.multi_indices(N, K)
+    brute = sorted(t for t in itertools.product(range(K + 1), repeat=N) if sum(t) <= K)
+    assert len(got) == len(brute) == math.comb(N + K, K)
+    assert sorted(map(tuple, got.tolist())) == brute
+    # root first, levels non-decreasing
+    assert tuple(got[0]) == (0,) * N
+    assert np.all(np.diff(got.sum(axis=1)) >= 0)
+
+
+# ----------------------------------------------------------------------------
+# Closed forms
+# ----------------------------------------------------------------------------
+
+def test_rabi_oscillation_lambda_zero():
+    """lambda = 0: the auxiliaries stay zero and the dimer oscillates coherently,
+    P_1(t) = 1 - (4 J^2 / Omega^2) sin^2(Omega t / 2), Omega = sqrt(Delta^2 + 4 J^2)."""
+    w = workloads.dimer()
+    p = dict(w["params"])
+    p["lam"] = np.zeros(2)
+    r1 = oracle.propagate(p, w["rho0"], 1.0, 1000, 1)
+    r2 = oracle.propagate(p, w["rho0"], 0.5, 2000, 2)
+    t = np.arange(1001) * 1.0
+    om = math.sqrt(100.0 ** 2 + 4 * 100.0 ** 2) * W
+    p1 = 1.0 - (4 * 100.0 ** 2 / (100.0 ** 2 + 4 * 100.0 ** 2)) * np.sin(om * t / 2) ** 2
+    e1 = np.abs(r1["pops"][:, 0] - p1).max()
+    e2 = np.abs(r2["pops"][:, 0] - p1).max()
+    assert e1 < 1e-6
+    assert 12.0 < e1 / e2 < 20.0  # RK4: error ~ dt^4
+    assert np.abs(r1["trace"] - 1.0).max() < 1e-13
+
+
+def _pure_dephasing_exact(lam, gam, T, e1, e2, t):
+    """Two uncoupled sites, one Drude bath each: the (1,2) element of the
+    hierarchy decouples into a scalar chain whose infinite-depth solution is
+    rho_12(t) = rho_12(0) exp(-i(e1-e2)t - (a1 - i b1) f1(t) - (a2 + i b2) f2(t)),
+    a = 2 lambda k_B T, b = lambda gamma, f(t) = (gamma t - 1 + exp(-gamma t)) / gamma^2."""
+    a = 2 * lam * W * KB * T * W
+    b = lam * gam * W * W
+    g = gam * W
+    f = (g * t - 1 + np.exp(-g * t)) / g ** 2
+    return np.exp(-1j * (e1 - e2) * W * t - (a[0] - 1j * b[0]) * f[0] - (a[1] + 1j * b[1]) * f[1])
+
+
+def test_pure_dephasing_closed_form():
+    lam = np.array([35.0, 10.0])
+    gam = np.array([106.0, 60.0])
+    H = np.diag([0.0, 150.0]).astype(complex)
+    p = dict(N=2, K=30, H=H, lam=lam, gam=gam, T=300.0)
+    rho0 = np.full((2, 2), 0.5, dtype=complex)
+    exact = 0.5 * _pure_dephasing_exact(lam, gam, 300.0, 0.0, 150.0, 200.0)
+    r1 = oracle.propagate(p, rho0, 1.0, 200, 200)
+    r2 = oracle.propagate(p, rho0, 0.5, 400, 400)
+    e1 = abs(r1["rho"][0, 1] - exact) / abs(exact)
+    e2 = abs(r2["rho"][0, 1] - exact) / abs(exact)
+    assert e1 < 2e-6
+    assert 10.0 < e1 / e2 < 22.0
+    # populations do not move without inter-site coupling
+    assert np.abs(r1["pops"] - 0.5).max() < 1e-14
+
+
+def test_markov_terminator_reduces_truncation_error():
+    lam = np.array([35.0, 10.0])
+    gam = np.array([106.0, 60.0])
+    H = np.diag([0.0, 150.0]).astype(complex)
+    rho0 = np.full((2, 2), 0.5, dtype=complex)
+    exact = 0.5 * _pure_dephasing_exact(lam, gam, 300.0, 0.0, 150.0, 200.0)
+    for K in (2, 4, 6):
+        errs = []
+        for term in (0, 1):
+            p = dict(N=2, K=K, H=H, lam=lam, gam=gam, T=300.0, terminator=term)
+            r = oracle.propagate(p, rho0, 0.5, 400, 400)
+            errs.append(abs(r["rho"][0, 1] - exact))
+        assert errs[1] < errs[0] / 2
+
+
+def test_single_site_trap_and_decay_closed_form():
+    """One site with trap rate G_t and radiative rate G_r (ps^-1): the bath
+    cannot act (V^x vanishes on a 1x1 block), so rho_11 = exp(-(G_t+G_r) t),
+    eta = G_t/(G_t+G_r) (1 - exp(-(G_t+G_r) t)), loss likewise with G_r."""
+    gt, gr = 0.8, 0.05
+    p = dict(N=1, K=3, H=np.array([[12345.0]]), lam=35.0, gam=106.0, T=300.0,
+             trap=np.array([gt]), recomb=np.array([gr]))
+    r = oracle.propagate(p, np.array([[1.0]]), 1.0, 3000, 100)
+    t = np.arange(r["pops"].shape[0]) * 100.0
+    g = (gt + gr) * 1e-3
+    assert np.abs(r["pops"][:, 0] - np.exp(-g * t)).max() < 1e-12
+    assert np.abs(r["eta"] - gt / (gt + gr) * (1 - np.exp(-g * t))).max() < 1e-12
+    assert np.abs(r["loss"] - gr / (gt + gr) * (1 - np.exp(-g * t))).max() < 1e-12
+
+
+def test_nonhermitian_dimer_without_bath():
+    """lambda = 0 with a trap: a pure state evolves with the non-Hermitian
+    H_eff = H - (i/2) diag(Gamma), so rho(t) = psi psi^+ with
+    psi = expm(-i H_eff t) psi(0), and eta = 1 - |psi|^2 (all loss goes to RC)."""
+    H = np.array([[0.0, 80.0], [80.0, 120.0]], dtype=complex)
+    trap = np.array([0.0, 1.5])
+    p = dict(N=2, K=2, H=H, lam=0.0, gam=106.0, T=300.0, trap=trap)
+    r = oracle.propagate(p, workloads.pure_state(2, 0), 0.5, 4000, 100)
+    heff = H * W - 0.5j * np.diag(trap * 1e-3)
+    for o, t in enumerate(np.arange(r["pops"].shape[0]) * 50.0):
+        psi = expm(-1j * heff * t) @ np.array([1.0, 0.0])
+        # RK4 error at dt = 0.5 fs over 2 ps is a few 1e-9 here
+        assert np.abs(r["pops"][o] - np.abs(psi) ** 2).max() < 1e-8
+        assert abs(r["eta"][o] - (1.0 - np.vdot(psi, psi).real)) < 1e-8
+
+
+# ----------------------------------------------------------------------------
+# Invariants
+# ----------------------------------------------------------------------------
+
+def test_hermiticity_and_probability_conservation():
+    w = workloads.random_instance(3, 3, seed=11, trap=True)
+    p = w["params"]
+    r = oracle.propagate(p, w["rho0"], 1.0, 300, 10, want_state=True)
+    st = r["state"]
+    herm = np.abs(st - np.conj(np.transpose(st, (0, 2, 1)))).max()
+    assert herm < 1e-14
+    total = r["trace"] + r["eta"] + r["loss"]
+    assert np.abs(total - 1.0).max() < 1e-13
+    assert r["eta"][-1] > 1e-3  # the trap is active
+
+
+def test_no_trap_means_no_efficiency():
+    w = workloads.random_instance(3, 3, seed=5, trap=False)
+    r = oracle.propagate(w["params"], w["rho0"], 1.0, 300, 10)
+    assert np.all(r["eta"] == 0.0) and np.all(r["loss"] == 0.0)
+    assert np.abs(r["trace"] - 1.0).max() < 1e-13
+
+
+# ----------------------------------------------------------------------------
+# RK4 against the dense generator of the dimer hierarchy
+# ----------------------------------------------------------------------------
+
+def test_rk4_equals_taylor_polynomial_and_approaches_expm():
+    w = workloads.dimer()
+    p = dict(w["params"])
+    p["trap"] = np.array([0.0, 0.7])
+    p["recomb"] = np.array([0.01, 0.01])
+    N, K = 2, 4
+    nodes = oracle.num_nodes(N, K)
+    D = N + 2
+    dim = nodes * D * D
+    L = np.zeros((dim, dim), dtype=complex)
+    for k in range(dim):
+        e = np.zeros(dim, dtype=complex)
+        e[k] = 1.0
+        L[:, k] = oracle.rhs(p, e.reshape(nodes, D, D)).reshape(-1)
+    y0 = np.zeros((nodes, D, D), dtype=complex)
+    y0[0, :N, :N] = w["rho0"]
+    y0 = y0.reshape(-1)
+    h, n = 1.0, 200
+    x = h * L
+    P = np.eye(dim) + x + x @ x / 2 + x @ x @ x / 6 + x @ x @ x @ x / 24
+    y_poly = np.linalg.matrix_power(P, n) @ y0
+    r = oracle.propagate(p, w["rho0"], h, n, n, want_state=True)
+    y_rk4 = r["state"].reshape(-1)
+    assert np.abs(y_rk4 - y_poly).max() < 1e-12
+    y_exact = expm(L * h * n) @ y0
+    err1 = np.abs(y_rk4 - y_exact).max()
+    r2 = oracle.propagate(p, w["rho0"], h / 2, 2 * n, 2 * n, want_state=True)
+    err2 = np.abs(r2["state"].reshape(-1) - y_exact).max()
+    assert err1 < 1e-7
+    assert 10.0 < err1 / err2 < 22.0
+    # ground and RC entries never feed back into the site block (why the
+    # trap and the radiative decay act like an anti-Hermitian part of H)
+    idx = np.arange(dim).reshape(nodes, D, D)
+    site_rows = idx[:, :N, :N].reshape(-1)
+    outside = np.setdiff1d(np.arange(dim), site_rows)
+    assert np.all(L[np.ix_(site_rows, outside)] == 0.0)
+
+
+# ----------------------------------------------------------------------------
+# Physics: long-time state of the isolated dimer is close to Gibbs
+# (Sec. "Trapping time for different temperatures": agreement above 100 K)
+# ----------------------------------------------------------------------------
+
+def test_isolated_dimer_relaxes_near_gibbs_state():
+    w = workloads.dimer()
+    p = dict(w["params"])
+    p["K"] = 6
+    r = oracle.propagate(p, w["rho0"], 1.0, 4000, 1000)
+    Hr = p["H"].real
+    beta = 1.0 / (KB * p["T"])
+    ev, U = np.linalg.eigh(Hr)
+    rho_th = U @ np.diag(np.exp(-beta * ev)) @ U.T
+    rho_th /= np.trace(rho_th)
+    # stationary
+    assert np.abs(r["pops"][-1] - r["pops"][-2]).max() < 1e-5
+    assert np.abs(r["pops"][-1] - np.diag(rho_th)).max() < 0.03
+
+
+def test_depth_convergence_of_efficiency():
+    """Truncation converges: the change of eta from depth K to K+1 shrinks."""
+    w = workloads.fmo_trap()
+    p = dict(w["params"])
+    # three sites keep this quick: the first three of the FMO-like model
+    H = p["H"][:3, :3]
+    base = dict(N=3, H=H, lam=p["lam"][:3], gam=p["gam"][:3], T=300.0, trap=np.array([0.0, 0.0, 1.0]),
+                recomb=np.full(3, 1e-3))
+    etas = []
+    for K in (1, 2, 3, 4, 5):
+        r = oracle.propagate(dict(base, K=K), workloads.pure_state(3, 0), 2.0, 500, 500)
+        etas.append(r["eta"][-1])
+    d = np.abs(np.diff(etas))
+    assert d[-1] < d[0]
+    assert d[-1] < 1e-3
+
+
+def test_fmo_table_fixture_is_hermitian():
+    H = _load_table("fmo_table1.txt")
+    assert H.shape == (7, 7)
+    assert np.array_equal(H, H.T)
