@@ -1,0 +1,232 @@
+/*
+ * heom.h -- C ABI of libheom, a GB300 (sm_103a) implementation of the
+ * hierarchical equations of motion (HEOM) for excitonic energy transfer with
+ * trapping, as set up by Kreisbeck, Kramer, Rodriguez and Hein,
+ * "High-performance solution of hierarchical equations of motions for studying
+ * energy-transfer in light-harvesting complexes" (arXiv:1012.4382).
+ *
+ * What the library computes (paper passages in brackets):
+ *   * system: N exciton sites with a Hermitian Hamiltonian H (Sec. "Model",
+ *     Eq. H_ex); one Drude-Lorentz bath per site with reorganisation energy
+ *     lambda_m and correlation rate gamma_m in the high-temperature form
+ *     (App. A2, Eq. gamma and the S(t), chi(t) forms);
+ *   * trapping into the reaction centre at rate Gamma_RC,m and radiative decay
+ *     to the ground state at rate Gamma_phot,m (App. A1, Eqs. lab2, lab3),
+ *     carried as the anti-Hermitian part -(i/2) diag(Gamma_RC + Gamma_phot) of
+ *     an effective Hamiltonian, which the paper states is equivalent
+ *     (App. A1, end);
+ *   * the hierarchy of auxiliary density matrices sigma_n, |n| <= K = N_max
+ *     (App. A2, Eqs. labsevena and lab8, truncation at its end), propagated
+ *     with 4th-order Runge-Kutta (App. B);
+ *   * the efficiency eta = <RC|rho(t)|RC> (Eq. eta), obtained as the time
+ *     integral of sum_m Gamma_RC,m <m|rho|m> integrated by the same RK4, and
+ *     the radiative loss <0|rho|0> likewise.
+ * Readings taken where the paper is ambiguous: damping term
+ * -sum_m n_m gamma_m sigma_n (the printed sign in lab8 would be unstable);
+ * theta_m = i (2 lambda_m k_B T V_m^x - i lambda_m gamma_m V_m^o) (the printed
+ * temperature factor is dimensionally inconsistent).
+ *
+ * Units at this boundary: energies and couplings in cm^-1, rates in ps^-1,
+ * temperature in K, time in fs.  Complex arrays are interleaved (re, im)
+ * doubles, row-major.
+ *
+ * Ownership: every pointer argument is owned by the caller and only read or
+ * written during the call (or, for the *_device variants, until the work
+ * queued on the context's stream has finished).  Contexts own all device
+ * memory they allocate; it stays resident between calls (App. B keeps the
+ * sigma-matrices on the GPU and copies only rho out).
+ *
+ * Errors: every function returns HEOM_OK (0) or a positive HEOM_E* code and
+ * sets a thread-local message readable with heom_last_error().  Nothing throws
+ * across this boundary.  There is no CPU fallback: without a usable CUDA
+ * device, functions that need one return HEOM_ECUDA.
+ */
+#ifndef HEOM_H
+#define HEOM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define HEOM_OK 0
+#define HEOM_EINVAL 1       /* invalid argument (message says which) */
+#define HEOM_ENOMEM 2       /* host or device allocation failed */
+#define HEOM_ECUDA 3        /* CUDA runtime error or no usable device */
+#define HEOM_ETIMEOUT 4     /* a bounded device-side wait expired; results of that call are invalid */
+#define HEOM_EUNSUPPORTED 5 /* valid request this build does not implement (message says what) */
+
+/* precision of the propagation */
+#define HEOM_FP64 0         /* every array and every operation in double precision */
+#define HEOM_FP32_MIXED 1   /* auxiliary matrices and right-hand side in float; rho itself,
+                               its RK4 accumulation, populations and eta in double */
+
+/* truncation of the hierarchy at |n| = K (the paper only says "truncate") */
+#define HEOM_TERM_NONE 0    /* sigma_{n+e_j} = 0 beyond the last level */
+#define HEOM_TERM_MARKOV 1  /* sigma_{n+e_j} ~ (n_j+1) theta_j sigma_n / (sum_k n_k gamma_k + gamma_j) */
+
+/* largest supported number of sites and of hierarchy nodes per instance */
+#define HEOM_MAX_SITES 24
+#define HEOM_MAX_NODES 16777215
+
+typedef struct heom_params {
+  int32_t N;                 /* number of sites, 1..HEOM_MAX_SITES */
+  int32_t K;                 /* hierarchy depth N_max, >= 0 */
+  const double* H;           /* N*N complex Hamiltonian (cm^-1), must be Hermitian */
+  const double* lambda;      /* N reorganisation energies (cm^-1), >= 0 */
+  const double* gamma;       /* N bath correlation rates (cm^-1), > 0 */
+  double T_kelvin;           /* temperature (K), > 0 */
+  const double* trap_rate;   /* N trapping rates Gamma_RC (ps^-1), >= 0; NULL = none */
+  const double* recomb_rate; /* N radiative decay rates Gamma_phot (ps^-1), >= 0; NULL = none */
+  int32_t precision;         /* HEOM_FP64 or HEOM_FP32_MIXED */
+  int32_t terminator;        /* HEOM_TERM_NONE or HEOM_TERM_MARKOV */
+  int32_t add_reorg_to_H;    /* 0: H used as given; 1: lambda_m added to H_mm (Eq. H_ex) */
+  int32_t reserved;          /* must be 0 */
+} heom_params;
+
+typedef struct heom_ctx heom_ctx;     /* one propagated hierarchy */
+typedef struct heom_batch heom_batch; /* many independent hierarchies */
+
+/* ---------------------------------------------------------------- host-only */
+
+/* Number of hierarchy nodes C(N+K, K) (App. B, N_tot).  HEOM_EINVAL when N is
+ * outside 1..HEOM_MAX_SITES, K < 0, or the count exceeds HEOM_MAX_NODES. */
+int heom_num_nodes(int32_t N, int32_t K, int64_t* out);
+
+/* Writes the library's node order and neighbour tables (App. B: each sigma
+ * has 2N neighbours).  Nodes are ordered by level |n|, then lexicographically
+ * descending (n_1 first); node 0 is n = 0.  For nodes i and sites j:
+ *   multi[i*N + j] = n_j,
+ *   up[i*N + j]    = index of n + e_j, or -1 when |n| = K,
+ *   down[i*N + j]  = index of n - e_j, or -1 when n_j = 0.
+ * Each output may be NULL.  Arrays hold nodes*N int32 values. */
+int heom_build_index(int32_t N, int32_t K, int32_t* multi, int32_t* up, int32_t* down);
+
+/* Device memory hooks.  When set, every device allocation of the library goes
+ * through alloc/release (e.g. a framework's caching allocator); otherwise
+ * cudaMalloc/cudaFree are used.  alloc returns NULL on failure.  Set before
+ * creating contexts; contexts keep the hooks they were created with. */
+typedef void* (*heom_alloc_fn)(size_t bytes, void* user);
+typedef void (*heom_free_fn)(void* ptr, size_t bytes, void* user);
+int heom_set_allocator(heom_alloc_fn alloc, heom_free_fn release, void* user);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* heom_last_error(void);
+
+/* ------------------------------------------------------- single hierarchy */
+
+/* Creates a context: validates params, converts units, builds the node tables,
+ * allocates the device state on the current CUDA device and sets rho(0) =
+ * |0><0| (site index 0).  cuda_stream is a cudaStream_t (NULL: the legacy
+ * default stream); all device work of the context is ordered on it.  The
+ * params and their arrays may be freed after the call. */
+int heom_create(const heom_params* params, void* cuda_stream, heom_ctx** out);
+
+/* Sets rho(0) from a host N*N complex Hermitian matrix (|rho - rho^+| must be
+ * <= 1e-12 elementwise, else HEOM_EINVAL), zeroes every auxiliary matrix
+ * (App. A2: "the sigma-matrices are initially set to zero") and the eta and
+ * loss integrals.  Blocking. */
+int heom_set_rho0(heom_ctx* ctx, const double* rho0);
+
+/* Same from a device buffer of N*N complex doubles; asynchronous on the
+ * context's stream, no host synchronisation, no validation of hermiticity. */
+int heom_set_rho0_device(heom_ctx* ctx, const double* d_rho0);
+
+/* Advances the state by nsteps RK4 steps of dt_fs and records, at steps
+ * 0, out_every, 2*out_every, ... of this call (nout = nsteps/out_every + 1
+ * rows), the site populations pops_out[nout*N], their sum trace_out[nout]
+ * and eta_out[nout] (each may be NULL).  Resumable: a later call continues
+ * from the state this one left.  Blocking; returns HEOM_ETIMEOUT if a device
+ * wait expired. */
+int heom_propagate(heom_ctx* ctx, double dt_fs, int64_t nsteps, int64_t out_every, double* pops_out,
+                   double* trace_out, double* eta_out);
+
+/* Same with device output buffers d_pops[nout*N] and d_eta_loss[nout*2]
+ * ((eta, loss) per row); either may be NULL.  Asynchronous on the context's
+ * stream; call heom_synchronize() to wait and to collect device errors. */
+int heom_propagate_device(heom_ctx* ctx, double dt_fs, int64_t nsteps, int64_t out_every, double* d_pops,
+                          double* d_eta_loss);
+
+/* Waits for the context's stream and reports HEOM_ETIMEOUT / HEOM_ECUDA
+ * raised by work queued since the last check. */
+int heom_synchronize(heom_ctx* ctx);
+
+/* eta = <RC|rho|RC> (Eq. eta) and the radiative loss <0|rho|0> at the current
+ * time; loss_out may be NULL.  Blocking. */
+int heom_efficiency(heom_ctx* ctx, double* eta_out, double* loss_out);
+
+/* Current reduced density matrix on the sites, N*N complex.  Blocking. */
+int heom_get_rho(heom_ctx* ctx, double* rho_out);
+
+/* Full state for checkpoints and checks: every node's N*N complex matrix in
+ * the order of heom_build_index (nodes*N*N complex doubles), plus eta and
+ * loss in extra[2] (may be NULL).  heom_set_state restores it exactly
+ * (FP64) or to float rounding (auxiliaries in HEOM_FP32_MIXED).  Blocking. */
+int heom_get_state(heom_ctx* ctx, double* state_out, double* extra);
+int heom_set_state(heom_ctx* ctx, const double* state_in, const double* extra);
+
+/* Number of nodes of the context's hierarchy. */
+int heom_ctx_num_nodes(const heom_ctx* ctx, int64_t* out);
+
+/* Launch shape.  mode 0: one thread-block cluster of `team_ctas` CTAs
+ * (1..16) per hierarchy with hardware cluster barriers between RK4 stages;
+ * mode 1: the whole GPU per hierarchy (cooperative launch, software grid
+ * barrier with a bounded wait).  block_threads: multiple of 32, 64..512
+ * (64..256 for HEOM_FP64, whose kernels are compiled for that register budget);
+ * node_threads: threads sharing one node's matrix (1, 2, 4 or 8).  Any
+ * argument <= 0 keeps the current value. */
+int heom_set_launch(heom_ctx* ctx, int32_t mode, int32_t team_ctas, int32_t block_threads, int32_t node_threads);
+int heom_get_launch(const heom_ctx* ctx, int32_t* mode, int32_t* team_ctas, int32_t* block_threads,
+                    int32_t* node_threads);
+
+/* Autotuner: times `trial_steps` steps for each candidate launch shape on
+ * this context's hierarchy, keeps the fastest and restores the state it
+ * found.  best_us_per_step may be NULL. */
+int heom_autotune(heom_ctx* ctx, int64_t trial_steps, double* best_us_per_step);
+
+/* Releases the context and its device memory (NULL-safe). */
+void heom_destroy(heom_ctx* ctx);
+
+/* -------------------------------------------------------------- batches */
+
+/* count independent hierarchies propagated together: every instance with
+ * the same N runs in one persistent launch, one thread-block cluster per
+ * instance at a time.  All instances must have the same precision.
+ * Instances start from rho(0) = |0><0|. */
+int heom_batch_create(const heom_params* params, int32_t count, void* cuda_stream, heom_batch** out);
+int heom_batch_count(const heom_batch* b, int32_t* count);
+
+/* rho0_all: the count initial matrices concatenated (sum_i N_i^2 complex). */
+int heom_batch_set_rho0(heom_batch* b, const double* rho0_all);
+
+/* Advances instance i by nsteps[i] steps of dt_fs[i] (arrays of count;
+ * nsteps may hold 0).  Outputs, each may be NULL, concatenated over
+ * instances: pops_out rows of N_i (nout_i = nsteps[i]/out_every + 1 rows per
+ * instance), eta_out nout_i values per instance.  Blocking. */
+int heom_batch_propagate(heom_batch* b, const double* dt_fs, const int64_t* nsteps, int64_t out_every,
+                         double* pops_out, double* eta_out);
+
+/* Asynchronous form with device outputs at the same offsets (d_eta_loss holds
+ * two doubles per row). */
+int heom_batch_propagate_device(heom_batch* b, const double* dt_fs, const int64_t* nsteps, int64_t out_every,
+                                double* d_pops, double* d_eta_loss);
+int heom_batch_synchronize(heom_batch* b);
+
+/* eta_out[count], loss_out[count] (may be NULL); blocking. */
+int heom_batch_efficiency(heom_batch* b, double* eta_out, double* loss_out);
+int heom_batch_get_rho(heom_batch* b, int32_t i, double* rho_out);
+
+/* Launch shape of the batch's persistent launches (see heom_set_launch;
+ * mode must be 0). */
+int heom_batch_set_launch(heom_batch* b, int32_t team_ctas, int32_t block_threads, int32_t node_threads);
+
+void heom_batch_destroy(heom_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HEOM_H */

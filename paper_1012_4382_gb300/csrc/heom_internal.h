@@ -1,0 +1,25 @@
+// Private declarations shared by the translation units of libheom.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+namespace heom {
+
+// Engine kernel entry points for N = 1..8 (nullptr otherwise).
+const void* engine_kernel_f64(int N);
+const void* engine_kernel_f32(int N);
+
+// Hierarchy index builder (heom_index.cpp).
+int64_t num_nodes(int N, int K);  // -1 on overflow beyond int64
+struct Index {
+  int N = 0, K = 0;
+  int64_t M = 0;
+  std::vector<int32_t> multi;  // [M][N]
+  std::vector<int32_t> up;     // [M][N]
+  std::vector<int32_t> down;   // [M][N]
+};
+void build_index(int N, int K, Index& out);
+int64_t rank_of(const int32_t* n, int N, int K);
+
+}  // namespace heom

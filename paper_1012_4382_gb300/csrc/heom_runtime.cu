@@ -1,0 +1,1133 @@
+// heom_runtime.cu -- host runtime and C ABI of libheom (declared in include/heom.h).
+//
+// Owns contexts and batches: parameter validation, unit conversion and
+// coefficient precompute, node tables, device memory, launch shapes, the
+// persistent engine launches and the small utility kernels that move rho and
+// the full state in and out.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <queue>
+#include <string>
+#include <vector>
+
+#include "heom.h"
+#include "heom_engine.cuh"
+#include "heom_internal.h"
+
+using heom::CoefLayout;
+using heom::EngineArgs;
+using heom::Inst;
+
+namespace {
+
+// ------------------------------------------------------------------ errors
+
+thread_local std::string t_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(x)                                                                      \
+  do {                                                                                   \
+    cudaError_t e_ = (x);                                                                \
+    if (e_ != cudaSuccess) return fail(HEOM_ECUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define TRY(x)                   \
+  do {                           \
+    int r_ = (x);                \
+    if (r_ != HEOM_OK) return r_; \
+  } while (0)
+
+// --------------------------------------------------------------- constants
+// Unit conversion: an energy or rate nu in cm^-1 is the angular frequency
+// 2 pi c nu; with c in cm/fs this is rad/fs (hbar = 1).
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kSpeedOfLightCmPerFs = 2.99792458e-5;
+constexpr double kCmToRadPerFs = 2.0 * kPi * kSpeedOfLightCmPerFs;
+constexpr double kBoltzmannCmPerK = 0.6950348004;  // k_B / (h c)
+constexpr double kPerPsToPerFs = 1e-3;
+
+// ------------------------------------------------------------------ memory
+
+struct Hooks {
+  heom_alloc_fn alloc = nullptr;
+  heom_free_fn release = nullptr;
+  void* user = nullptr;
+};
+std::mutex g_hooks_mu;
+Hooks g_hooks;
+
+Hooks current_hooks() {
+  std::lock_guard<std::mutex> lk(g_hooks_mu);
+  return g_hooks;
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  Hooks hooks;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  int alloc(size_t n, const Hooks& h) {
+    release();
+    hooks = h;
+    if (n == 0) n = 16;
+    if (hooks.alloc) {
+      p = hooks.alloc(n, hooks.user);
+      if (!p) return fail(HEOM_ENOMEM, "device allocation of %zu bytes failed (allocator hook)", n);
+    } else {
+      cudaError_t e = cudaMalloc(&p, n);
+      if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? HEOM_ENOMEM : HEOM_ECUDA, "cudaMalloc(%zu): %s", n,
+                    cudaGetErrorString(e));
+      }
+    }
+    bytes = n;
+    return HEOM_OK;
+  }
+  void release() {
+    if (!p) return;
+    if (hooks.release)
+      hooks.release(p, bytes, hooks.user);
+    else
+      cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+struct PinnedBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~PinnedBuf() {
+    if (p) cudaFreeHost(p);
+  }
+  int ensure(size_t n) {
+    if (n <= bytes) return HEOM_OK;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+    CUDA_TRY(cudaHostAlloc(&p, n, cudaHostAllocDefault));
+    bytes = n;
+    return HEOM_OK;
+  }
+};
+
+// ------------------------------------------------------------- utilities
+
+template <typename R>
+__global__ void set_root_kernel(R* y, int Mpad, double* y0, const double* rho, int N, double* acc) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < N * N) {
+    const int a = p / N, b = p - (p / N) * N;
+    double v;
+    if (a < b)
+      v = rho[2 * (a * N + b)];
+    else if (a > b)
+      v = rho[2 * (b * N + a) + 1];
+    else
+      v = rho[2 * (a * N + a)];
+    y[(size_t)p * Mpad] = (R)v;
+    if (y0) y0[p] = v;
+  }
+  if (p == 0) {
+    acc[0] = 0.0;
+    acc[1] = 0.0;
+  }
+}
+
+// packed element-major state -> full complex matrices [M][N][N]
+template <typename R>
+__global__ void unpack_state_kernel(const R* y, int Mpad, int64_t M, int N, const double* y0, double* out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int NN = N * N;
+  if (idx >= M * NN) return;
+  const int64_t n = idx / NN;
+  const int e = (int)(idx - n * NN);
+  const int a = e / N, b = e - (e / N) * N;
+  auto P = [&](int k, int l) -> double {
+    if (n == 0 && y0) return y0[k * N + l];
+    return (double)y[(size_t)(k * N + l) * Mpad + n];
+  };
+  double re, im;
+  if (a < b) {
+    re = P(a, b);
+    im = P(b, a);
+  } else if (a > b) {
+    re = P(b, a);
+    im = -P(a, b);
+  } else {
+    re = P(a, a);
+    im = 0.0;
+  }
+  out[2 * idx] = re;
+  out[2 * idx + 1] = im;
+}
+
+template <typename R>
+__global__ void pack_state_kernel(const double* in, R* y, int Mpad, int64_t M, int N, double* y0) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int NN = N * N;
+  if (idx >= M * NN) return;
+  const int64_t n = idx / NN;
+  const int p = (int)(idx - n * NN);
+  const int a = p / N, b = p - (p / N) * N;
+  const double* m = in + 2 * n * NN;
+  double v;
+  if (a < b)
+    v = m[2 * (a * N + b)];
+  else if (a > b)
+    v = m[2 * (b * N + a) + 1];
+  else
+    v = m[2 * (a * N + a)];
+  y[(size_t)p * Mpad + n] = (R)v;
+  if (n == 0 && y0) y0[p] = v;
+}
+
+int launch_blocks(int64_t work, int threads) { return (int)((work + threads - 1) / threads); }
+
+// --------------------------------------------------------------- structures
+
+struct Tables {
+  int N = 0, K = 0;
+  int64_t M = 0;
+  int Mpad = 0;
+  DevBuf up, dn;
+};
+
+struct Instance {
+  int N = 0, K = 0;
+  int64_t M = 0;
+  int Mpad = 0;
+  int complex_h = 0, terminator = 0;
+  std::shared_ptr<Tables> tab;
+  DevBuf y, wa, wb, root64, coef, acc, stage;
+  std::vector<unsigned char> coef_host;
+};
+
+struct LaunchCfg {
+  int mode = 0;       // 0: cluster teams, 1: whole grid
+  int team_ctas = 1;
+  int block = 256;
+  int G = 1;
+};
+
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+// Validates one parameter set; fills the instance's host coefficients.
+template <typename R>
+void fill_coefficients(const heom_params& p, std::vector<unsigned char>& out, int* complex_h) {
+  using L = CoefLayout<R>;
+  const int N = p.N;
+  out.assign(L::bytes(N), 0);
+  R* c = reinterpret_cast<R*>(out.data());
+  double* cd = reinterpret_cast<double*>(out.data() + L::dbl_offset(N));
+  double mean = 0.0;
+  std::vector<double> diag(N);
+  for (int a = 0; a < N; ++a) {
+    diag[a] = p.H[2 * (a * N + a)] + (p.add_reorg_to_H ? p.lambda[a] : 0.0);
+    mean += diag[a];
+  }
+  mean /= N;
+  int cplx = 0;
+  for (int a = 0; a < N; ++a)
+    for (int b = 0; b < N; ++b) {
+      if (a == b) continue;
+      c[L::J(N) + a * N + b] = (R)(p.H[2 * (a * N + b)] * kCmToRadPerFs);
+      const double im = p.H[2 * (a * N + b) + 1];
+      c[L::Ji(N) + a * N + b] = (R)(im * kCmToRadPerFs);
+      if (im != 0.0) cplx = 1;
+    }
+  const double kT = kBoltzmannCmPerK * p.T_kelvin * kCmToRadPerFs;
+  for (int a = 0; a < N; ++a) {
+    const double lam = p.lambda[a] * kCmToRadPerFs;
+    const double gam = p.gamma[a] * kCmToRadPerFs;
+    const double tr = p.trap_rate ? p.trap_rate[a] * kPerPsToPerFs : 0.0;
+    const double rc = p.recomb_rate ? p.recomb_rate[a] * kPerPsToPerFs : 0.0;
+    c[L::eps(N) + a] = (R)((diag[a] - mean) * kCmToRadPerFs);
+    c[L::ghalf(N) + a] = (R)(0.5 * (tr + rc));
+    c[L::alpha(N) + a] = (R)(2.0 * lam * kT);
+    c[L::beta(N) + a] = (R)(lam * gam);
+    c[L::gam(N) + a] = (R)gam;
+    cd[a] = tr;
+    cd[N + a] = rc;
+  }
+  *complex_h = cplx;
+}
+
+int validate(const heom_params* p, int idx) {
+  if (!p) return fail(HEOM_EINVAL, "params[%d] is NULL", idx);
+  if (p->N < 1 || p->N > HEOM_MAX_SITES) return fail(HEOM_EINVAL, "params[%d]: N=%d outside 1..%d", idx, p->N, HEOM_MAX_SITES);
+  if (p->K < 0 || p->K > 255) return fail(HEOM_EINVAL, "params[%d]: K=%d outside 0..255", idx, p->K);
+  const int64_t M = heom::num_nodes(p->N, p->K);
+  if (M < 0 || M > HEOM_MAX_NODES)
+    return fail(HEOM_EINVAL, "params[%d]: C(N+K,K) nodes exceed %d", idx, HEOM_MAX_NODES);
+  if (!p->H || !p->lambda || !p->gamma) return fail(HEOM_EINVAL, "params[%d]: H, lambda and gamma are required", idx);
+  if (!(p->T_kelvin > 0.0) || !std::isfinite(p->T_kelvin)) return fail(HEOM_EINVAL, "params[%d]: T must be > 0", idx);
+  if (p->precision != HEOM_FP64 && p->precision != HEOM_FP32_MIXED)
+    return fail(HEOM_EINVAL, "params[%d]: unknown precision %d", idx, p->precision);
+  if (p->terminator != HEOM_TERM_NONE && p->terminator != HEOM_TERM_MARKOV)
+    return fail(HEOM_EINVAL, "params[%d]: unknown terminator %d", idx, p->terminator);
+  if (p->add_reorg_to_H != 0 && p->add_reorg_to_H != 1)
+    return fail(HEOM_EINVAL, "params[%d]: add_reorg_to_H must be 0 or 1", idx);
+  if (p->reserved != 0) return fail(HEOM_EINVAL, "params[%d]: reserved must be 0", idx);
+  const int N = p->N;
+  double scale = 0.0;
+  for (int i = 0; i < 2 * N * N; ++i) {
+    if (!std::isfinite(p->H[i])) return fail(HEOM_EINVAL, "params[%d]: H has a non-finite entry", idx);
+    scale = std::max(scale, std::fabs(p->H[i]));
+  }
+  for (int a = 0; a < N; ++a)
+    for (int b = 0; b < N; ++b) {
+      const double dr = p->H[2 * (a * N + b)] - p->H[2 * (b * N + a)];
+      const double di = p->H[2 * (a * N + b) + 1] + p->H[2 * (b * N + a) + 1];
+      if (std::fabs(dr) > 1e-12 * std::max(1.0, scale) || std::fabs(di) > 1e-12 * std::max(1.0, scale))
+        return fail(HEOM_EINVAL, "params[%d]: H is not Hermitian at (%d,%d)", idx, a, b);
+    }
+  for (int a = 0; a < N; ++a) {
+    if (!(p->lambda[a] >= 0.0) || !std::isfinite(p->lambda[a]))
+      return fail(HEOM_EINVAL, "params[%d]: lambda[%d] must be finite and >= 0", idx, a);
+    if (!(p->gamma[a] > 0.0) || !std::isfinite(p->gamma[a]))
+      return fail(HEOM_EINVAL, "params[%d]: gamma[%d] must be finite and > 0", idx, a);
+    if (p->trap_rate && (!(p->trap_rate[a] >= 0.0) || !std::isfinite(p->trap_rate[a])))
+      return fail(HEOM_EINVAL, "params[%d]: trap_rate[%d] must be finite and >= 0", idx, a);
+    if (p->recomb_rate && (!(p->recomb_rate[a] >= 0.0) || !std::isfinite(p->recomb_rate[a])))
+      return fail(HEOM_EINVAL, "params[%d]: recomb_rate[%d] must be finite and >= 0", idx, a);
+  }
+  if (N > heom::kMaxSmallN)
+    return fail(HEOM_EUNSUPPORTED, "params[%d]: N=%d > %d sites needs the large-N engine", idx, N, heom::kMaxSmallN);
+  return HEOM_OK;
+}
+
+int validate_rho(const double* rho, int N) {
+  if (!rho) return fail(HEOM_EINVAL, "rho0 is NULL");
+  for (int a = 0; a < N; ++a)
+    for (int b = 0; b < N; ++b) {
+      const double re = rho[2 * (a * N + b)], im = rho[2 * (a * N + b) + 1];
+      if (!std::isfinite(re) || !std::isfinite(im)) return fail(HEOM_EINVAL, "rho0 has a non-finite entry");
+      if (std::fabs(re - rho[2 * (b * N + a)]) > 1e-12 || std::fabs(im + rho[2 * (b * N + a) + 1]) > 1e-12)
+        return fail(HEOM_EINVAL, "rho0 is not Hermitian at (%d,%d)", a, b);
+    }
+  return HEOM_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ engine
+
+struct Engine {
+  int prec = HEOM_FP64;
+  int device = 0;
+  int sms = 0;
+  cudaStream_t stream = nullptr;
+  Hooks hooks;
+  std::vector<std::unique_ptr<Instance>> inst;
+  std::map<std::pair<int, int>, std::shared_ptr<Tables>> tables;
+  std::map<int, LaunchCfg> cfg;  // per N
+  DevBuf d_args, d_status, d_gsync, d_out;
+  PinnedBuf h_args;
+  cudaEvent_t args_done = nullptr;
+  bool args_pending = false;
+
+  ~Engine() {
+    if (args_done) {
+      cudaEventSynchronize(args_done);
+      cudaEventDestroy(args_done);
+    }
+    if (stream) cudaStreamSynchronize(stream);
+  }
+
+  size_t rsize() const { return prec == HEOM_FP64 ? sizeof(double) : sizeof(float); }
+  // the FP64 kernels are compiled for at most 256 threads per block (register budget)
+  int max_block() const { return prec == HEOM_FP64 ? 256 : 512; }
+
+  int ensure_device() {
+    int cur = -1;
+    CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != device) CUDA_TRY(cudaSetDevice(device));
+    return HEOM_OK;
+  }
+
+  int init(const heom_params* params, int count, void* s) {
+    if (count < 1) return fail(HEOM_EINVAL, "count must be >= 1");
+    if (!params) return fail(HEOM_EINVAL, "params is NULL");
+    for (int i = 0; i < count; ++i) TRY(validate(&params[i], i));
+    prec = params[0].precision;
+    for (int i = 1; i < count; ++i)
+      if (params[i].precision != prec) return fail(HEOM_EINVAL, "params[%d]: all instances need the same precision", i);
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev < 1) {
+      cudaGetLastError();
+      return fail(HEOM_ECUDA, "no usable CUDA device (%s)", cudaGetErrorString(e));
+    }
+    CUDA_TRY(cudaGetDevice(&device));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    stream = static_cast<cudaStream_t>(s);
+    hooks = current_hooks();
+    CUDA_TRY(cudaEventCreateWithFlags(&args_done, cudaEventDisableTiming));
+    TRY(d_status.alloc(sizeof(int) * 4, hooks));
+    TRY(d_gsync.alloc(sizeof(unsigned) * 4, hooks));
+    CUDA_TRY(cudaMemsetAsync(d_status.p, 0, sizeof(int) * 4, stream));
+    for (int i = 0; i < count; ++i) TRY(add_instance(params[i]));
+    for (auto& in : inst)
+      if (!cfg.count(in->N)) cfg[in->N] = default_cfg(in->N, count);
+    // rho(0) = |0><0| everywhere
+    std::vector<double> rho;
+    for (int i = 0; i < count; ++i) {
+      const int N = inst[i]->N;
+      rho.assign(2 * N * N, 0.0);
+      rho[0] = 1.0;
+      TRY(set_rho0_host(i, rho.data()));
+    }
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    return HEOM_OK;
+  }
+
+  LaunchCfg default_cfg(int N, int count) const {
+    LaunchCfg c;
+    int64_t Mmax = 0;
+    for (auto& in : inst)
+      if (in->N == N) Mmax = std::max<int64_t>(Mmax, in->M);
+    if (count == 1) {
+      if (prec == HEOM_FP64 && Mmax >= 256) {
+        c.mode = 1;
+        c.block = 256;
+        c.G = 4;
+        c.team_ctas = 1;
+      } else {
+        c.mode = 0;
+        c.block = 256;
+        c.G = N >= 4 ? 4 : 1;
+        const int64_t units = ((Mmax + 31) / 32) * c.G;
+        const int64_t warps = c.block / 32;
+        int ctas = (int)std::min<int64_t>(16, std::max<int64_t>(1, (units + warps - 1) / warps));
+        int p2 = 1;
+        while (p2 < ctas) p2 <<= 1;
+        c.team_ctas = std::min(16, p2);
+      }
+    } else {
+      c.mode = 0;
+      c.block = 256;
+      c.G = 1;
+      c.team_ctas = 4;
+    }
+    return c;
+  }
+
+  int add_instance(const heom_params& p) {
+    auto in = std::make_unique<Instance>();
+    in->N = p.N;
+    in->K = p.K;
+    in->M = heom::num_nodes(p.N, p.K);
+    in->Mpad = (int)((in->M + 31) / 32 * 32);
+    in->terminator = p.terminator;
+    if (prec == HEOM_FP64)
+      fill_coefficients<double>(p, in->coef_host, &in->complex_h);
+    else
+      fill_coefficients<float>(p, in->coef_host, &in->complex_h);
+    auto key = std::make_pair(p.N, p.K);
+    auto it = tables.find(key);
+    if (it == tables.end()) {
+      auto t = std::make_shared<Tables>();
+      t->N = p.N;
+      t->K = p.K;
+      t->M = in->M;
+      t->Mpad = in->Mpad;
+      heom::Index idx;
+      heom::build_index(p.N, p.K, idx);
+      std::vector<int32_t> up((size_t)p.N * t->Mpad, -1), dn((size_t)p.N * t->Mpad, -1);
+      for (int64_t n = 0; n < t->M; ++n)
+        for (int j = 0; j < p.N; ++j) {
+          up[(size_t)j * t->Mpad + n] = idx.up[(size_t)n * p.N + j];
+          const int32_t d = idx.down[(size_t)n * p.N + j];
+          const int32_t nj = idx.multi[(size_t)n * p.N + j];
+          dn[(size_t)j * t->Mpad + n] = d < 0 ? -1 : ((nj << 24) | d);
+        }
+      TRY(t->up.alloc(up.size() * 4, hooks));
+      TRY(t->dn.alloc(dn.size() * 4, hooks));
+      CUDA_TRY(cudaMemcpyAsync(t->up.p, up.data(), up.size() * 4, cudaMemcpyHostToDevice, stream));
+      CUDA_TRY(cudaMemcpyAsync(t->dn.p, dn.data(), dn.size() * 4, cudaMemcpyHostToDevice, stream));
+      CUDA_TRY(cudaStreamSynchronize(stream));
+      tables[key] = t;
+      in->tab = t;
+    } else {
+      in->tab = it->second;
+    }
+    const size_t arr = (size_t)p.N * p.N * in->Mpad * rsize();
+    TRY(in->y.alloc(arr, hooks));
+    TRY(in->wa.alloc(arr, hooks));
+    TRY(in->wb.alloc(arr, hooks));
+    TRY(in->root64.alloc(3 * sizeof(double) * p.N * p.N, hooks));
+    TRY(in->coef.alloc(in->coef_host.size(), hooks));
+    TRY(in->acc.alloc(4 * sizeof(double), hooks));
+    TRY(in->stage.alloc(2 * sizeof(double) * p.N * p.N, hooks));
+    CUDA_TRY(cudaMemcpyAsync(in->coef.p, in->coef_host.data(), in->coef_host.size(), cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(cudaMemsetAsync(in->y.p, 0, arr, stream));
+    CUDA_TRY(cudaMemsetAsync(in->acc.p, 0, 4 * sizeof(double), stream));
+    CUDA_TRY(cudaStreamSynchronize(stream));  // coef_host must outlive the copy
+    inst.push_back(std::move(in));
+    return HEOM_OK;
+  }
+
+  double* root_ptr(const Instance& in, int which) const {
+    if (prec == HEOM_FP64) return nullptr;
+    return in.root64.as<double>() + (size_t)which * in.N * in.N;
+  }
+
+  int set_rho0_device(int i, const double* d_rho) {
+    Instance& in = *inst[i];
+    const size_t arr = (size_t)in.N * in.N * in.Mpad * rsize();
+    CUDA_TRY(cudaMemsetAsync(in.y.p, 0, arr, stream));
+    const int NN = in.N * in.N;
+    if (prec == HEOM_FP64)
+      set_root_kernel<double><<<launch_blocks(NN, 128), 128, 0, stream>>>(in.y.as<double>(), in.Mpad, nullptr, d_rho,
+                                                                         in.N, in.acc.as<double>());
+    else
+      set_root_kernel<float><<<launch_blocks(NN, 128), 128, 0, stream>>>(in.y.as<float>(), in.Mpad, root_ptr(in, 0),
+                                                                        d_rho, in.N, in.acc.as<double>());
+    CUDA_TRY(cudaGetLastError());
+    return HEOM_OK;
+  }
+
+  int set_rho0_host(int i, const double* rho) {
+    Instance& in = *inst[i];
+    TRY(validate_rho(rho, in.N));
+    CUDA_TRY(cudaMemcpyAsync(in.stage.p, rho, sizeof(double) * 2 * in.N * in.N, cudaMemcpyHostToDevice, stream));
+    return set_rho0_device(i, in.stage.as<double>());
+  }
+
+  // Output offsets (rows) of instance i for a call with these step counts.
+  static int64_t nout_of(int64_t nsteps, int64_t out_every) { return nsteps / out_every + 1; }
+
+  int propagate(const double* dt, const int64_t* nsteps, int64_t out_every, double* d_pops, double* d_el) {
+    TRY(ensure_device());
+    if (out_every < 1) return fail(HEOM_EINVAL, "out_every must be >= 1");
+    const int count = (int)inst.size();
+    for (int i = 0; i < count; ++i) {
+      if (nsteps[i] < 0) return fail(HEOM_EINVAL, "nsteps[%d] < 0", i);
+      if (!(dt[i] > 0.0) || !std::isfinite(dt[i])) return fail(HEOM_EINVAL, "dt[%d] must be > 0", i);
+    }
+    // descriptors for every instance
+    std::vector<Inst> hi(count);
+    int64_t pop_off = 0, row_off = 0;
+    for (int i = 0; i < count; ++i) {
+      Instance& in = *inst[i];
+      Inst& d = hi[i];
+      memset(&d, 0, sizeof(d));
+      d.N = in.N;
+      d.K = in.K;
+      d.M = (int32_t)in.M;
+      d.Mpad = in.Mpad;
+      d.complex_h = in.complex_h;
+      d.terminator = in.terminator;
+      d.up = in.tab->up.as<int32_t>();
+      d.dn = in.tab->dn.as<int32_t>();
+      d.y = in.y.p;
+      d.wa = in.wa.p;
+      d.wb = in.wb.p;
+      d.y0 = root_ptr(in, 0);
+      d.w0a = root_ptr(in, 1);
+      d.w0b = root_ptr(in, 2);
+      d.coef = in.coef.p;
+      d.acc = in.acc.as<double>();
+      d.out_pops = d_pops ? d_pops + pop_off : nullptr;
+      d.out_el = d_el ? d_el + 2 * row_off : nullptr;
+      d.nsteps = nsteps[i];
+      d.out_every = out_every;
+      d.dt = dt[i];
+      const int64_t nout = nout_of(nsteps[i], out_every);
+      pop_off += nout * in.N;
+      row_off += nout;
+    }
+    // group by N, assign instances to teams (longest first, least loaded team)
+    struct Group {
+      int N;
+      LaunchCfg c;
+      int nteams;
+      std::vector<int32_t> first, list;
+    };
+    std::vector<Group> groups;
+    std::map<int, std::vector<int>> byN;
+    for (int i = 0; i < count; ++i) byN[inst[i]->N].push_back(i);
+    for (auto& kv : byN) {
+      Group g;
+      g.N = kv.first;
+      g.c = cfg[g.N];
+      std::vector<int>& ids = kv.second;
+      if (g.c.mode == 1) {
+        g.nteams = 1;
+      } else {
+        int maxc = max_active_teams(g.N, g.c);
+        if (maxc < 1) return HEOM_ECUDA;
+        g.nteams = std::max(1, std::min<int>((int)ids.size(), maxc));
+      }
+      std::vector<std::vector<int32_t>> lists(g.nteams);
+      std::sort(ids.begin(), ids.end(), [&](int a, int b) {
+        return (double)inst[a]->M * (double)nsteps[a] > (double)inst[b]->M * (double)nsteps[b];
+      });
+      typedef std::pair<double, int> Load;
+      std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
+      for (int t = 0; t < g.nteams; ++t) pq.push(Load(0.0, t));
+      for (int id : ids) {
+        Load l = pq.top();
+        pq.pop();
+        lists[l.second].push_back(id);
+        l.first += (double)inst[id]->M * (double)std::max<int64_t>(nsteps[id], 1);
+        pq.push(l);
+      }
+      g.first.push_back(0);
+      for (int t = 0; t < g.nteams; ++t) {
+        for (int32_t id : lists[t]) g.list.push_back(id);
+        g.first.push_back((int32_t)g.list.size());
+      }
+      groups.push_back(std::move(g));
+    }
+    // stage descriptors and team lists in one pinned buffer, one copy
+    size_t bytes = sizeof(Inst) * count;
+    std::vector<size_t> off_first(groups.size()), off_list(groups.size());
+    for (size_t k = 0; k < groups.size(); ++k) {
+      off_first[k] = bytes;
+      bytes += sizeof(int32_t) * groups[k].first.size();
+      off_list[k] = bytes;
+      bytes += sizeof(int32_t) * groups[k].list.size();
+      bytes = (bytes + 15) / 16 * 16;
+    }
+    if (args_pending) {
+      CUDA_TRY(cudaEventSynchronize(args_done));
+      args_pending = false;
+    }
+    TRY(h_args.ensure(bytes));
+    if (d_args.bytes < bytes) TRY(d_args.alloc(bytes * 2, hooks));
+    unsigned char* hb = static_cast<unsigned char*>(h_args.p);
+    memcpy(hb, hi.data(), sizeof(Inst) * count);
+    for (size_t k = 0; k < groups.size(); ++k) {
+      memcpy(hb + off_first[k], groups[k].first.data(), sizeof(int32_t) * groups[k].first.size());
+      memcpy(hb + off_list[k], groups[k].list.data(), sizeof(int32_t) * groups[k].list.size());
+    }
+    CUDA_TRY(cudaMemcpyAsync(d_args.p, hb, bytes, cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(cudaEventRecord(args_done, stream));
+    args_pending = true;
+    unsigned char* db = d_args.as<unsigned char>();
+    for (size_t k = 0; k < groups.size(); ++k) {
+      Group& g = groups[k];
+      EngineArgs A;
+      A.insts = reinterpret_cast<const Inst*>(db);
+      A.team_first = reinterpret_cast<const int32_t*>(db + off_first[k]);
+      A.team_list = reinterpret_cast<const int32_t*>(db + off_list[k]);
+      A.G = g.c.G;
+      A.logG = ilog2(g.c.G);
+      A.mode = g.c.mode;
+      A.team_ctas = g.c.team_ctas;
+      A.gsync = d_gsync.as<unsigned>();
+      A.status = d_status.as<int>();
+      TRY(launch(g.N, g.c, g.nteams, A));
+    }
+    return HEOM_OK;
+  }
+
+  const void* kernel_for(int N) const {
+    return prec == HEOM_FP64 ? heom::engine_kernel_f64(N) : heom::engine_kernel_f32(N);
+  }
+
+  int max_active_teams(int N, const LaunchCfg& c) {
+    const void* k = kernel_for(N);
+    if (!k) return fail(HEOM_EUNSUPPORTED, "no engine kernel for N=%d", N);
+    if (c.team_ctas > 8) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(c.team_ctas);
+    lc.blockDim = dim3(c.block);
+    lc.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = c.team_ctas;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    int n = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&n, k, &lc);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fail(HEOM_ECUDA, "cudaOccupancyMaxActiveClusters(N=%d, ctas=%d, block=%d): %s", N, c.team_ctas, c.block,
+           cudaGetErrorString(e));
+      return 0;
+    }
+    if (n < 1) fail(HEOM_ECUDA, "launch shape N=%d ctas=%d block=%d cannot be resident", N, c.team_ctas, c.block);
+    return n;
+  }
+
+  int launch(int N, const LaunchCfg& c, int nteams, EngineArgs& A) {
+    const void* k = kernel_for(N);
+    if (!k) return fail(HEOM_EUNSUPPORTED, "no engine kernel for N=%d", N);
+    if (c.mode == 1) {
+      int per_sm = 0;
+      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, c.block, 0));
+      if (per_sm < 1) return fail(HEOM_ECUDA, "block of %d threads cannot be resident", c.block);
+      const int grid = per_sm * sms;
+      CUDA_TRY(cudaMemsetAsync(A.gsync, 0, sizeof(unsigned), stream));
+      void* args[] = {&A};
+      CUDA_TRY(cudaLaunchCooperativeKernel(k, dim3(grid), dim3(c.block), args, 0, stream));
+      return HEOM_OK;
+    }
+    if (c.team_ctas > 8) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(nteams * c.team_ctas);
+    lc.blockDim = dim3(c.block);
+    lc.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = c.team_ctas;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    void* args[] = {&A};
+    CUDA_TRY(cudaLaunchKernelExC(&lc, k, args));
+    return HEOM_OK;
+  }
+
+  int check_status() {
+    int st = 0;
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    CUDA_TRY(cudaMemcpy(&st, d_status.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) {
+      CUDA_TRY(cudaMemset(d_status.p, 0, sizeof(int)));
+      if (st & heom::kStatusTimeout)
+        return fail(HEOM_ETIMEOUT, "a grid barrier wait expired on the device; the call's results are invalid");
+      return fail(HEOM_ECUDA, "device status 0x%x", st);
+    }
+    return HEOM_OK;
+  }
+
+  // host-side blocking propagate with host outputs
+  int propagate_host(const double* dt, const int64_t* nsteps, int64_t out_every, double* pops, double* eta,
+                     double* trace) {
+    if (out_every < 1) return fail(HEOM_EINVAL, "out_every must be >= 1");
+    int64_t pop_total = 0, rows = 0;
+    for (size_t i = 0; i < inst.size(); ++i) {
+      if (nsteps[i] < 0) return fail(HEOM_EINVAL, "nsteps[%zu] < 0", i);
+      const int64_t nout = nout_of(nsteps[i], out_every);
+      pop_total += nout * inst[i]->N;
+      rows += nout;
+    }
+    const bool want = pops || eta || trace;
+    double* dp = nullptr;
+    double* de = nullptr;
+    if (want) {
+      const size_t need = sizeof(double) * (pop_total + 2 * rows);
+      if (d_out.bytes < need) TRY(d_out.alloc(need, hooks));
+      dp = d_out.as<double>();
+      de = dp + pop_total;
+    }
+    TRY(propagate(dt, nsteps, out_every, dp, de));
+    TRY(check_status());
+    if (!want) return HEOM_OK;
+    std::vector<double> hp(pop_total), he(2 * rows);
+    CUDA_TRY(cudaMemcpy(hp.data(), dp, sizeof(double) * pop_total, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(he.data(), de, sizeof(double) * 2 * rows, cudaMemcpyDeviceToHost));
+    if (pops) memcpy(pops, hp.data(), sizeof(double) * pop_total);
+    int64_t po = 0, ro = 0;
+    for (size_t i = 0; i < inst.size(); ++i) {
+      const int64_t nout = nout_of(nsteps[i], out_every);
+      const int N = inst[i]->N;
+      for (int64_t o = 0; o < nout; ++o) {
+        if (eta) eta[ro + o] = he[2 * (ro + o)];
+        if (trace) {
+          double s = 0.0;
+          for (int a = 0; a < N; ++a) s += hp[po + o * N + a];
+          trace[ro + o] = s;
+        }
+      }
+      po += nout * N;
+      ro += nout;
+    }
+    return HEOM_OK;
+  }
+
+  int efficiency(double* eta, double* loss) {
+    TRY(ensure_device());
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    for (size_t i = 0; i < inst.size(); ++i) {
+      double v[2];
+      CUDA_TRY(cudaMemcpy(v, inst[i]->acc.p, sizeof(v), cudaMemcpyDeviceToHost));
+      if (eta) eta[i] = v[0];
+      if (loss) loss[i] = v[1];
+    }
+    return HEOM_OK;
+  }
+
+  int get_states(int i, int64_t nodes, double* out, bool only_root) {
+    TRY(ensure_device());
+    Instance& in = *inst[i];
+    const int64_t M = only_root ? 1 : in.M;
+    const size_t bytes = sizeof(double) * 2 * (size_t)M * in.N * in.N;
+    DevBuf tmp;
+    TRY(tmp.alloc(bytes, hooks));
+    const int64_t work = M * in.N * in.N;
+    if (prec == HEOM_FP64)
+      unpack_state_kernel<double><<<launch_blocks(work, 256), 256, 0, stream>>>(in.y.as<double>(), in.Mpad, M, in.N,
+                                                                               nullptr, tmp.as<double>());
+    else
+      unpack_state_kernel<float><<<launch_blocks(work, 256), 256, 0, stream>>>(in.y.as<float>(), in.Mpad, M, in.N,
+                                                                              root_ptr(in, 0), tmp.as<double>());
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    CUDA_TRY(cudaMemcpy(out, tmp.p, bytes, cudaMemcpyDeviceToHost));
+    (void)nodes;
+    return HEOM_OK;
+  }
+
+  int set_state(int i, const double* in_state, const double* extra) {
+    TRY(ensure_device());
+    Instance& in = *inst[i];
+    const size_t bytes = sizeof(double) * 2 * (size_t)in.M * in.N * in.N;
+    for (int64_t n = 0; n < in.M; ++n) {
+      int r = validate_rho(in_state + 2 * (size_t)n * in.N * in.N, in.N);
+      if (r != HEOM_OK) return fail(HEOM_EINVAL, "state of node %lld is not Hermitian", (long long)n);
+    }
+    DevBuf tmp;
+    TRY(tmp.alloc(bytes, hooks));
+    CUDA_TRY(cudaMemcpyAsync(tmp.p, in_state, bytes, cudaMemcpyHostToDevice, stream));
+    const int64_t work = in.M * in.N * in.N;
+    if (prec == HEOM_FP64)
+      pack_state_kernel<double><<<launch_blocks(work, 256), 256, 0, stream>>>(tmp.as<double>(), in.y.as<double>(),
+                                                                             in.Mpad, in.M, in.N, nullptr);
+    else
+      pack_state_kernel<float><<<launch_blocks(work, 256), 256, 0, stream>>>(tmp.as<double>(), in.y.as<float>(),
+                                                                            in.Mpad, in.M, in.N, root_ptr(in, 0));
+    CUDA_TRY(cudaGetLastError());
+    double acc[2] = {extra ? extra[0] : 0.0, extra ? extra[1] : 0.0};
+    CUDA_TRY(cudaMemcpyAsync(in.acc.p, acc, sizeof(acc), cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    return HEOM_OK;
+  }
+};
+
+struct heom_ctx {
+  Engine e;
+};
+struct heom_batch {
+  Engine e;
+};
+
+// ------------------------------------------------------------------- C ABI
+
+extern "C" {
+
+const char* heom_last_error(void) { return t_err.c_str(); }
+
+int heom_num_nodes(int32_t N, int32_t K, int64_t* out) {
+  if (!out) return fail(HEOM_EINVAL, "out is NULL");
+  if (N < 1 || N > HEOM_MAX_SITES) return fail(HEOM_EINVAL, "N=%d outside 1..%d", N, HEOM_MAX_SITES);
+  if (K < 0) return fail(HEOM_EINVAL, "K=%d < 0", K);
+  const int64_t M = heom::num_nodes(N, K);
+  if (M < 0 || M > HEOM_MAX_NODES) return fail(HEOM_EINVAL, "C(N+K,K) exceeds %d nodes", HEOM_MAX_NODES);
+  *out = M;
+  return HEOM_OK;
+}
+
+int heom_build_index(int32_t N, int32_t K, int32_t* multi, int32_t* up, int32_t* down) {
+  int64_t M = 0;
+  TRY(heom_num_nodes(N, K, &M));
+  heom::Index idx;
+  heom::build_index(N, K, idx);
+  const size_t n = (size_t)M * N;
+  if (multi) memcpy(multi, idx.multi.data(), n * 4);
+  if (up) memcpy(up, idx.up.data(), n * 4);
+  if (down) memcpy(down, idx.down.data(), n * 4);
+  return HEOM_OK;
+}
+
+int heom_set_allocator(heom_alloc_fn alloc, heom_free_fn release, void* user) {
+  if ((alloc == nullptr) != (release == nullptr)) return fail(HEOM_EINVAL, "set both hooks or neither");
+  std::lock_guard<std::mutex> lk(g_hooks_mu);
+  g_hooks.alloc = alloc;
+  g_hooks.release = release;
+  g_hooks.user = user;
+  return HEOM_OK;
+}
+
+int heom_create(const heom_params* params, void* cuda_stream, heom_ctx** out) {
+  if (!out) return fail(HEOM_EINVAL, "out is NULL");
+  *out = nullptr;
+  auto c = std::make_unique<heom_ctx>();
+  TRY(c->e.init(params, 1, cuda_stream));
+  *out = c.release();
+  return HEOM_OK;
+}
+
+void heom_destroy(heom_ctx* ctx) { delete ctx; }
+
+int heom_set_rho0(heom_ctx* ctx, const double* rho0) {
+  if (!ctx) return fail(HEOM_EINVAL, "ctx is NULL");
+  TRY(ctx->e.ensure_device());
+  TRY(ctx->e.set_rho0_host(0, rho0));
+  CUDA_TRY(cudaStreamSynchronize(ctx->e.stream));
+  return HEOM_OK;
+}
+
+int heom_set_rho0_device(heom_ctx* ctx, const double* d_rho0) {
+  if (!ctx || !d_rho0) return fail(HEOM_EINVAL, "ctx or d_rho0 is NULL");
+  TRY(ctx->e.ensure_device());
+  return ctx->e.set_rho0_device(0, d_rho0);
+}
+
+int heom_propagate(heom_ctx* ctx, double dt_fs, int64_t nsteps, int64_t out_every, double* pops_out,
+                   double* trace_out, double* eta_out) {
+  if (!ctx) return fail(HEOM_EINVAL, "ctx is NULL");
+  TRY(ctx->e.ensure_device());
+  return ctx->e.propagate_host(&dt_fs, &nsteps, out_every, pops_out, eta_out, trace_out);
+}
+
+int heom_propagate_device(heom_ctx* ctx, double dt_fs, int64_t nsteps, int64_t out_every, double* d_pops,
+                          double* d_eta_loss) {
+  if (!ctx) return fail(HEOM_EINVAL, "ctx is NULL");
+  return ctx->e.propagate(&dt_fs, &nsteps, out_every, d_pops, d_eta_loss);
+}
+
+int heom_synchronize(heom_ctx* ctx) {
+  if (!ctx) return fail(HEOM_EINVAL, "ctx is NULL");
+  TRY(ctx->e.ensure_device());
+  return ctx->e.check_status();
+}
+
+int heom_efficiency(heom_ctx* ctx, double* eta_out, double* loss_out) {
+  if (!ctx || !eta_out) return fail(HEOM_EINVAL, "ctx or eta_out is NULL");
+  return ctx->e.efficiency(eta_out, loss_out);
+}
+
+int heom_get_rho(heom_ctx* ctx, double* rho_out) {
+  if (!ctx || !rho_out) return fail(HEOM_EINVAL, "ctx or rho_out is NULL");
+  return ctx->e.get_states(0, 1, rho_out, true);
+}
+
+int heom_get_state(heom_ctx* ctx, double* state_out, double* extra) {
+  if (!ctx || !state_out) return fail(HEOM_EINVAL, "ctx or state_out is NULL");
+  TRY(ctx->e.get_states(0, ctx->e.inst[0]->M, state_out, false));
+  if (extra) TRY(ctx->e.efficiency(&extra[0], &extra[1]));
+  return HEOM_OK;
+}
+
+int heom_set_state(heom_ctx* ctx, const double* state_in, const double* extra) {
+  if (!ctx || !state_in) return fail(HEOM_EINVAL, "ctx or state_in is NULL");
+  return ctx->e.set_state(0, state_in, extra);
+}
+
+int heom_ctx_num_nodes(const heom_ctx* ctx, int64_t* out) {
+  if (!ctx || !out) return fail(HEOM_EINVAL, "ctx or out is NULL");
+  *out = ctx->e.inst[0]->M;
+  return HEOM_OK;
+}
+
+int heom_set_launch(heom_ctx* ctx, int32_t mode, int32_t team_ctas, int32_t block_threads, int32_t node_threads) {
+  if (!ctx) return fail(HEOM_EINVAL, "ctx is NULL");
+  LaunchCfg& c = ctx->e.cfg[ctx->e.inst[0]->N];
+  LaunchCfg n = c;
+  if (mode >= 0) n.mode = mode;
+  if (team_ctas > 0) n.team_ctas = team_ctas;
+  if (block_threads > 0) n.block = block_threads;
+  if (node_threads > 0) n.G = node_threads;
+  if (n.mode != 0 && n.mode != 1) return fail(HEOM_EINVAL, "mode must be 0 or 1");
+  if (n.team_ctas < 1 || n.team_ctas > 16) return fail(HEOM_EINVAL, "team_ctas must be 1..16");
+  const int maxb = ctx->e.max_block();
+  if (n.block < 64 || n.block > maxb || n.block % 32)
+    return fail(HEOM_EINVAL, "block_threads must be 64..%d, multiple of 32", maxb);
+  if (n.G != 1 && n.G != 2 && n.G != 4 && n.G != 8) return fail(HEOM_EINVAL, "node_threads must be 1, 2, 4 or 8");
+  c = n;
+  return HEOM_OK;
+}
+
+int heom_get_launch(const heom_ctx* ctx, int32_t* mode, int32_t* team_ctas, int32_t* block_threads,
+                    int32_t* node_threads) {
+  if (!ctx) return fail(HEOM_EINVAL, "ctx is NULL");
+  const LaunchCfg& c = ctx->e.cfg.at(ctx->e.inst[0]->N);
+  if (mode) *mode = c.mode;
+  if (team_ctas) *team_ctas = c.team_ctas;
+  if (block_threads) *block_threads = c.block;
+  if (node_threads) *node_threads = c.G;
+  return HEOM_OK;
+}
+
+int heom_autotune(heom_ctx* ctx, int64_t trial_steps, double* best_us_per_step) {
+  if (!ctx) return fail(HEOM_EINVAL, "ctx is NULL");
+  if (trial_steps < 1) return fail(HEOM_EINVAL, "trial_steps must be >= 1");
+  Engine& e = ctx->e;
+  TRY(e.ensure_device());
+  Instance& in = *e.inst[0];
+  // snapshot the state
+  const size_t arr = (size_t)in.N * in.N * in.Mpad * e.rsize();
+  DevBuf sy, sr, sa;
+  TRY(sy.alloc(arr, e.hooks));
+  TRY(sr.alloc(in.root64.bytes, e.hooks));
+  TRY(sa.alloc(in.acc.bytes, e.hooks));
+  CUDA_TRY(cudaMemcpyAsync(sy.p, in.y.p, arr, cudaMemcpyDeviceToDevice, e.stream));
+  CUDA_TRY(cudaMemcpyAsync(sr.p, in.root64.p, in.root64.bytes, cudaMemcpyDeviceToDevice, e.stream));
+  CUDA_TRY(cudaMemcpyAsync(sa.p, in.acc.p, in.acc.bytes, cudaMemcpyDeviceToDevice, e.stream));
+  std::vector<LaunchCfg> cands;
+  for (int G : {1, 2, 4, 8}) {
+    for (int block : {128, 256, 512})
+      for (int ctas : {1, 2, 4, 8, 16}) {
+        if (block > e.max_block()) continue;
+        LaunchCfg c;
+        c.mode = 0;
+        c.team_ctas = ctas;
+        c.block = block;
+        c.G = G;
+        const int64_t units = ((in.M + 31) / 32) * G;
+        if ((int64_t)ctas * block / 32 > 4 * units && ctas > 1) continue;  // mostly idle warps
+        cands.push_back(c);
+      }
+    for (int block : {128, 256}) {
+      LaunchCfg c;
+      c.mode = 1;
+      c.block = block;
+      c.G = G;
+      cands.push_back(c);
+    }
+  }
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  const LaunchCfg saved = e.cfg[in.N];
+  LaunchCfg best = saved;
+  float best_ms = 1e30f;
+  const double dt = 1.0;
+  for (const LaunchCfg& c : cands) {
+    e.cfg[in.N] = c;
+    if (c.mode == 0 && e.max_active_teams(in.N, c) < 1) {
+      t_err.clear();
+      continue;
+    }
+    int64_t warm = 1;
+    if (e.propagate(&dt, &warm, 1, nullptr, nullptr) != HEOM_OK) { t_err.clear(); continue; }
+    cudaEventRecord(e0, e.stream);
+    if (e.propagate(&dt, &trial_steps, trial_steps, nullptr, nullptr) != HEOM_OK) { t_err.clear(); continue; }
+    cudaEventRecord(e1, e.stream);
+    if (e.check_status() != HEOM_OK) { t_err.clear(); continue; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  e.cfg[in.N] = best;
+  CUDA_TRY(cudaMemcpyAsync(in.y.p, sy.p, arr, cudaMemcpyDeviceToDevice, e.stream));
+  CUDA_TRY(cudaMemcpyAsync(in.root64.p, sr.p, in.root64.bytes, cudaMemcpyDeviceToDevice, e.stream));
+  CUDA_TRY(cudaMemcpyAsync(in.acc.p, sa.p, in.acc.bytes, cudaMemcpyDeviceToDevice, e.stream));
+  CUDA_TRY(cudaStreamSynchronize(e.stream));
+  if (best_us_per_step) *best_us_per_step = best_ms * 1e3 / (double)trial_steps;
+  if (best_ms >= 1e30f) return fail(HEOM_ECUDA, "no launch shape ran");
+  return HEOM_OK;
+}
+
+int heom_batch_create(const heom_params* params, int32_t count, void* cuda_stream, heom_batch** out) {
+  if (!out) return fail(HEOM_EINVAL, "out is NULL");
+  *out = nullptr;
+  auto b = std::make_unique<heom_batch>();
+  TRY(b->e.init(params, count, cuda_stream));
+  *out = b.release();
+  return HEOM_OK;
+}
+
+int heom_batch_count(const heom_batch* b, int32_t* count) {
+  if (!b || !count) return fail(HEOM_EINVAL, "batch or count is NULL");
+  *count = (int32_t)b->e.inst.size();
+  return HEOM_OK;
+}
+
+int heom_batch_set_rho0(heom_batch* b, const double* rho0_all) {
+  if (!b || !rho0_all) return fail(HEOM_EINVAL, "batch or rho0_all is NULL");
+  TRY(b->e.ensure_device());
+  size_t off = 0;
+  for (size_t i = 0; i < b->e.inst.size(); ++i) {
+    TRY(b->e.set_rho0_host((int)i, rho0_all + off));
+    CUDA_TRY(cudaStreamSynchronize(b->e.stream));  // the staging copy reads rho0_all
+    off += 2 * (size_t)b->e.inst[i]->N * b->e.inst[i]->N;
+  }
+  return HEOM_OK;
+}
+
+int heom_batch_propagate(heom_batch* b, const double* dt_fs, const int64_t* nsteps, int64_t out_every,
+                         double* pops_out, double* eta_out) {
+  if (!b || !dt_fs || !nsteps) return fail(HEOM_EINVAL, "batch, dt_fs or nsteps is NULL");
+  TRY(b->e.ensure_device());
+  return b->e.propagate_host(dt_fs, nsteps, out_every, pops_out, eta_out, nullptr);
+}
+
+int heom_batch_propagate_device(heom_batch* b, const double* dt_fs, const int64_t* nsteps, int64_t out_every,
+                                double* d_pops, double* d_eta_loss) {
+  if (!b || !dt_fs || !nsteps) return fail(HEOM_EINVAL, "batch, dt_fs or nsteps is NULL");
+  TRY(b->e.ensure_device());
+  return b->e.propagate(dt_fs, nsteps, out_every, d_pops, d_eta_loss);
+}
+
+int heom_batch_synchronize(heom_batch* b) {
+  if (!b) return fail(HEOM_EINVAL, "batch is NULL");
+  TRY(b->e.ensure_device());
+  return b->e.check_status();
+}
+
+int heom_batch_efficiency(heom_batch* b, double* eta_out, double* loss_out) {
+  if (!b) return fail(HEOM_EINVAL, "batch is NULL");
+  return b->e.efficiency(eta_out, loss_out);
+}
+
+int heom_batch_get_rho(heom_batch* b, int32_t i, double* rho_out) {
+  if (!b || !rho_out) return fail(HEOM_EINVAL, "batch or rho_out is NULL");
+  if (i < 0 || i >= (int32_t)b->e.inst.size()) return fail(HEOM_EINVAL, "instance %d out of range", i);
+  return b->e.get_states(i, 1, rho_out, true);
+}
+
+int heom_batch_set_launch(heom_batch* b, int32_t team_ctas, int32_t block_threads, int32_t node_threads) {
+  if (!b) return fail(HEOM_EINVAL, "batch is NULL");
+  for (auto& kv : b->e.cfg) {
+    LaunchCfg n = kv.second;
+    n.mode = 0;
+    if (team_ctas > 0) n.team_ctas = team_ctas;
+    if (block_threads > 0) n.block = block_threads;
+    if (node_threads > 0) n.G = node_threads;
+    if (n.team_ctas < 1 || n.team_ctas > 16) return fail(HEOM_EINVAL, "team_ctas must be 1..16");
+    const int maxb = b->e.max_block();
+    if (n.block < 64 || n.block > maxb || n.block % 32)
+      return fail(HEOM_EINVAL, "block_threads must be 64..%d, multiple of 32", maxb);
+    if (n.G != 1 && n.G != 2 && n.G != 4 && n.G != 8) return fail(HEOM_EINVAL, "node_threads must be 1, 2, 4 or 8");
+    kv.second = n;
+  }
+  return HEOM_OK;
+}
+
+void heom_batch_destroy(heom_batch* b) { delete b; }
+
+}  // extern "C"
