@@ -1,0 +1,376 @@
+"""Benchmark of the HEOM RK4 hot path on one or more GB300 GPUs.
+
+One "step" is one complete solve of the FMO-like N = 7 trap workload
+(depth 6, 1716 hierarchy nodes, dt = 1 fs for 10 ps = 10 000 RK4 steps, seeded
+synthetic Hamiltonian) through the library's C ABI.  The headline value is
+node-RHS evaluations per second (nodes x 4 RK4 stages x steps / time) of the
+mixed-precision path (float auxiliaries, double rho and eta); the plain FP64
+path is timed beside it on the same input.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (N > 1) runs are replicas launched by torchrun: every rank solves
+its own copies of the workload; only the timing is reduced across ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1012_4382_gb300 import workloads  # noqa: E402
+
+METRIC = "HEOM node-RHS evals/s, batched solves/s and p99 latency vs plain FP64 path"
+UNIT = "node-RHS evals/s"
+WORKLOAD = "FMO-like N=7 with trap: K=6 (1716 nodes), dt=1 fs for 10 ps, seed 1234"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-scan measurement")
+    ap.add_argument("--cpu-sample-steps", type=int, default=0, help="RK4 steps of the oracle sample (0: auto)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_init(n):
+    rank, world, local = 0, 1, 0
+    if n > 1 or "WORLD_SIZE" in os.environ and int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        import torch.distributed as dist
+        rank = int(os.environ.get("RANK", "0"))
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        import torch
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# -------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[3:]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def algorithmic_bytes_per_node_step(N, elem_bytes):
+    """Horner-form RK4 over Hermitian-packed nodes: stage 0 reads y and writes
+    wa; stages 1-3 read the stage input and y and write the output, so a node
+    moves 11 packed arrays of N*N reals per step."""
+    return 11 * N * N * elem_bytes
+
+
+def oracle_sample(w, steps):
+    import oracle
+    oracle.build()
+    nodes = oracle.num_nodes(w["params"]["N"], w["params"]["K"])
+    t0 = time.perf_counter()
+    oracle.propagate(w["params"], w["rho0"], w["dt"], steps, steps)
+    dt = time.perf_counter() - t0
+    return {"value": nodes * 4.0 * steps / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d RK4 steps of the %d-node workload (%.2f s)" % (steps, nodes, dt)}
+
+
+# ----------------------------------------------------------------- reference
+
+def run_reference(args):
+    rank, world, _ = dist_init(args.gpus)
+    if rank != 0:
+        barrier(world)
+        return
+    w = workloads.fmo_trap()
+    steps = args.cpu_sample_steps or 20
+    for _ in range(max(args.warmup, 0)):
+        oracle_sample(w, 2)
+    vals = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_sample(w, steps))
+    wall = time.perf_counter() - t_all
+    v = sum(x["value"] for x in vals) / len(vals)
+    nodes = w["params"]["N"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": 1, "seq_len": None, "parallelism": "replicas",
+                   "sample": "each step: %d RK4 steps of the full hierarchy on the host cores" % steps},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                         "sample": vals[0]["sample"]},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    barrier(world)
+
+
+# ---------------------------------------------------------------------- ours
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    rank, world, local = dist_init(args.gpus)
+    assert torch.cuda.is_available(), "bench.py needs a CUDA GPU"
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_1012_4382_gb300 import build as heom_build
+    heom_build.build()
+    from paper_1012_4382_gb300 import heom
+
+    w = workloads.fmo_trap()
+    p = w["params"]
+    N, K = p["N"], p["K"]
+    nsteps, out_every, dt = w["nsteps"], w["out_every"], w["dt"]
+    nodes = heom.num_nodes(N, K)
+    units_per_solve = nodes * 4.0 * nsteps
+    nout = nsteps // out_every + 1
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    rho0_dev = torch.from_numpy(np.ascontiguousarray(w["rho0"])).to(dev)
+    d_pops = torch.empty(nout * N, dtype=torch.float64, device=dev)
+    d_el = torch.empty(2 * nout, dtype=torch.float64, device=dev)
+
+    def timed_device(ctx, steps, warm):
+        """Per-solve device time (ms) with inputs resident; L2 flushed between solves."""
+        times = []
+        with torch.cuda.stream(stream):
+            for i in range(warm + steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.set_rho0_device(rho0_dev)
+                ctx.propagate_device(dt, nsteps, out_every, d_pops, d_el)
+                e1.record(stream)
+                if i >= warm:
+                    times.append((e0, e1))
+        stream.synchronize()
+        ctx.synchronize()
+        return [a.elapsed_time(b) for a, b in times]
+
+    results = {}
+    for prec in ("fp32", "fp64"):
+        ctx = heom.Context(p, prec, stream=stream)
+        ctx.autotune(trial_steps=50)
+        results[prec] = {"ctx": ctx, "launch": ctx.get_launch()}
+
+    # ---- timed region: mixed-precision path (headline)
+    ctx = results["fp32"]["ctx"]
+    timed_device(ctx, 0, args.warmup)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    per = timed_device(ctx, args.steps, 0)
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    dev_ms = sum(per)
+    dev_ms_max = allreduce_max(dev_ms, world)
+    total_units = allreduce_sum(units_per_solve * args.steps, world)
+    value = total_units / (dev_ms_max * 1e-3)
+    pops_gpu = d_pops.view(nout, N).cpu().numpy()
+    eta_gpu = d_el.view(nout, 2)[:, 0].cpu().numpy()
+
+    # ---- e2e: host buffers through the public blocking API
+    e2e_times = []
+    for i in range(1 + args.steps):
+        t = time.perf_counter()
+        ctx.set_rho0(w["rho0"])
+        r = ctx.propagate(dt, nsteps, out_every)
+        if i > 0:
+            e2e_times.append(time.perf_counter() - t)
+    e2e_s = allreduce_max(sum(e2e_times), world)
+    e2e_value = total_units / e2e_s
+    h2d = 16 * N * N
+    d2h = 8 * (nout * N + 2 * nout)
+
+    # ---- plain FP64 path, same workload
+    ctx64 = results["fp64"]["ctx"]
+    timed_device(ctx64, 0, 1)
+    per64 = timed_device(ctx64, max(1, args.steps // 2), 0)
+    fp64_value = units_per_solve * len(per64) / (sum(per64) * 1e-3)
+    pops64 = d_pops.view(nout, N).cpu().numpy()
+    eta64 = d_el.view(nout, 2)[:, 0].cpu().numpy()
+
+    # ---- roofline of the dominant kernel (the persistent engine launch)
+    launch_ms = statistics.mean(per)
+    bytes_per_launch = algorithmic_bytes_per_node_step(N, 4) * nodes * nsteps
+    achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (f64 rho, populations and eta)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": world, "seq_len": None,
+                   "parallelism": "replicas x%d" % world,
+                   "l2": "flushed (256 MB write) before every solve; the 1.0 MB state is L2-resident within a solve",
+                   "launch": results["fp32"]["launch"]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "wall_s": wall,
+        "fp64_path": {"value": fp64_value, "unit": UNIT, "ms_per_solve": statistics.mean(per64),
+                      "launch": results["fp64"]["launch"],
+                      "mixed_vs_fp64_speedup": value / world / fp64_value,
+                      "max_abs_pop_diff_vs_mixed": float(np.abs(pops64 - pops_gpu).max()),
+                      "abs_eta_diff_vs_mixed": float(abs(eta64[-1] - eta_gpu[-1]))},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "heom_engine_kernel<7, float, mixed>",
+                     "algorithmic_bytes_per_launch": bytes_per_launch},
+        "eta_10ps": float(eta_gpu[-1]),
+    }
+    if rank == 0 and not args.no_batched:
+        line["batched"] = bench_batched(heom, torch, stream)
+    if rank == 0:
+        n_sample = args.cpu_sample_steps or 25
+        line["cpu_baseline"] = oracle_sample(w, n_sample)
+        print(json.dumps(line), flush=True)
+    for v in results.values():
+        v["ctx"].close()
+    barrier(world)
+
+
+def bench_batched(heom, torch, stream):
+    """Batched scan: 256 seeded N = 7 trap instances, depth 4..8, lambda and T
+    scanned, 5 ps each, mixed precision, one persistent launch."""
+    ws = workloads.batched_scan()
+    b = heom.Batch([w["params"] for w in ws], "fp32", stream=stream)
+    nodes = sum(heom.num_nodes(w["params"]["N"], w["params"]["K"]) for w in ws)
+    nsteps = ws[0]["nsteps"]
+    b.set_rho0([w["rho0"] for w in ws])
+    with torch.cuda.stream(stream):
+        b.propagate_device(1.0, nsteps, nsteps)
+    b.synchronize()
+    b.set_rho0([w["rho0"] for w in ws])
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        b.propagate_device(1.0, nsteps, nsteps)
+        e1.record(stream)
+    b.synchronize()
+    ms = e0.elapsed_time(e1)
+    eta, _ = b.efficiency()
+    b.close()
+    return {"workload": "256 x N=7 trap, K~U{4..8}, lambda~U(2,200), T~U(77,300), 5 ps, fp32 mixed",
+            "solves_per_s": len(ws) / (ms * 1e-3), "node_rhs_per_s": nodes * 4.0 * nsteps / (ms * 1e-3),
+            "ms": ms, "total_nodes": nodes, "eta_mean": float(np.mean(eta))}
+
+
+if __name__ == "__main__":
+    main()

@@ -182,7 +182,12 @@ def test_batch_matches_oracle_and_single_contexts():
         o = run_oracle(w, nsteps=steps[i], out_every=5)
         assert np.abs(res[i]["pops"] - o["pops"]).max() < TOL64
         assert np.abs(res[i]["eta"] - o["eta"]).max() < TOL64
-        assert abs(eta[i] - o["eta"][-1]) < TOL64
+        if steps[i] > 0:
+            o_end = run_oracle(w, nsteps=steps[i], out_every=steps[i])
+            assert abs(eta[i] - o_end["eta"][-1]) < TOL64
+            assert abs(loss[i] - o_end["loss"][-1]) < TOL64
+        else:
+            assert eta[i] == 0.0 and loss[i] == 0.0
 
 
 def test_batch_fp32_matches_oracle():
