@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-scan measurement")
     ap.add_argument("--cpu-sample-steps", type=int, default=0, help="RK4 steps of the oracle sample (0: auto)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline (profiling runs)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes (profiling runs)")
+    ap.add_argument("--solve-steps", type=int, default=0,
+                    help="RK4 steps per solve instead of the workload's 10 000 (profiling runs; not a bench value)")
     return ap.parse_args()
 
 
@@ -231,6 +235,8 @@ def main():
     p = w["params"]
     N, K = p["N"], p["K"]
     nsteps, out_every, dt = w["nsteps"], w["out_every"], w["dt"]
+    if args.solve_steps > 0:
+        nsteps = args.solve_steps
     nodes = heom.num_nodes(N, K)
     units_per_solve = nodes * 4.0 * nsteps
     nout = nsteps // out_every + 1
@@ -261,7 +267,8 @@ def main():
     results = {}
     for prec in ("fp32", "fp64"):
         ctx = heom.Context(p, prec, stream=stream)
-        ctx.autotune(trial_steps=50)
+        if not args.no_autotune:
+            ctx.autotune(trial_steps=50)
         results[prec] = {"ctx": ctx, "launch": ctx.get_launch()}
 
     # ---- timed region: mixed-precision path (headline)
@@ -338,7 +345,8 @@ def main():
         line["batched"] = bench_batched(heom, torch, stream)
     if rank == 0:
         n_sample = args.cpu_sample_steps or 25
-        line["cpu_baseline"] = oracle_sample(w, n_sample)
+        if not args.no_cpu:
+            line["cpu_baseline"] = oracle_sample(w, n_sample)
         print(json.dumps(line), flush=True)
     for v in results.values():
         v["ctx"].close()
