@@ -225,6 +225,46 @@ int heom_batch_set_launch(heom_batch* b, int32_t team_ctas, int32_t block_thread
 
 void heom_batch_destroy(heom_batch* b);
 
+/* --------------------------------------------- allocation-free propagation */
+
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot call cudaMalloc -- code that runs under a device-memory budget fixed
+ * before it starts, or inside a host framework that owns every device
+ * allocation -- and so cannot create a heom_ctx.
+ *
+ * One complete propagation from rho(0), like heom_create + heom_set_rho0 +
+ * heom_propagate_device on a fresh context, that allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine, no host heap.  All
+ * device working memory (node tables, coefficients, the state and both RK4
+ * stage buffers, launch descriptor, status words) lives in one file-scope
+ * device array of HEOM_STATIC_SCRATCH_BYTES, which every GPU that loads the
+ * library holds until the process exits.  Problems that need more than that
+ * (N = 7: up to depth 8 in HEOM_FP64 and depth 9 in HEOM_FP32_MIXED; N = 8:
+ * depth 6 and 7) are
+ * rejected with HEOM_EINVAL and a message giving the bytes needed; only
+ * N <= 8 is supported.
+ *
+ * Inputs: params (host, read during the call) and d_rho0, a device buffer of
+ * N*N complex doubles whose upper triangle and diagonal define the Hermitian
+ * rho(0).  Outputs (device, each may be NULL): d_pops[nout*N],
+ * d_eta_loss[nout*2] with nout = nsteps/out_every + 1 (rows as in
+ * heom_propagate_device), and d_rho_out[N*N complex], rho at the end.
+ * The work is queued on cuda_stream (a cudaStream_t; NULL = legacy default
+ * stream); the call waits for earlier work on that stream before it stages
+ * its inputs and returns once the propagation is queued.
+ *
+ * Set-up: the first call on each device looks up the device address of the
+ * static array (cudaGetSymbolAddress, with that device current); make that
+ * first call before any stream capture.  Every call shares the one array,
+ * which keeps the last call's contents; each call clears what must start at
+ * zero.  Calls whose work overlaps on the GPU (different streams, or other
+ * threads) race on the array and give wrong results: order them on one
+ * stream or synchronise between them. */
+#define HEOM_STATIC_SCRATCH_BYTES (8u << 20)
+int heom_propagate_static(const heom_params* params, const double* d_rho0, double dt_fs, int64_t nsteps,
+                          int64_t out_every, double* d_pops, double* d_eta_loss, double* d_rho_out,
+                          void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -111,3 +111,69 @@ void build_index(int N, int K, Index& out) {
 }
 
 }  // namespace heom
+
+namespace heom {
+
+namespace {
+
+struct TableWriter {
+  int N, K, Mpad;
+  int32_t* up;
+  int32_t* dn;
+  int64_t next;
+  int32_t cur[32];
+};
+
+void write_level(TableWriter& w, int j, int remaining, int level) {
+  if (j == w.N - 1) {
+    w.cur[j] = remaining;
+    const int64_t i = w.next++;
+    int32_t nb[32];
+    for (int k = 0; k < w.N; ++k) nb[k] = w.cur[k];
+    for (int k = 0; k < w.N; ++k) {
+      int32_t u = -1, d = -1;
+      if (level < w.K) {
+        nb[k] += 1;
+        u = (int32_t)rank_of(nb, w.N, w.K);
+        nb[k] -= 1;
+      }
+      if (w.cur[k] > 0) {
+        nb[k] -= 1;
+        d = (w.cur[k] << 24) | (int32_t)rank_of(nb, w.N, w.K);
+        nb[k] += 1;
+      }
+      w.up[(size_t)k * w.Mpad + i] = u;
+      w.dn[(size_t)k * w.Mpad + i] = d;
+    }
+    w.cur[j] = 0;
+    return;
+  }
+  for (int v = remaining; v >= 0; --v) {
+    w.cur[j] = v;
+    write_level(w, j + 1, remaining - v, level);
+  }
+  w.cur[j] = 0;
+}
+
+}  // namespace
+
+int64_t write_packed_tables(int N, int K, int Mpad, int32_t* up, int32_t* dn) {
+  if (N < 1 || N > 32 || K < 0) return -1;
+  TableWriter w;
+  w.N = N;
+  w.K = K;
+  w.Mpad = Mpad;
+  w.up = up;
+  w.dn = dn;
+  w.next = 0;
+  for (int k = 0; k < 32; ++k) w.cur[k] = 0;
+  for (int level = 0; level <= K; ++level) write_level(w, 0, level, level);
+  for (int k = 0; k < N; ++k)
+    for (int64_t i = w.next; i < Mpad; ++i) {
+      up[(size_t)k * Mpad + i] = -1;
+      dn[(size_t)k * Mpad + i] = -1;
+    }
+  return w.next;
+}
+
+}  // namespace heom

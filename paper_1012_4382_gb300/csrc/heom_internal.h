@@ -21,5 +21,8 @@ struct Index {
 };
 void build_index(int N, int K, Index& out);
 int64_t rank_of(const int32_t* n, int N, int K);
+// Writes the element-major tables up[j*Mpad + i] and the packed down links
+// (n_j << 24 | index) without allocating; returns the number of nodes.
+int64_t write_packed_tables(int N, int K, int Mpad, int32_t* up, int32_t* dn);
 
 }  // namespace heom

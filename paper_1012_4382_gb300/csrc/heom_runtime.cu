@@ -1131,3 +1131,237 @@ int heom_batch_set_launch(heom_batch* b, int32_t team_ctas, int32_t block_thread
 void heom_batch_destroy(heom_batch* b) { delete b; }
 
 }  // extern "C"
+
+// ----------------------------------------------------- allocation-free entry
+//
+// heom_propagate_static: one complete propagation that allocates nothing.
+// Callers that cannot call cudaMalloc (code running under a device-memory
+// budget fixed up front, or inside a host framework that owns every device
+// allocation) get all of the working memory from the file-scope array below:
+// the node tables, the coefficient block, the state and both RK4 stage
+// buffers, the launch descriptor and the status words.  The caller passes the
+// input rho(0) and the output buffers.  Host-side staging uses a static host
+// array under a mutex, so no heap memory is taken either.
+
+namespace {
+
+__device__ __align__(256) unsigned char g_heom_static_scratch[HEOM_STATIC_SCRATCH_BYTES];
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kStaticMaxDevices] = {};
+int32_t g_static_host_tables[HEOM_STATIC_SCRATCH_BYTES / 8];  // up and down tables, at most half the area
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+// Device address of the static area on the current device, looked up once per
+// device (with that device current) and cached.  Caller holds g_static_mu.
+int static_scratch_address(void** out) {
+  int dev = -1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kStaticMaxDevices) return fail(HEOM_EUNSUPPORTED, "device %d beyond %d", dev, kStaticMaxDevices);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    CUDA_TRY(cudaGetSymbolAddress(&p, g_heom_static_scratch));
+    if (!p) return fail(HEOM_ECUDA, "cudaGetSymbolAddress returned NULL for the static area");
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return HEOM_OK;
+}
+
+// Coefficient block of CoefLayout<R> written into a caller buffer (no heap).
+template <typename R>
+void write_coefficients_static(const heom_params& p, unsigned char* out, int* complex_h) {
+  using L = CoefLayout<R>;
+  const int N = p.N;
+  memset(out, 0, L::bytes(N));
+  R* c = reinterpret_cast<R*>(out);
+  double* cd = reinterpret_cast<double*>(out + L::dbl_offset(N));
+  double diag[heom::kMaxSmallN];
+  double mean = 0.0;
+  for (int a = 0; a < N; ++a) {
+    diag[a] = p.H[2 * (a * N + a)] + (p.add_reorg_to_H ? p.lambda[a] : 0.0);
+    mean += diag[a];
+  }
+  mean /= N;
+  int cplx = 0;
+  for (int a = 0; a < N; ++a)
+    for (int b = 0; b < N; ++b) {
+      if (a == b) continue;
+      c[L::J(N) + a * N + b] = (R)(p.H[2 * (a * N + b)] * kCmToRadPerFs);
+      const double im = p.H[2 * (a * N + b) + 1];
+      c[L::Ji(N) + a * N + b] = (R)(im * kCmToRadPerFs);
+      if (im != 0.0) cplx = 1;
+    }
+  const double kT = kBoltzmannCmPerK * p.T_kelvin * kCmToRadPerFs;
+  for (int a = 0; a < N; ++a) {
+    const double lam = p.lambda[a] * kCmToRadPerFs;
+    const double gam = p.gamma[a] * kCmToRadPerFs;
+    const double tr = p.trap_rate ? p.trap_rate[a] * kPerPsToPerFs : 0.0;
+    const double rc = p.recomb_rate ? p.recomb_rate[a] * kPerPsToPerFs : 0.0;
+    c[L::eps(N) + a] = (R)((diag[a] - mean) * kCmToRadPerFs);
+    c[L::ghalf(N) + a] = (R)(0.5 * (tr + rc));
+    c[L::alpha(N) + a] = (R)(2.0 * lam * kT);
+    c[L::beta(N) + a] = (R)(lam * gam);
+    c[L::gam(N) + a] = (R)gam;
+    cd[a] = tr;
+    cd[N + a] = rc;
+  }
+  *complex_h = cplx;
+}
+
+}  // namespace
+
+extern "C" int heom_propagate_static(const heom_params* params, const double* d_rho0, double dt_fs, int64_t nsteps,
+                                     int64_t out_every, double* d_pops, double* d_eta_loss, double* d_rho_out,
+                                     void* cuda_stream) {
+  TRY(validate(params, 0));
+  if (!d_rho0) return fail(HEOM_EINVAL, "d_rho0 is NULL");
+  if (nsteps < 0) return fail(HEOM_EINVAL, "nsteps < 0");
+  if (out_every < 1) return fail(HEOM_EINVAL, "out_every must be >= 1");
+  if (!(dt_fs > 0.0) || !std::isfinite(dt_fs)) return fail(HEOM_EINVAL, "dt_fs must be > 0");
+  const heom_params& p = *params;
+  const int N = p.N;
+  const bool fp64 = p.precision == HEOM_FP64;
+  const size_t rs = fp64 ? sizeof(double) : sizeof(float);
+  const int64_t M = heom::num_nodes(N, p.K);
+  const int Mpad = (int)((M + 31) / 32 * 32);
+  // layout of the static area
+  const size_t o_inst = 0;
+  const size_t o_team = align256(o_inst + sizeof(Inst));
+  const size_t o_status = align256(o_team + 4 * sizeof(int32_t));
+  const size_t o_gsync = o_status + 4 * sizeof(int);
+  const size_t o_acc = align256(o_gsync + 4 * sizeof(unsigned));
+  const size_t o_coef = align256(o_acc + 4 * sizeof(double));
+  const size_t coef_bytes = fp64 ? CoefLayout<double>::bytes(N) : CoefLayout<float>::bytes(N);
+  const size_t o_root = align256(o_coef + coef_bytes);
+  const size_t o_up = align256(o_root + 3 * sizeof(double) * N * N);
+  const size_t tab_bytes = sizeof(int32_t) * (size_t)N * Mpad;
+  const size_t o_dn = align256(o_up + tab_bytes);
+  const size_t arr = (size_t)N * N * Mpad * rs;
+  const size_t o_y = align256(o_dn + tab_bytes);
+  const size_t o_wa = align256(o_y + arr);
+  const size_t o_wb = align256(o_wa + arr);
+  const size_t total = align256(o_wb + arr);
+  if (total > HEOM_STATIC_SCRATCH_BYTES)
+    return fail(HEOM_EINVAL,
+                "N=%d, K=%d (%lld nodes) needs %zu bytes of working memory; the static area holds %u bytes",
+                N, p.K, (long long)M, total, (unsigned)HEOM_STATIC_SCRATCH_BYTES);
+  if (2 * tab_bytes > sizeof(g_static_host_tables)) return fail(HEOM_EINVAL, "node tables exceed the staging area");
+
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  void* base_v = nullptr;
+  TRY(static_scratch_address(&base_v));
+  unsigned char* base = static_cast<unsigned char*>(base_v);
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+
+  // host staging: tables, coefficients, descriptor (no heap)
+  int32_t* h_up = g_static_host_tables;
+  int32_t* h_dn = g_static_host_tables + (size_t)N * Mpad;
+  if (heom::write_packed_tables(N, p.K, Mpad, h_up, h_dn) != M) return fail(HEOM_EINVAL, "table construction failed");
+  alignas(8) unsigned char h_coef[CoefLayout<double>::bytes(heom::kMaxSmallN)];
+  int complex_h = 0;
+  if (fp64)
+    write_coefficients_static<double>(p, h_coef, &complex_h);
+  else
+    write_coefficients_static<float>(p, h_coef, &complex_h);
+
+  Inst d;
+  memset(&d, 0, sizeof(d));
+  d.N = N;
+  d.K = p.K;
+  d.M = (int32_t)M;
+  d.Mpad = Mpad;
+  d.complex_h = complex_h;
+  d.terminator = p.terminator;
+  d.up = reinterpret_cast<const int32_t*>(base + o_up);
+  d.dn = reinterpret_cast<const int32_t*>(base + o_dn);
+  d.y = base + o_y;
+  d.wa = base + o_wa;
+  d.wb = base + o_wb;
+  double* root = reinterpret_cast<double*>(base + o_root);
+  d.y0 = fp64 ? nullptr : root;
+  d.w0a = fp64 ? nullptr : root + N * N;
+  d.w0b = fp64 ? nullptr : root + 2 * N * N;
+  d.coef = base + o_coef;
+  d.acc = reinterpret_cast<double*>(base + o_acc);
+  d.out_pops = d_pops;
+  d.out_el = d_eta_loss;
+  d.nsteps = nsteps;
+  d.out_every = out_every;
+  d.dt = dt_fs;
+  const int32_t team[4] = {0, 1, 0, 0};  // team_first = {0, 1}, team_list = {0}
+
+  // one team (a thread-block cluster) for the single hierarchy
+  const int block = 256;
+  const int G = N >= 4 ? 4 : 1;
+  const int64_t units = ((M + 31) / 32) * G;
+  int ctas = (int)std::min<int64_t>(16, std::max<int64_t>(1, (units + block / 32 - 1) / (block / 32)));
+  int p2 = 1;
+  while (p2 < ctas) p2 <<= 1;
+  ctas = std::min(16, p2);
+  const void* k = fp64 ? heom::engine_kernel_f64(N) : heom::engine_kernel_f32(N);
+  if (!k) return fail(HEOM_EUNSUPPORTED, "no engine kernel for N=%d", N);
+  cudaLaunchConfig_t lc = {};
+  cudaLaunchAttribute at[1];
+  for (;;) {
+    if (ctas > 8) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    lc = cudaLaunchConfig_t{};
+    lc.gridDim = dim3(ctas);
+    lc.blockDim = dim3(block);
+    lc.stream = stream;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = ctas;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    int nclusters = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, k, &lc);
+    if (e == cudaSuccess && nclusters >= 1) break;
+    cudaGetLastError();
+    if (ctas == 1) return fail(HEOM_ECUDA, "no resident launch shape for N=%d", N);
+    ctas >>= 1;
+  }
+
+  // everything that must start at zero: status and barrier words, the state
+  CUDA_TRY(cudaMemsetAsync(base + o_status, 0, o_acc - o_status, stream));
+  CUDA_TRY(cudaMemsetAsync(base + o_y, 0, arr, stream));
+  CUDA_TRY(cudaMemcpyAsync(base + o_coef, h_coef, coef_bytes, cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(base + o_up, h_up, tab_bytes, cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(base + o_dn, h_dn, tab_bytes, cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(base + o_inst, &d, sizeof(d), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(base + o_team, team, sizeof(team), cudaMemcpyHostToDevice, stream));
+  const int NN = N * N;
+  if (fp64)
+    set_root_kernel<double><<<launch_blocks(NN, 128), 128, 0, stream>>>(static_cast<double*>(d.y), Mpad, nullptr,
+                                                                       d_rho0, N, d.acc);
+  else
+    set_root_kernel<float><<<launch_blocks(NN, 128), 128, 0, stream>>>(static_cast<float*>(d.y), Mpad, d.y0, d_rho0,
+                                                                      N, d.acc);
+  CUDA_TRY(cudaGetLastError());
+
+  EngineArgs A;
+  A.insts = reinterpret_cast<const Inst*>(base + o_inst);
+  A.team_first = reinterpret_cast<const int32_t*>(base + o_team);
+  A.team_list = reinterpret_cast<const int32_t*>(base + o_team) + 2;
+  A.G = G;
+  A.logG = ilog2(G);
+  A.mode = 0;
+  A.team_ctas = ctas;
+  A.gsync = reinterpret_cast<unsigned*>(base + o_gsync);
+  A.status = reinterpret_cast<int*>(base + o_status);
+  void* args[] = {&A};
+  CUDA_TRY(cudaLaunchKernelExC(&lc, k, args));
+  if (d_rho_out) {
+    if (fp64)
+      unpack_state_kernel<double><<<launch_blocks(NN, 128), 128, 0, stream>>>(static_cast<double*>(d.y), Mpad, 1, N,
+                                                                             nullptr, d_rho_out);
+    else
+      unpack_state_kernel<float><<<launch_blocks(NN, 128), 128, 0, stream>>>(static_cast<float*>(d.y), Mpad, 1, N,
+                                                                            d.y0, d_rho_out);
+    CUDA_TRY(cudaGetLastError());
+  }
+  return HEOM_OK;
+}
