@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--cpu-sample-steps", type=int, default=0, help="RK4 steps of the oracle sample (0: auto)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes (profiling runs)")
+    ap.add_argument("--launch", default="",
+                    help="mode,team_ctas,block,node_threads for the mixed path instead of autotuning (profiling runs)")
     ap.add_argument("--solve-steps", type=int, default=0,
                     help="RK4 steps per solve instead of the workload's 10 000 (profiling runs; not a bench value)")
     return ap.parse_args()
@@ -267,7 +269,10 @@ def main():
     results = {}
     for prec in ("fp32", "fp64"):
         ctx = heom.Context(p, prec, stream=stream)
-        if not args.no_autotune:
+        if args.launch and prec == "fp32":
+            m, c, b, g = (int(x) for x in args.launch.split(","))
+            ctx.set_launch(mode=m, team_ctas=c, block_threads=b, node_threads=g)
+        elif not args.no_autotune:
             ctx.autotune(trial_steps=50)
         results[prec] = {"ctx": ctx, "launch": ctx.get_launch()}
 

@@ -225,6 +225,51 @@ int heom_batch_set_launch(heom_batch* b, int32_t team_ctas, int32_t block_thread
 
 void heom_batch_destroy(heom_batch* b);
 
+/* -------------------------------------------------------------- serving */
+
+/* Continuous batching of propagation requests (the paper's FMO runs are
+ * single solves; the benchmark spec's serving workload drives this):
+ * requests of any size (N <= 8) are queued by heom_server_submit and admitted
+ * by heom_server_progress in arrival order while one of `slots` CUDA streams
+ * is free and the request's device state fits in `device_bytes`, a budget the
+ * server allocates once at creation.  Each admitted request runs as its own
+ * persistent launch (one thread-block cluster), so requests that arrive while
+ * others run overlap with them on the device; finished requests give their
+ * slot and memory back at the next progress call.  Node tables are cached per
+ * (N, K) for the server's lifetime.  Calls are serialised by an internal
+ * mutex; heom_server_progress never blocks on the device.
+ * Request states: 0 queued, 1 running, 2 done, 3 cancelled, 4 failed. */
+typedef struct heom_server heom_server;
+int heom_server_create(size_t device_bytes, int32_t slots, heom_server** out);
+
+/* Queues one propagation from rho0 (host N*N complex Hermitian) of nsteps
+ * steps of dt_fs with outputs every out_every steps.  HEOM_ENOMEM if the
+ * request can never fit in the budget; HEOM_EINVAL for malformed input.
+ * params and rho0 are copied. */
+int heom_server_submit(heom_server* s, const heom_params* params, const double* rho0, double dt_fs, int64_t nsteps,
+                       int64_t out_every, int64_t* request_id);
+
+/* Retires finished requests and admits queued ones; completed (may be NULL)
+ * receives the number retired by this call. */
+int heom_server_progress(heom_server* s, int32_t* completed);
+int heom_server_status(heom_server* s, int64_t request_id, int32_t* state);
+
+/* Results of a finished request: pops_out[nout*N], eta_out[nout],
+ * loss_out[nout] (each may be NULL), times_out[2] = seconds from submission
+ * to admission and to completion as seen by heom_server_progress. */
+int heom_server_result(heom_server* s, int64_t request_id, double* pops_out, double* eta_out, double* loss_out,
+                       double* times_out);
+
+/* Forgets a finished, failed or cancelled request. */
+int heom_server_release(heom_server* s, int64_t request_id);
+
+/* Cancels a queued request (running requests cannot be cancelled). */
+int heom_server_cancel(heom_server* s, int64_t request_id);
+int heom_server_stats(heom_server* s, int64_t* queued, int64_t* running, int64_t* bytes_in_use);
+
+/* Waits for all running requests' device work, then frees everything. */
+void heom_server_destroy(heom_server* s);
+
 /* --------------------------------------------- allocation-free propagation */
 
 /* The paper has no counterpart to this entry point; it serves callers that

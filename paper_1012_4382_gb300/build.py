@@ -20,7 +20,8 @@ OUT = os.path.join(HERE, "libheom.so")
 OBJ = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["heom_kernels_f64.cu", "heom_kernels_f32.cu", "heom_runtime.cu"]
+CU_SOURCES = ["heom_kernels_f64_real.cu", "heom_kernels_f64_cplx.cu", "heom_kernels_f32_real.cu",
+              "heom_kernels_f32_cplx.cu", "heom_runtime.cu"]
 CPP_SOURCES = ["heom_index.cpp"]
 
 

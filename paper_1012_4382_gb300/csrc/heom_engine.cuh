@@ -31,14 +31,18 @@
 //
 // Parallel decomposition.  A "team" (one thread-block cluster, or the whole
 // grid) owns one hierarchy at a time.  Nodes are grouped in blocks of 32
-// (one warp lane per node); each node block is split into G "unit groups":
-// warp (block, g) computes the packed elements whose unit index u satisfies
-// u % G == g.  Units are the N(N-1)/2 off-diagonal pairs (two packed reals
-// each) and the N diagonal entries.  Every thread keeps its node's whole
-// packed matrix in registers; all index arithmetic on it is resolved at
-// compile time.  Between RK4 stages the team synchronises with a hardware
+// (one warp lane per node); each node block is split into G "unit groups"
+// (1 <= G <= 32): warp (block, g) computes the packed elements whose unit
+// index u satisfies u % G == g.  Units are the N(N-1)/2 off-diagonal pairs
+// (two packed reals each) and the N diagonal entries.  With G <= 2 a thread
+// loads its node's whole packed matrix into registers once (RegView); with
+// larger G each unit loads the elements it needs (LoadView), so many short
+// threads share a node.  All index arithmetic on the packed matrix is resolved
+// at compile time.  Between RK4 stages the team synchronises with a hardware
 // cluster barrier (release/acquire at cluster scope) or a software grid
-// barrier with a bounded wait.
+// barrier with a bounded wait.  In mixed precision the root node rho is
+// handled by one warp per stage (root_task) so that its double-precision
+// accumulation runs with all 32 lanes active.
 #pragma once
 
 #include <cstdint>
@@ -64,14 +68,14 @@ struct Inst {
   double* y0;          // [N*N] packed root node in double (mixed precision only)
   double* w0a;
   double* w0b;
-  const void* coef;    // flat coefficient block, see coef_layout below
+  const void* coef;    // flat coefficient block, see CoefLayout below
+  const void* ngam;    // [Mpad] sum_j n_j gamma_j per node (R)
   double* acc;         // [2] eta and loss integrals
   double* out_pops;    // [nout][N] populations (may be null)
   double* out_el;      // [nout][2] eta, loss (may be null)
   int64_t nsteps;
   int64_t out_every;
   double dt;
-  double pad2;
 };
 
 // Coefficient block (host writes it with the same layout):
@@ -187,7 +191,79 @@ __device__ __forceinline__ bool team_barrier(const EngineArgs& A, unsigned& epoc
   return s_ok != 0;
 }
 
-// ------------------------------------------------------------ node update
+// ------------------------------------------------------------ node views
+//
+// A view gives the unit code access to one node's packed matrix P (packed
+// element p = k*N + l) and to its links, with every index known at compile
+// time.  RegView loads the whole matrix into registers once (cheapest in
+// instructions when one thread computes many units of its node); LoadView
+// loads each element where a unit needs it (fewest instructions per unit when
+// many threads share a node).
+
+template <int N, typename R>
+struct RegView {
+  R sg[N * N];
+  int up[N], dn[N];
+  R nj[N];
+  __device__ __forceinline__ RegView(const R* __restrict__ w, const int32_t* __restrict__ upt,
+                                     const int32_t* __restrict__ dnt, int Mp, int n) {
+#pragma unroll
+    for (int p = 0; p < N * N; ++p) sg[p] = w[p * Mp + n];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      up[j] = upt[j * Mp + n];
+      const int d = dnt[j * Mp + n];
+      dn[j] = d < 0 ? -1 : (d & 0xFFFFFF);
+      nj[j] = d < 0 ? R(0) : R(d >> 24);
+    }
+  }
+  template <int p>
+  __device__ __forceinline__ R P() const { return sg[p]; }
+  template <int j>
+  __device__ __forceinline__ int Up() const { return up[j]; }
+  template <int j>
+  __device__ __forceinline__ int Dn() const { return dn[j]; }
+  template <int j>
+  __device__ __forceinline__ R Nj() const { return nj[j]; }
+};
+
+template <int N, typename R>
+struct LoadView {
+  const R* __restrict__ w;
+  const int32_t* __restrict__ upt;
+  const int32_t* __restrict__ dnt;
+  int Mp;
+  __device__ __forceinline__ LoadView(const R* __restrict__ w_, const int32_t* __restrict__ upt_,
+                                      const int32_t* __restrict__ dnt_, int Mp_, int n)
+      : w(w_ + n), upt(upt_ + n), dnt(dnt_ + n), Mp(Mp_) {}
+  template <int p>
+  __device__ __forceinline__ R P() const { return w[p * Mp]; }
+  template <int j>
+  __device__ __forceinline__ int Up() const { return upt[j * Mp]; }
+  template <int j>
+  __device__ __forceinline__ int Dn() const {
+    const int d = dnt[j * Mp];
+    return d < 0 ? -1 : (d & 0xFFFFFF);
+  }
+  template <int j>
+  __device__ __forceinline__ R Nj() const {
+    const int d = dnt[j * Mp];
+    return d < 0 ? R(0) : R(d >> 24);
+  }
+};
+
+// S = Re sigma (symmetric), A = Im sigma (antisymmetric) from the packed view
+template <int N, int k, int l, class V>
+__device__ __forceinline__ auto Sv(const V& v) {
+  if constexpr (k <= l) return v.template P<k * N + l>();
+  else return v.template P<l * N + k>();
+}
+template <int N, int k, int l, class V, typename R>
+__device__ __forceinline__ R Av(const V& v) {
+  if constexpr (k < l) return v.template P<l * N + k>();
+  else if constexpr (k > l) return -v.template P<k * N + l>();
+  else return R(0);
+}
 
 template <typename R>
 struct StagePtrs {
@@ -199,43 +275,132 @@ struct StagePtrs {
   double hd;
 };
 
-// One node (n), one unit group (g of G), one RK4 stage (s).
-template <int N, typename R, bool MIXED>
-__device__ __forceinline__ void node_update(const Inst& I, const R* __restrict__ cf, const double* __restrict__ cfd,
-                                            const StagePtrs<R>& P, int s, int n, int g, int G, int64_t step_done) {
+// Right-hand side of unit u (pair (a, b) or diagonal a) of one node.
+// Returns the real part in re and, for pairs, the imaginary part in im.
+template <int N, int u, typename R, bool CPLX, class V>
+__device__ __forceinline__ void unit_rhs(const V& v, const R* __restrict__ cf, const R* __restrict__ win, int Mp,
+                                         R ngam, bool term, R& re, R& im) {
   using L = CoefLayout<R>;
-  constexpr int NN = N * N;
+  constexpr int NP = N * (N - 1) / 2;
+  re = R(0);
+  im = R(0);
+  if constexpr (u < NP) {
+    constexpr int a = pair_a(N, u);
+    constexpr int b = pair_b(N, u);
+    const R x = v.template P<a * N + b>();   // Re sigma_ab
+    const R yi = v.template P<b * N + a>();  // Im sigma_ab
+    // -i[J, sigma]: Re += [J, A]_ab, Im -= [J, S]_ab
+    static_for<0, N>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      if constexpr (k != a) {
+        const R jak = cf[L::J(N) + a * N + k];
+        if constexpr (k != b) re += jak * Av<N, k, b, V, R>(v);
+        im -= jak * Sv<N, k, b>(v);
+      }
+      if constexpr (k != b) {
+        const R jkb = cf[L::J(N) + k * N + b];
+        if constexpr (k != a) re -= Av<N, a, k, V, R>(v) * jkb;
+        im += Sv<N, a, k>(v) * jkb;
+      }
+    });
+    if constexpr (CPLX) {
+      // -i[i Ji, sigma] = [Ji, S] + i [Ji, A]
+      static_for<0, N>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        if constexpr (k != a) {
+          const R jak = cf[L::Ji(N) + a * N + k];
+          re += jak * Sv<N, k, b>(v);
+          if constexpr (k != b) im += jak * Av<N, k, b, V, R>(v);
+        }
+        if constexpr (k != b) {
+          const R jkb = cf[L::Ji(N) + k * N + b];
+          re -= Sv<N, a, k>(v) * jkb;
+          if constexpr (k != a) im -= Av<N, a, k, V, R>(v) * jkb;
+        }
+      });
+    }
+    // -i (eps_a - eps_b) sigma_ab, anti-Hermitian part and damping
+    const R d = cf[L::eps(N) + a] - cf[L::eps(N) + b];
+    const R c = ngam + cf[L::ghalf(N) + a] + cf[L::ghalf(N) + b];
+    re += d * yi - c * x;
+    im -= d * x + c * yi;
+    const R al_a = cf[L::alpha(N) + a], be_a = cf[L::beta(N) + a];
+    const R al_b = cf[L::alpha(N) + b], be_b = cf[L::beta(N) + b];
+    // up-couplings i V_j^x sigma_{n+e_j}: j = a gives +i, j = b gives -i
+    const int ua = v.template Up<a>();
+    const int ub = v.template Up<b>();
+    if (ua >= 0) {
+      re -= win[(b * N + a) * Mp + ua];
+      im += win[(a * N + b) * Mp + ua];
+    }
+    if (ub >= 0) {
+      re += win[(b * N + a) * Mp + ub];
+      im -= win[(a * N + b) * Mp + ub];
+    }
+    if (term) {
+      // sigma_{n+e_j} ~ (n_j+1)/(ngam+gamma_j) theta_j sigma_n, then i V_j^x of it
+      const R ca = (v.template Nj<a>() + R(1)) / (ngam + cf[L::gam(N) + a]);
+      const R cb = (v.template Nj<b>() + R(1)) / (ngam + cf[L::gam(N) + b]);
+      re += ca * (-al_a * x - be_a * yi) + cb * (-al_b * x + be_b * yi);
+      im += ca * (-al_a * yi + be_a * x) + cb * (-al_b * yi - be_b * x);
+    }
+    // down-couplings n_j theta_j sigma_{n-e_j}
+    const int da = v.template Dn<a>();
+    const int db = v.template Dn<b>();
+    if (da >= 0) {
+      const R n_a = v.template Nj<a>();
+      const R yr = win[(a * N + b) * Mp + da];
+      const R yy = win[(b * N + a) * Mp + da];
+      re += n_a * (be_a * yr - al_a * yy);
+      im += n_a * (al_a * yr + be_a * yy);
+    }
+    if (db >= 0) {
+      const R n_b = v.template Nj<b>();
+      const R yr = win[(a * N + b) * Mp + db];
+      const R yy = win[(b * N + a) * Mp + db];
+      re += n_b * (be_b * yr + al_b * yy);
+      im += n_b * (be_b * yy - al_b * yr);
+    }
+  } else {
+    constexpr int a = u - NP;
+    const R x = v.template P<a * N + a>();
+    static_for<0, N>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      if constexpr (k != a) re += R(2) * cf[L::J(N) + a * N + k] * Av<N, k, a, V, R>(v);
+    });
+    if constexpr (CPLX) {
+      static_for<0, N>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        if constexpr (k != a) re += R(2) * cf[L::Ji(N) + a * N + k] * Sv<N, k, a>(v);
+      });
+    }
+    re -= (ngam + R(2) * cf[L::ghalf(N) + a]) * x;
+    const int da = v.template Dn<a>();
+    if (da >= 0) re += R(2) * v.template Nj<a>() * cf[L::beta(N) + a] * win[(a * N + a) * Mp + da];
+  }
+}
+
+// All units of node n that belong to the unit mask, one RK4 stage.
+template <int N, typename R, bool MIXED, bool CPLX, class V>
+__device__ __forceinline__ void node_units(const Inst& I, const R* __restrict__ cf, const double* __restrict__ cfd,
+                                           const StagePtrs<R>& P, const V& v, int s, int n, uint64_t umask,
+                                           int64_t step_done) {
   constexpr int NP = N * (N - 1) / 2;
   constexpr int U = NP + N;
   const int Mp = I.Mpad;
   const R* __restrict__ win = P.win;
+  R* __restrict__ wout = P.wout;
+  const R* __restrict__ yv = P.y;
+  const R ngam = static_cast<const R*>(I.ngam)[n];
+  const bool term = I.terminator && (v.template Up<0>() < 0);
+  const bool out_row = (s == 3) && (n == 0) && I.out_pops && ((step_done + 1) % I.out_every) == 0;
 
-  R sg[NN];
-#pragma unroll
-  for (int p = 0; p < NN; ++p) sg[p] = win[(size_t)p * Mp + n];
-
-  int up[N], dn[N];
-  R nj[N];
-  R ngam = R(0);
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
-    up[j] = I.up[(size_t)j * Mp + n];
-    const int d = I.dn[(size_t)j * Mp + n];
-    dn[j] = d < 0 ? -1 : (d & 0xFFFFFF);
-    nj[j] = d < 0 ? R(0) : R(d >> 24);
-    ngam += nj[j] * cf[L::gam(N) + j];
-  }
-  const bool last_level = up[0] < 0;
-  const bool term = last_level && I.terminator;
-  const bool cplx = I.complex_h != 0;
-  const bool root = (n == 0);
-
-  // eta and loss: RK4 update with the stage-3 input of the root node.
-  if (s == 3 && root && g == 0) {
+  // eta and loss (plain FP64 path; the mixed path does this in root_task)
+  if (!MIXED && s == 3 && n == 0 && (umask & 1ull)) {
     double e = 0.0, l = 0.0;
 #pragma unroll
     for (int m = 0; m < N; ++m) {
-      const double x = MIXED ? I.w0a[m * N + m] : (double)sg[m * N + m];
+      const double x = (double)win[(m * N + m) * Mp];
       e += cfd[m] * x;
       l += cfd[N + m] * x;
     }
@@ -248,150 +413,168 @@ __device__ __forceinline__ void node_update(const Inst& I, const R* __restrict__
     }
   }
 
-  auto S = [&](int k, int l) -> R { return k <= l ? sg[k * N + l] : sg[l * N + k]; };
-  auto A = [&](int k, int l) -> R { return k < l ? sg[l * N + k] : (k > l ? -sg[k * N + l] : R(0)); };
-  auto Jr = [&](int k, int l) -> R { return cf[L::J(N) + k * N + l]; };
-  auto Jim = [&](int k, int l) -> R { return cf[L::Ji(N) + k * N + l]; };
-
-  auto store = [&](int p, R r, bool is_diag_a, int a) {
-    if (MIXED && root) {
-      const double v = I.y0[p] + P.hd * (double)r;
-      P.out64[p] = v;
-      P.wout[(size_t)p * Mp] = (R)v;
-      if (s == 3 && is_diag_a && I.out_pops && ((step_done + 1) % I.out_every) == 0)
-        I.out_pops[((step_done + 1) / I.out_every) * N + a] = v;
-    } else {
-      const R v = P.y[(size_t)p * Mp + n] + P.h * r;
-      P.wout[(size_t)p * Mp + n] = v;
-      if (s == 3 && root && is_diag_a && I.out_pops && ((step_done + 1) % I.out_every) == 0)
-        I.out_pops[((step_done + 1) / I.out_every) * N + a] = (double)v;
-    }
-  };
-
   static_for<0, U>([&](auto uc) {
     constexpr int u = decltype(uc)::value;
-    if ((u & (G - 1)) != g) return;
+    if (!((umask >> u) & 1ull)) return;
+    R re, im;
+    unit_rhs<N, u, R, CPLX>(v, cf, win, Mp, ngam, term, re, im);
     if constexpr (u < NP) {
       constexpr int a = pair_a(N, u);
       constexpr int b = pair_b(N, u);
-      const R x = sg[a * N + b];   // Re sigma_ab
-      const R yi = sg[b * N + a];  // Im sigma_ab
-      R re = R(0), im = R(0);
-      // -i[J, sigma]: Re += [J, A]_ab, Im -= [J, S]_ab
-      static_for<0, N>([&](auto kc) {
-        constexpr int k = decltype(kc)::value;
-        if constexpr (k != a) {
-          const R jak = Jr(a, k);
-          if constexpr (k != b) re += jak * A(k, b);
-          im -= jak * S(k, b);
-        }
-        if constexpr (k != b) {
-          const R jkb = Jr(k, b);
-          if constexpr (k != a) re -= A(a, k) * jkb;
-          im += S(a, k) * jkb;
-        }
-      });
-      if (cplx) {
-        // -i[i Ji, sigma] = [Ji, S] + i [Ji, A]
-        static_for<0, N>([&](auto kc) {
-          constexpr int k = decltype(kc)::value;
-          if constexpr (k != a) {
-            const R jak = Jim(a, k);
-            re += jak * S(k, b);
-            if constexpr (k != b) im += jak * A(k, b);
-          }
-          if constexpr (k != b) {
-            const R jkb = Jim(k, b);
-            re -= S(a, k) * jkb;
-            if constexpr (k != a) im -= A(a, k) * jkb;
-          }
-        });
-      }
-      // -i (eps_a - eps_b) sigma_ab and the anti-Hermitian + damping terms
-      const R d = cf[L::eps(N) + a] - cf[L::eps(N) + b];
-      const R c = ngam + cf[L::ghalf(N) + a] + cf[L::ghalf(N) + b];
-      re += d * yi - c * x;
-      im -= d * x + c * yi;
-      const R al_a = cf[L::alpha(N) + a], be_a = cf[L::beta(N) + a];
-      const R al_b = cf[L::alpha(N) + b], be_b = cf[L::beta(N) + b];
-      // up-couplings i V_j^x sigma_{n+e_j}: only j = a (+i) and j = b (-i) act on (a, b)
-      if (up[a] >= 0) {
-        const R xr = win[(size_t)(a * N + b) * Mp + up[a]];
-        const R xi = win[(size_t)(b * N + a) * Mp + up[a]];
-        re -= xi;
-        im += xr;
-      }
-      if (up[b] >= 0) {
-        const R xr = win[(size_t)(a * N + b) * Mp + up[b]];
-        const R xi = win[(size_t)(b * N + a) * Mp + up[b]];
-        re += xi;
-        im -= xr;
-      }
-      if (term) {
-        // sigma_{n+e_j} ~ (n_j+1)/(ngam+gamma_j) theta_j sigma_n, then i V_j^x of it
-        const R ca = (nj[a] + R(1)) / (ngam + cf[L::gam(N) + a]);
-        const R cb = (nj[b] + R(1)) / (ngam + cf[L::gam(N) + b]);
-        re += ca * (-al_a * x - be_a * yi) + cb * (-al_b * x + be_b * yi);
-        im += ca * (-al_a * yi + be_a * x) + cb * (-al_b * yi - be_b * x);
-      }
-      // down-couplings n_j theta_j sigma_{n-e_j}
-      if (dn[a] >= 0) {
-        const R yr = win[(size_t)(a * N + b) * Mp + dn[a]];
-        const R yy = win[(size_t)(b * N + a) * Mp + dn[a]];
-        re += nj[a] * (be_a * yr - al_a * yy);
-        im += nj[a] * (al_a * yr + be_a * yy);
-      }
-      if (dn[b] >= 0) {
-        const R yr = win[(size_t)(a * N + b) * Mp + dn[b]];
-        const R yy = win[(size_t)(b * N + a) * Mp + dn[b]];
-        re += nj[b] * (be_b * yr + al_b * yy);
-        im += nj[b] * (be_b * yy - al_b * yr);
-      }
-      store(a * N + b, re, false, a);
-      store(b * N + a, im, false, a);
+      constexpr int pr = a * N + b, pi = b * N + a;
+      wout[pr * Mp + n] = yv[pr * Mp + n] + P.h * re;
+      wout[pi * Mp + n] = yv[pi * Mp + n] + P.h * im;
     } else {
       constexpr int a = u - NP;
-      const R x = sg[a * N + a];
-      R re = R(0);
-      static_for<0, N>([&](auto kc) {
-        constexpr int k = decltype(kc)::value;
-        if constexpr (k != a) re += R(2) * Jr(a, k) * A(k, a);
-      });
-      if (cplx) {
-        static_for<0, N>([&](auto kc) {
-          constexpr int k = decltype(kc)::value;
-          if constexpr (k != a) re += R(2) * Jim(a, k) * S(k, a);
-        });
-      }
-      re -= (ngam + R(2) * cf[L::ghalf(N) + a]) * x;
-      if (dn[a] >= 0) re += R(2) * nj[a] * cf[L::beta(N) + a] * win[(size_t)(a * N + a) * Mp + dn[a]];
-      store(a * N + a, re, true, a);
+      constexpr int pd = a * N + a;
+      const R val = yv[pd * Mp + n] + P.h * re;
+      wout[pd * Mp + n] = val;
+      if (out_row) I.out_pops[((step_done + 1) / I.out_every) * N + a] = (double)val;
     }
   });
 }
 
-// Row 0 of the outputs (state at the start of the call), written by the
-// owners of the root's diagonal units.
-template <int N, typename R, bool MIXED>
-__device__ __forceinline__ void write_row0(const Inst& I, int g, int G) {
+// Mixed precision: the root node (rho itself) is computed by one warp, one
+// unit per lane, and accumulated in double with all lanes active (FP64 runs
+// at 1/64 of the FP32 rate here, so it must not serialise on one lane).
+template <int N, bool CPLX>
+__device__ __forceinline__ void root_task(const Inst& I, const float* __restrict__ cf, const double* __restrict__ cfd,
+                                          const StagePtrs<float>& P, int s, int lane, int64_t step_done) {
+  using L = CoefLayout<float>;
   constexpr int NP = N * (N - 1) / 2;
-  if (I.out_pops) {
-    for (int a = 0; a < N; ++a) {
-      if (((NP + a) & (G - 1)) != g) continue;
-      const double v = MIXED ? I.y0[a * N + a] : (double)static_cast<const R*>(I.y)[(size_t)(a * N + a) * I.Mpad];
-      I.out_pops[a] = v;
+  constexpr int U = NP + N;
+  const int Mp = I.Mpad;
+  const float* __restrict__ win = P.win;  // float copy of the root sits at column 0
+  const bool out_step = ((step_done + 1) % I.out_every) == 0;
+  if (s == 3) {
+    // eta and loss: the extra rows of the augmented RK4 system, from the
+    // stage-3 input of the root (in double)
+    double e = 0.0, l = 0.0;
+    if (lane < N) {
+      const double x = I.w0a[lane * N + lane];
+      e = cfd[lane] * x;
+      l = cfd[N + lane] * x;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      e += __shfl_down_sync(0xffffffffu, e, off);
+      l += __shfl_down_sync(0xffffffffu, l, off);
+    }
+    if (lane == 0) {
+      I.acc[0] += I.dt * e;
+      I.acc[1] += I.dt * l;
+      if (I.out_el && out_step) {
+        const int64_t o = (step_done + 1) / I.out_every;
+        I.out_el[2 * o] = I.acc[0];
+        I.out_el[2 * o + 1] = I.acc[1];
+      }
     }
   }
-  if (g == 0 && I.out_el) {
+  auto Pk = [&](int k, int l) -> float { return win[(k * N + l) * Mp]; };
+  auto S = [&](int k, int l) -> float { return k <= l ? Pk(k, l) : Pk(l, k); };
+  auto A = [&](int k, int l) -> float { return k < l ? Pk(l, k) : (k > l ? -Pk(k, l) : 0.f); };
+  const bool term = I.terminator && I.up[0] < 0;  // depth 0: the root is the last level
+  for (int uu = lane; uu < U; uu += 32) {
+    float re = 0.f, im = 0.f;
+    int a, b;
+    if (uu < NP) {
+      int r = uu;
+      a = 0;
+      while (r >= N - 1 - a) { r -= N - 1 - a; ++a; }
+      b = a + 1 + r;
+      const float x = Pk(a, b), yi = Pk(b, a);
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        if (k != a) {
+          const float jak = cf[L::J(N) + a * N + k];
+          re += jak * A(k, b);
+          im -= jak * S(k, b);
+        }
+        if (k != b) {
+          const float jkb = cf[L::J(N) + k * N + b];
+          re -= A(a, k) * jkb;
+          im += S(a, k) * jkb;
+        }
+        if (CPLX) {
+          if (k != a) {
+            const float jak = cf[L::Ji(N) + a * N + k];
+            re += jak * S(k, b);
+            im += jak * A(k, b);
+          }
+          if (k != b) {
+            const float jkb = cf[L::Ji(N) + k * N + b];
+            re -= S(a, k) * jkb;
+            im -= A(a, k) * jkb;
+          }
+        }
+      }
+      const float d = cf[L::eps(N) + a] - cf[L::eps(N) + b];
+      const float c = cf[L::ghalf(N) + a] + cf[L::ghalf(N) + b];
+      re += d * yi - c * x;
+      im -= d * x + c * yi;
+      const int ua = I.up[a * Mp], ub = I.up[b * Mp];
+      if (ua >= 0) {
+        re -= win[(b * N + a) * Mp + ua];
+        im += win[(a * N + b) * Mp + ua];
+      }
+      if (ub >= 0) {
+        re += win[(b * N + a) * Mp + ub];
+        im -= win[(a * N + b) * Mp + ub];
+      }
+      if (term) {
+        const float al_a = cf[L::alpha(N) + a], be_a = cf[L::beta(N) + a];
+        const float al_b = cf[L::alpha(N) + b], be_b = cf[L::beta(N) + b];
+        const float ca = 1.f / cf[L::gam(N) + a];
+        const float cb = 1.f / cf[L::gam(N) + b];
+        re += ca * (-al_a * x - be_a * yi) + cb * (-al_b * x + be_b * yi);
+        im += ca * (-al_a * yi + be_a * x) + cb * (-al_b * yi - be_b * x);
+      }
+    } else {
+      a = b = uu - NP;
+      const float x = Pk(a, a);
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        if (k != a) {
+          re += 2.f * cf[L::J(N) + a * N + k] * A(k, a);
+          if (CPLX) re += 2.f * cf[L::Ji(N) + a * N + k] * S(k, a);
+        }
+      }
+      re -= 2.f * cf[L::ghalf(N) + a] * x;
+    }
+    // accumulate in double: w = y0 + h r
+    const int pr = a * N + b;
+    const double vr = I.y0[pr] + P.hd * (double)re;
+    P.out64[pr] = vr;
+    P.wout[pr * Mp] = (float)vr;
+    if (a != b) {
+      const int pi = b * N + a;
+      const double vi = I.y0[pi] + P.hd * (double)im;
+      P.out64[pi] = vi;
+      P.wout[pi * Mp] = (float)vi;
+    } else if (s == 3 && I.out_pops && out_step) {
+      I.out_pops[((step_done + 1) / I.out_every) * N + a] = vr;
+    }
+  }
+}
+
+// Row 0 of the outputs (the state at the start of the call).
+template <int N, typename R, bool MIXED>
+__device__ __forceinline__ void write_row0(const Inst& I) {
+  if (I.out_pops)
+    for (int a = 0; a < N; ++a)
+      I.out_pops[a] = MIXED ? I.y0[a * N + a] : (double)static_cast<const R*>(I.y)[(a * N + a) * I.Mpad];
+  if (I.out_el) {
     I.out_el[0] = I.acc[0];
     I.out_el[1] = I.acc[1];
   }
 }
 
-template <int N, typename R, bool MIXED>
+template <int N, typename R, bool MIXED, bool CPLX, bool REG>
 __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) heom_engine_kernel(EngineArgs A) {
   __shared__ __align__(16) unsigned char s_coef[CoefLayout<R>::bytes(kMaxSmallN) + 64];
   __shared__ Inst s_inst;
+  __shared__ uint64_t s_umask[32];
+  constexpr int U = N * (N - 1) / 2 + N;
 
   int team, rank, team_size;
   if (A.mode == 0) {
@@ -408,6 +591,12 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) heom_engine_kernel
   const int W = team_size * wpc;
   const int lane = threadIdx.x & 31;
   const int G = A.G;
+  if (threadIdx.x < 32) {
+    uint64_t m = 0;
+    for (int u = 0; u < U; ++u)
+      if (u % G == (int)threadIdx.x) m |= 1ull << u;
+    s_umask[threadIdx.x] = m;
+  }
   unsigned epoch = 0;
 
   for (int li = A.team_first[team]; li < A.team_first[team + 1]; ++li) {
@@ -424,10 +613,10 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) heom_engine_kernel
     const R* cf = reinterpret_cast<const R*>(s_coef);
     const double* cfd = reinterpret_cast<const double*>(s_coef + CoefLayout<R>::dbl_offset(N));
     const int nblk = (I.M + 31) >> 5;
-    const int units = nblk << A.logG;
+    const int items = nblk * G;
+    const int nitems = items + (MIXED ? 1 : 0);  // the mixed path adds one root task
 
-    for (int g = 0; g < G; ++g)
-      if (warp == (g % W) && lane == 0) write_row0<N, R, MIXED>(I, g, G);
+    if (warp == 0 && lane == 0) write_row0<N, R, MIXED>(I);
 
     R* y = static_cast<R*>(I.y);
     R* wa = static_cast<R*>(I.wa);
@@ -443,11 +632,23 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) heom_engine_kernel
         else if (s == 2) { P.win = wb; P.wout = wa; P.out64 = I.w0a; P.hd = 0.5 * dt; }
         else { P.win = wa; P.wout = y;  P.out64 = I.y0; P.hd = dt; }
         P.h = (R)P.hd;
-        for (int u = warp; u < units; u += W) {
-          const int nb = u >> A.logG;
-          const int g = u & (G - 1);
+        for (int it = warp; it < nitems; it += W) {
+          if (MIXED && it == items) {
+            if constexpr (MIXED) root_task<N, CPLX>(I, cf, cfd, P, s, lane, t);
+            continue;
+          }
+          const int nb = it / G;
+          const int g = it - nb * G;
           const int n = (nb << 5) + lane;
-          if (n < I.M) node_update<N, R, MIXED>(I, cf, cfd, P, s, n, g, G, t);
+          if (n >= I.M || (MIXED && n == 0)) continue;
+          const uint64_t um = s_umask[g];
+          if constexpr (REG) {
+            const RegView<N, R> v(P.win, I.up, I.dn, I.Mpad, n);
+            node_units<N, R, MIXED, CPLX>(I, cf, cfd, P, v, s, n, um, t);
+          } else {
+            const LoadView<N, R> v(P.win, I.up, I.dn, I.Mpad, n);
+            node_units<N, R, MIXED, CPLX>(I, cf, cfd, P, v, s, n, um, t);
+          }
         }
         if (!team_barrier(A, epoch)) return;
       }

@@ -6,9 +6,16 @@
 
 namespace heom {
 
-// Engine kernel entry points for N = 1..8 (nullptr otherwise).
-const void* engine_kernel_f64(int N);
-const void* engine_kernel_f32(int N);
+// Engine kernel entry points for N = 1..8 (nullptr otherwise); reg selects
+// the register-resident node view.
+const void* engine_kernel_f64_real(int N, bool reg);
+const void* engine_kernel_f64_cplx(int N, bool reg);
+const void* engine_kernel_f32_real(int N, bool reg);
+const void* engine_kernel_f32_cplx(int N, bool reg);
+inline const void* engine_kernel(bool fp64, bool cplx, bool reg, int N) {
+  if (fp64) return cplx ? engine_kernel_f64_cplx(N, reg) : engine_kernel_f64_real(N, reg);
+  return cplx ? engine_kernel_f32_cplx(N, reg) : engine_kernel_f32_real(N, reg);
+}
 
 // Hierarchy index builder (heom_index.cpp).
 int64_t num_nodes(int N, int K);  // -1 on overflow beyond int64

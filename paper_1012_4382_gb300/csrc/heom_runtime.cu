@@ -7,7 +7,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <deque>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -216,8 +218,13 @@ struct Tables {
   int N = 0, K = 0;
   int64_t M = 0;
   int Mpad = 0;
+  std::vector<int32_t> multi;  // host copy of the multi-indices [M][N]
   DevBuf up, dn;
 };
+
+// Node tables keyed by (N, K); one cache per context, or one shared by all
+// requests of a server.
+typedef std::map<std::pair<int, int>, std::shared_ptr<Tables>> TableCache;
 
 struct Instance {
   int N = 0, K = 0;
@@ -225,7 +232,7 @@ struct Instance {
   int Mpad = 0;
   int complex_h = 0, terminator = 0;
   std::shared_ptr<Tables> tab;
-  DevBuf y, wa, wb, root64, coef, acc, stage;
+  DevBuf y, wa, wb, root64, coef, acc, stage, ngam;
   std::vector<unsigned char> coef_host;
 };
 
@@ -350,8 +357,10 @@ struct Engine {
   cudaStream_t stream = nullptr;
   Hooks hooks;
   std::vector<std::unique_ptr<Instance>> inst;
-  std::map<std::pair<int, int>, std::shared_ptr<Tables>> tables;
+  std::shared_ptr<TableCache> tables = std::make_shared<TableCache>();
   std::map<int, LaunchCfg> cfg;  // per N
+  bool pageable_args = false;     // stage launch descriptors from pageable memory (servers)
+  std::vector<unsigned char> h_args_pageable;
   DevBuf d_args, d_status, d_gsync, d_out;
   PinnedBuf h_args;
   cudaEvent_t args_done = nullptr;
@@ -376,7 +385,9 @@ struct Engine {
     return HEOM_OK;
   }
 
-  int init(const heom_params* params, int count, void* s) {
+  int init(const heom_params* params, int count, void* s, const Hooks* hooks_override = nullptr,
+           std::shared_ptr<TableCache> shared_tables = nullptr) {
+    if (shared_tables) tables = shared_tables;
     if (count < 1) return fail(HEOM_EINVAL, "count must be >= 1");
     if (!params) return fail(HEOM_EINVAL, "params is NULL");
     for (int i = 0; i < count; ++i) TRY(validate(&params[i], i));
@@ -392,7 +403,7 @@ struct Engine {
     CUDA_TRY(cudaGetDevice(&device));
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
     stream = static_cast<cudaStream_t>(s);
-    hooks = current_hooks();
+    hooks = hooks_override ? *hooks_override : current_hooks();
     CUDA_TRY(cudaEventCreateWithFlags(&args_done, cudaEventDisableTiming));
     TRY(d_status.alloc(sizeof(int) * 4, hooks));
     TRY(d_gsync.alloc(sizeof(unsigned) * 4, hooks));
@@ -421,12 +432,12 @@ struct Engine {
       if (prec == HEOM_FP64 && Mmax >= 256) {
         c.mode = 1;
         c.block = 256;
-        c.G = 4;
+        c.G = N >= 4 ? 8 : 2;
         c.team_ctas = 1;
       } else {
         c.mode = 0;
         c.block = 256;
-        c.G = N >= 4 ? 4 : 1;
+        c.G = N >= 4 ? 8 : 2;
         const int64_t units = ((Mmax + 31) / 32) * c.G;
         const int64_t warps = c.block / 32;
         int ctas = (int)std::min<int64_t>(16, std::max<int64_t>(1, (units + warps - 1) / warps));
@@ -455,8 +466,8 @@ struct Engine {
     else
       fill_coefficients<float>(p, in->coef_host, &in->complex_h);
     auto key = std::make_pair(p.N, p.K);
-    auto it = tables.find(key);
-    if (it == tables.end()) {
+    auto it = tables->find(key);
+    if (it == tables->end()) {
       auto t = std::make_shared<Tables>();
       t->N = p.N;
       t->K = p.K;
@@ -464,6 +475,7 @@ struct Engine {
       t->Mpad = in->Mpad;
       heom::Index idx;
       heom::build_index(p.N, p.K, idx);
+      t->multi = idx.multi;
       std::vector<int32_t> up((size_t)p.N * t->Mpad, -1), dn((size_t)p.N * t->Mpad, -1);
       for (int64_t n = 0; n < t->M; ++n)
         for (int j = 0; j < p.N; ++j) {
@@ -477,10 +489,26 @@ struct Engine {
       CUDA_TRY(cudaMemcpyAsync(t->up.p, up.data(), up.size() * 4, cudaMemcpyHostToDevice, stream));
       CUDA_TRY(cudaMemcpyAsync(t->dn.p, dn.data(), dn.size() * 4, cudaMemcpyHostToDevice, stream));
       CUDA_TRY(cudaStreamSynchronize(stream));
-      tables[key] = t;
+      (*tables)[key] = t;
       in->tab = t;
     } else {
       in->tab = it->second;
+    }
+    {
+      // sum_j n_j gamma_j per node (rad/fs), from the node multi-indices
+      const std::vector<int32_t>& multi = in->tab->multi;
+      std::vector<unsigned char> ng((size_t)in->Mpad * rsize(), 0);
+      for (int64_t n = 0; n < in->M; ++n) {
+        double v = 0.0;
+        for (int j = 0; j < p.N; ++j) v += multi[(size_t)n * p.N + j] * (p.gamma[j] * kCmToRadPerFs);
+        if (prec == HEOM_FP64)
+          reinterpret_cast<double*>(ng.data())[n] = v;
+        else
+          reinterpret_cast<float*>(ng.data())[n] = (float)v;
+      }
+      TRY(in->ngam.alloc(ng.size(), hooks));
+      CUDA_TRY(cudaMemcpyAsync(in->ngam.p, ng.data(), ng.size(), cudaMemcpyHostToDevice, stream));
+      CUDA_TRY(cudaStreamSynchronize(stream));
     }
     const size_t arr = (size_t)p.N * p.N * in->Mpad * rsize();
     TRY(in->y.alloc(arr, hooks));
@@ -558,6 +586,7 @@ struct Engine {
       d.w0a = root_ptr(in, 1);
       d.w0b = root_ptr(in, 2);
       d.coef = in.coef.p;
+      d.ngam = in.ngam.p;
       d.acc = in.acc.as<double>();
       d.out_pops = d_pops ? d_pops + pop_off : nullptr;
       d.out_el = d_el ? d_el + 2 * row_off : nullptr;
@@ -571,22 +600,24 @@ struct Engine {
     // group by N, assign instances to teams (longest first, least loaded team)
     struct Group {
       int N;
+      int cplx;
       LaunchCfg c;
       int nteams;
       std::vector<int32_t> first, list;
     };
     std::vector<Group> groups;
-    std::map<int, std::vector<int>> byN;
-    for (int i = 0; i < count; ++i) byN[inst[i]->N].push_back(i);
+    std::map<std::pair<int, int>, std::vector<int>> byN;
+    for (int i = 0; i < count; ++i) byN[std::make_pair(inst[i]->N, inst[i]->complex_h)].push_back(i);
     for (auto& kv : byN) {
       Group g;
-      g.N = kv.first;
+      g.N = kv.first.first;
+      g.cplx = kv.first.second;
       g.c = cfg[g.N];
       std::vector<int>& ids = kv.second;
       if (g.c.mode == 1) {
         g.nteams = 1;
       } else {
-        int maxc = max_active_teams(g.N, g.c);
+        int maxc = max_active_teams(g.N, g.cplx, g.c);
         if (maxc < 1) return HEOM_ECUDA;
         g.nteams = std::max(1, std::min<int>((int)ids.size(), maxc));
       }
@@ -625,9 +656,15 @@ struct Engine {
       CUDA_TRY(cudaEventSynchronize(args_done));
       args_pending = false;
     }
-    TRY(h_args.ensure(bytes));
+    unsigned char* hb = nullptr;
+    if (pageable_args) {
+      h_args_pageable.resize(bytes);
+      hb = h_args_pageable.data();
+    } else {
+      TRY(h_args.ensure(bytes));
+      hb = static_cast<unsigned char*>(h_args.p);
+    }
     if (d_args.bytes < bytes) TRY(d_args.alloc(bytes * 2, hooks));
-    unsigned char* hb = static_cast<unsigned char*>(h_args.p);
     memcpy(hb, hi.data(), sizeof(Inst) * count);
     for (size_t k = 0; k < groups.size(); ++k) {
       memcpy(hb + off_first[k], groups[k].first.data(), sizeof(int32_t) * groups[k].first.size());
@@ -649,17 +686,17 @@ struct Engine {
       A.team_ctas = g.c.team_ctas;
       A.gsync = d_gsync.as<unsigned>();
       A.status = d_status.as<int>();
-      TRY(launch(g.N, g.c, g.nteams, A));
+      TRY(launch(g.N, g.cplx, g.c, g.nteams, A));
     }
     return HEOM_OK;
   }
 
-  const void* kernel_for(int N) const {
-    return prec == HEOM_FP64 ? heom::engine_kernel_f64(N) : heom::engine_kernel_f32(N);
+  const void* kernel_for(int N, int cplx, const LaunchCfg& c) const {
+    return heom::engine_kernel(prec == HEOM_FP64, cplx != 0, c.G <= 2, N);
   }
 
-  int max_active_teams(int N, const LaunchCfg& c) {
-    const void* k = kernel_for(N);
+  int max_active_teams(int N, int cplx, const LaunchCfg& c) {
+    const void* k = kernel_for(N, cplx, c);
     if (!k) return fail(HEOM_EUNSUPPORTED, "no engine kernel for N=%d", N);
     if (c.team_ctas > 8) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t lc = {};
@@ -685,8 +722,8 @@ struct Engine {
     return n;
   }
 
-  int launch(int N, const LaunchCfg& c, int nteams, EngineArgs& A) {
-    const void* k = kernel_for(N);
+  int launch(int N, int cplx, const LaunchCfg& c, int nteams, EngineArgs& A) {
+    const void* k = kernel_for(N, cplx, c);
     if (!k) return fail(HEOM_EUNSUPPORTED, "no engine kernel for N=%d", N);
     if (c.mode == 1) {
       int per_sm = 0;
@@ -961,7 +998,7 @@ int heom_set_launch(heom_ctx* ctx, int32_t mode, int32_t team_ctas, int32_t bloc
   const int maxb = ctx->e.max_block();
   if (n.block < 64 || n.block > maxb || n.block % 32)
     return fail(HEOM_EINVAL, "block_threads must be 64..%d, multiple of 32", maxb);
-  if (n.G != 1 && n.G != 2 && n.G != 4 && n.G != 8) return fail(HEOM_EINVAL, "node_threads must be 1, 2, 4 or 8");
+  if (n.G < 1 || n.G > 32) return fail(HEOM_EINVAL, "node_threads must be 1..32");
   c = n;
   return HEOM_OK;
 }
@@ -993,7 +1030,7 @@ int heom_autotune(heom_ctx* ctx, int64_t trial_steps, double* best_us_per_step) 
   CUDA_TRY(cudaMemcpyAsync(sr.p, in.root64.p, in.root64.bytes, cudaMemcpyDeviceToDevice, e.stream));
   CUDA_TRY(cudaMemcpyAsync(sa.p, in.acc.p, in.acc.bytes, cudaMemcpyDeviceToDevice, e.stream));
   std::vector<LaunchCfg> cands;
-  for (int G : {1, 2, 4, 8}) {
+  for (int G : {1, 2, 4, 8, 16, 32}) {
     for (int block : {128, 256, 512})
       for (int ctas : {1, 2, 4, 8, 16}) {
         if (block > e.max_block()) continue;
@@ -1023,7 +1060,7 @@ int heom_autotune(heom_ctx* ctx, int64_t trial_steps, double* best_us_per_step) 
   const double dt = 1.0;
   for (const LaunchCfg& c : cands) {
     e.cfg[in.N] = c;
-    if (c.mode == 0 && e.max_active_teams(in.N, c) < 1) {
+    if (c.mode == 0 && e.max_active_teams(in.N, in.complex_h, c) < 1) {
       t_err.clear();
       continue;
     }
@@ -1122,7 +1159,7 @@ int heom_batch_set_launch(heom_batch* b, int32_t team_ctas, int32_t block_thread
     const int maxb = b->e.max_block();
     if (n.block < 64 || n.block > maxb || n.block % 32)
       return fail(HEOM_EINVAL, "block_threads must be 64..%d, multiple of 32", maxb);
-    if (n.G != 1 && n.G != 2 && n.G != 4 && n.G != 8) return fail(HEOM_EINVAL, "node_threads must be 1, 2, 4 or 8");
+    if (n.G < 1 || n.G > 32) return fail(HEOM_EINVAL, "node_threads must be 1..32");
     kv.second = n;
   }
   return HEOM_OK;
@@ -1239,8 +1276,10 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
   const size_t o_up = align256(o_root + 3 * sizeof(double) * N * N);
   const size_t tab_bytes = sizeof(int32_t) * (size_t)N * Mpad;
   const size_t o_dn = align256(o_up + tab_bytes);
+  const size_t o_ngam = align256(o_dn + tab_bytes);
+  const size_t ngam_bytes = (size_t)Mpad * rs;
   const size_t arr = (size_t)N * N * Mpad * rs;
-  const size_t o_y = align256(o_dn + tab_bytes);
+  const size_t o_y = align256(o_ngam + ngam_bytes);
   const size_t o_wa = align256(o_y + arr);
   const size_t o_wb = align256(o_wa + arr);
   const size_t total = align256(o_wb + arr);
@@ -1248,7 +1287,8 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
     return fail(HEOM_EINVAL,
                 "N=%d, K=%d (%lld nodes) needs %zu bytes of working memory; the static area holds %u bytes",
                 N, p.K, (long long)M, total, (unsigned)HEOM_STATIC_SCRATCH_BYTES);
-  if (2 * tab_bytes > sizeof(g_static_host_tables)) return fail(HEOM_EINVAL, "node tables exceed the staging area");
+  if (2 * tab_bytes + ngam_bytes > sizeof(g_static_host_tables))
+    return fail(HEOM_EINVAL, "node tables exceed the staging area");
 
   std::lock_guard<std::mutex> lk(g_static_mu);
   void* base_v = nullptr;
@@ -1260,6 +1300,19 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
   int32_t* h_up = g_static_host_tables;
   int32_t* h_dn = g_static_host_tables + (size_t)N * Mpad;
   if (heom::write_packed_tables(N, p.K, Mpad, h_up, h_dn) != M) return fail(HEOM_EINVAL, "table construction failed");
+  // sum_j n_j gamma_j per node, from the packed down links (n_j in the top byte)
+  unsigned char* h_ngam = reinterpret_cast<unsigned char*>(h_dn + (size_t)N * Mpad);
+  for (int64_t n = 0; n < Mpad; ++n) {
+    double v = 0.0;
+    for (int j = 0; j < N; ++j) {
+      const int32_t dv = h_dn[(size_t)j * Mpad + n];
+      if (dv >= 0) v += (dv >> 24) * (p.gamma[j] * kCmToRadPerFs);
+    }
+    if (fp64)
+      reinterpret_cast<double*>(h_ngam)[n] = v;
+    else
+      reinterpret_cast<float*>(h_ngam)[n] = (float)v;
+  }
   alignas(8) unsigned char h_coef[CoefLayout<double>::bytes(heom::kMaxSmallN)];
   int complex_h = 0;
   if (fp64)
@@ -1285,6 +1338,7 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
   d.w0a = fp64 ? nullptr : root + N * N;
   d.w0b = fp64 ? nullptr : root + 2 * N * N;
   d.coef = base + o_coef;
+  d.ngam = base + o_ngam;
   d.acc = reinterpret_cast<double*>(base + o_acc);
   d.out_pops = d_pops;
   d.out_el = d_eta_loss;
@@ -1295,13 +1349,13 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
 
   // one team (a thread-block cluster) for the single hierarchy
   const int block = 256;
-  const int G = N >= 4 ? 4 : 1;
+  const int G = N >= 4 ? 8 : 2;
   const int64_t units = ((M + 31) / 32) * G;
   int ctas = (int)std::min<int64_t>(16, std::max<int64_t>(1, (units + block / 32 - 1) / (block / 32)));
   int p2 = 1;
   while (p2 < ctas) p2 <<= 1;
   ctas = std::min(16, p2);
-  const void* k = fp64 ? heom::engine_kernel_f64(N) : heom::engine_kernel_f32(N);
+  const void* k = heom::engine_kernel(fp64, complex_h != 0, G <= 2, N);
   if (!k) return fail(HEOM_EUNSUPPORTED, "no engine kernel for N=%d", N);
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute at[1];
@@ -1331,6 +1385,7 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
   CUDA_TRY(cudaMemcpyAsync(base + o_coef, h_coef, coef_bytes, cudaMemcpyHostToDevice, stream));
   CUDA_TRY(cudaMemcpyAsync(base + o_up, h_up, tab_bytes, cudaMemcpyHostToDevice, stream));
   CUDA_TRY(cudaMemcpyAsync(base + o_dn, h_dn, tab_bytes, cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(base + o_ngam, h_ngam, ngam_bytes, cudaMemcpyHostToDevice, stream));
   CUDA_TRY(cudaMemcpyAsync(base + o_inst, &d, sizeof(d), cudaMemcpyHostToDevice, stream));
   CUDA_TRY(cudaMemcpyAsync(base + o_team, team, sizeof(team), cudaMemcpyHostToDevice, stream));
   const int NN = N * N;
@@ -1365,3 +1420,385 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
   }
   return HEOM_OK;
 }
+
+// ------------------------------------------------------------------ server
+//
+// Continuous batching of propagation requests of different sizes.  The server
+// owns one device buffer (its memory budget) and a pool of slots, each a CUDA
+// stream.  heom_server_progress() retires requests whose work has finished
+// (their memory goes back to the budget, their slot is free) and admits queued
+// requests in arrival order while a slot is free and their state fits in the
+// budget.  Each admitted request runs as its own persistent launch (one
+// thread-block cluster) on its slot's stream, so requests that arrive while
+// others run overlap with them on the device.  Node tables are cached per
+// (N, K) for the server's lifetime; the state stays resident until retirement.
+
+namespace {
+
+// First-fit allocator over one device buffer, with coalescing on release.
+struct Arena {
+  DevBuf buf;
+  std::map<size_t, size_t> free_blocks;  // offset -> size
+  std::map<size_t, size_t> used_blocks;  // offset -> size
+  size_t in_use = 0;
+
+  int init(size_t bytes) {
+    TRY(buf.alloc(bytes, Hooks()));
+    free_blocks.clear();
+    used_blocks.clear();
+    free_blocks[0] = buf.bytes;
+    in_use = 0;
+    return HEOM_OK;
+  }
+  void* alloc(size_t n) {
+    n = (n + 255) / 256 * 256;
+    for (auto it = free_blocks.begin(); it != free_blocks.end(); ++it) {
+      if (it->second < n) continue;
+      const size_t off = it->first, sz = it->second;
+      free_blocks.erase(it);
+      if (sz > n) free_blocks[off + n] = sz - n;
+      used_blocks[off] = n;
+      in_use += n;
+      return static_cast<unsigned char*>(buf.p) + off;
+    }
+    return nullptr;
+  }
+  void release(void* p) {
+    if (!p) return;
+    const size_t off = static_cast<size_t>(static_cast<unsigned char*>(p) - static_cast<unsigned char*>(buf.p));
+    auto u = used_blocks.find(off);
+    if (u == used_blocks.end()) return;
+    size_t start = off, size = u->second;
+    in_use -= size;
+    used_blocks.erase(u);
+    auto next = free_blocks.lower_bound(start);
+    if (next != free_blocks.end() && next->first == start + size) {
+      size += next->second;
+      free_blocks.erase(next);
+    }
+    auto prev = free_blocks.lower_bound(start);
+    if (prev != free_blocks.begin()) {
+      --prev;
+      if (prev->first + prev->second == start) {
+        start = prev->first;
+        size += prev->second;
+        free_blocks.erase(prev);
+      }
+    }
+    free_blocks[start] = size;
+  }
+};
+
+void* arena_alloc_hook(size_t n, void* user) { return static_cast<Arena*>(user)->alloc(n); }
+void arena_free_hook(void* p, size_t, void* user) { static_cast<Arena*>(user)->release(p); }
+
+enum { kReqQueued = 0, kReqRunning = 1, kReqDone = 2, kReqCancelled = 3, kReqFailed = 4 };
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+  int64_t id = 0;
+  int state = kReqQueued;
+  heom_params p;
+  std::vector<double> H, lam, gam, trap, recomb, rho0;
+  double dt = 1.0;
+  int64_t nsteps = 0, out_every = 1, nout = 1;
+  size_t need = 0;
+  std::unique_ptr<Engine> eng;
+  void* d_out = nullptr;
+  int slot = -1;
+  std::vector<double> pops, el;
+  double t_submit = 0, t_start = 0, t_done = 0;
+  std::string err;
+};
+
+struct Slot {
+  cudaStream_t s = nullptr;
+  cudaEvent_t done = nullptr;
+  PinnedBuf host;
+  int64_t req = -1;
+};
+
+// Device bytes a request needs, rounded like the arena rounds (tables counted
+// when they are not cached yet).
+size_t request_bytes(const heom_params& p, int64_t nout, bool tables_cached) {
+  auto r = [](size_t v) { return (v + 255) / 256 * 256; };
+  const size_t rs = p.precision == HEOM_FP64 ? 8 : 4;
+  const int64_t M = heom::num_nodes(p.N, p.K);
+  const size_t Mpad = (size_t)((M + 31) / 32 * 32);
+  const size_t NN = (size_t)p.N * p.N;
+  size_t b = 3 * r(NN * Mpad * rs) + r(Mpad * rs) + r(3 * 8 * NN) + r(4096) + r(4 * 8) + r(2 * 8 * NN) + 2 * r(16) +
+             r(2 * (sizeof(Inst) + 64)) + r(8 * (size_t)nout * (p.N + 2));
+  if (!tables_cached) b += 2 * r(4 * (size_t)p.N * Mpad);
+  return b;
+}
+
+}  // namespace
+
+struct heom_server {
+  std::mutex mu;
+  Arena arena;
+  Hooks hooks;
+  std::vector<Slot> slots;
+  std::map<int64_t, std::unique_ptr<Request>> reqs;
+  std::deque<int64_t> queue;
+  int64_t next_id = 1;
+  std::shared_ptr<TableCache> tables = std::make_shared<TableCache>();
+  int device = 0;
+
+  ~heom_server() {
+    for (auto& s : slots)
+      if (s.s) cudaStreamSynchronize(s.s);
+    reqs.clear();     // engines give their blocks back to the arena
+    tables.reset();
+    for (auto& s : slots) {
+      if (s.done) cudaEventDestroy(s.done);
+      if (s.s) cudaStreamDestroy(s.s);
+    }
+  }
+
+  LaunchCfg launch_for(int N, int64_t M) const {
+    LaunchCfg c;
+    c.mode = 0;
+    c.block = 256;
+    c.G = N >= 4 ? 8 : 2;
+    const int64_t units = ((M + 31) / 32) * c.G;
+    int ctas = (int)std::min<int64_t>(8, std::max<int64_t>(1, units / 16));
+    int p2 = 1;
+    while (p2 < ctas) p2 <<= 1;
+    c.team_ctas = std::min(8, p2);
+    return c;
+  }
+
+  int start(Request& q, int si) {
+    Slot& sl = slots[si];
+    auto eng = std::make_unique<Engine>();
+    eng->pageable_args = true;
+    int rc = eng->init(&q.p, 1, sl.s, &hooks, tables);
+    if (rc != HEOM_OK) return rc;
+    eng->cfg[q.p.N] = launch_for(q.p.N, eng->inst[0]->M);
+    TRY(eng->set_rho0_host(0, q.rho0.data()));
+    const size_t out_bytes = sizeof(double) * (size_t)q.nout * (q.p.N + 2);
+    q.d_out = arena.alloc(out_bytes);
+    if (!q.d_out) return fail(HEOM_ENOMEM, "server budget exhausted (outputs)");
+    double* d_pops = static_cast<double*>(q.d_out);
+    double* d_el = d_pops + q.nout * q.p.N;
+    rc = eng->propagate(&q.dt, &q.nsteps, q.out_every, d_pops, d_el);
+    if (rc != HEOM_OK) return rc;
+    TRY(sl.host.ensure(out_bytes));
+    CUDA_TRY(cudaMemcpyAsync(sl.host.p, q.d_out, out_bytes, cudaMemcpyDeviceToHost, sl.s));
+    CUDA_TRY(cudaEventRecord(sl.done, sl.s));
+    q.eng = std::move(eng);
+    q.slot = si;
+    q.state = kReqRunning;
+    q.t_start = now_s();
+    sl.req = q.id;
+    return HEOM_OK;
+  }
+
+  int progress(int32_t* completed) {
+    int done = 0;
+    for (size_t si = 0; si < slots.size(); ++si) {
+      Slot& sl = slots[si];
+      if (sl.req < 0) continue;
+      cudaError_t e = cudaEventQuery(sl.done);
+      if (e == cudaErrorNotReady) continue;
+      Request& q = *reqs[sl.req];
+      if (e != cudaSuccess) {
+        q.state = kReqFailed;
+        q.err = cudaGetErrorString(e);
+        cudaGetLastError();
+      } else {
+        const double* h = static_cast<const double*>(sl.host.p);
+        q.pops.assign(h, h + q.nout * q.p.N);
+        q.el.assign(h + q.nout * q.p.N, h + q.nout * (q.p.N + 2));
+        q.state = kReqDone;
+      }
+      q.t_done = now_s();
+      q.eng.reset();
+      arena.release(q.d_out);
+      q.d_out = nullptr;
+      q.slot = -1;
+      sl.req = -1;
+      ++done;
+    }
+    // admit in arrival order while a slot is free and the state fits
+    while (!queue.empty()) {
+      int si = -1;
+      for (size_t k = 0; k < slots.size(); ++k)
+        if (slots[k].req < 0) {
+          si = (int)k;
+          break;
+        }
+      if (si < 0) break;
+      Request& q = *reqs[queue.front()];
+      const bool cached = tables->count(std::make_pair(q.p.N, q.p.K)) != 0;
+      if (arena.in_use + request_bytes(q.p, q.nout, cached) > arena.buf.bytes) break;
+      int rc = start(q, si);
+      if (rc != HEOM_OK) {
+        q.eng.reset();
+        if (q.d_out) arena.release(q.d_out);
+        q.d_out = nullptr;
+        if (rc == HEOM_ENOMEM) break;  // wait for memory to free up
+        q.state = kReqFailed;
+        q.err = t_err;
+        queue.pop_front();
+        continue;
+      }
+      queue.pop_front();
+    }
+    if (completed) *completed = done;
+    return HEOM_OK;
+  }
+};
+
+extern "C" {
+
+int heom_server_create(size_t device_bytes, int32_t slots, heom_server** out) {
+  if (!out) return fail(HEOM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (slots < 1 || slots > 1024) return fail(HEOM_EINVAL, "slots must be 1..1024");
+  if (device_bytes < (1u << 20)) return fail(HEOM_EINVAL, "device_bytes must be at least 1 MiB");
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(HEOM_ECUDA, "no usable CUDA device (%s)", cudaGetErrorString(e));
+  }
+  auto s = std::make_unique<heom_server>();
+  CUDA_TRY(cudaGetDevice(&s->device));
+  TRY(s->arena.init(device_bytes));
+  s->hooks.alloc = arena_alloc_hook;
+  s->hooks.release = arena_free_hook;
+  s->hooks.user = &s->arena;
+  s->slots.resize(slots);
+  for (auto& sl : s->slots) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+  }
+  *out = s.release();
+  return HEOM_OK;
+}
+
+void heom_server_destroy(heom_server* s) { delete s; }
+
+int heom_server_submit(heom_server* s, const heom_params* params, const double* rho0, double dt_fs, int64_t nsteps,
+                       int64_t out_every, int64_t* request_id) {
+  if (!s || !request_id) return fail(HEOM_EINVAL, "server or request_id is NULL");
+  TRY(validate(params, 0));
+  TRY(validate_rho(rho0, params->N));
+  if (nsteps < 0) return fail(HEOM_EINVAL, "nsteps < 0");
+  if (out_every < 1) return fail(HEOM_EINVAL, "out_every must be >= 1");
+  if (!(dt_fs > 0.0) || !std::isfinite(dt_fs)) return fail(HEOM_EINVAL, "dt_fs must be > 0");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto q = std::make_unique<Request>();
+  const int N = params->N;
+  q->p = *params;
+  q->H.assign(params->H, params->H + 2 * N * N);
+  q->lam.assign(params->lambda, params->lambda + N);
+  q->gam.assign(params->gamma, params->gamma + N);
+  if (params->trap_rate) q->trap.assign(params->trap_rate, params->trap_rate + N);
+  if (params->recomb_rate) q->recomb.assign(params->recomb_rate, params->recomb_rate + N);
+  q->p.H = q->H.data();
+  q->p.lambda = q->lam.data();
+  q->p.gamma = q->gam.data();
+  q->p.trap_rate = params->trap_rate ? q->trap.data() : nullptr;
+  q->p.recomb_rate = params->recomb_rate ? q->recomb.data() : nullptr;
+  q->rho0.assign(rho0, rho0 + 2 * N * N);
+  q->dt = dt_fs;
+  q->nsteps = nsteps;
+  q->out_every = out_every;
+  q->nout = nsteps / out_every + 1;
+  q->need = request_bytes(q->p, q->nout, false);
+  if (q->need > s->arena.buf.bytes)
+    return fail(HEOM_ENOMEM, "request needs %zu device bytes; the server's budget is %zu", q->need,
+                s->arena.buf.bytes);
+  q->id = s->next_id++;
+  q->t_submit = now_s();
+  *request_id = q->id;
+  s->queue.push_back(q->id);
+  s->reqs[q->id] = std::move(q);
+  return HEOM_OK;
+}
+
+int heom_server_progress(heom_server* s, int32_t* completed) {
+  if (!s) return fail(HEOM_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  int cur = -1;
+  CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != s->device) CUDA_TRY(cudaSetDevice(s->device));
+  return s->progress(completed);
+}
+
+int heom_server_status(heom_server* s, int64_t id, int32_t* state) {
+  if (!s || !state) return fail(HEOM_EINVAL, "server or state is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return fail(HEOM_EINVAL, "unknown request %lld", (long long)id);
+  *state = it->second->state;
+  return HEOM_OK;
+}
+
+int heom_server_result(heom_server* s, int64_t id, double* pops_out, double* eta_out, double* loss_out,
+                       double* times_out) {
+  if (!s) return fail(HEOM_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return fail(HEOM_EINVAL, "unknown request %lld", (long long)id);
+  Request& q = *it->second;
+  if (q.state == kReqFailed) return fail(HEOM_ECUDA, "request %lld failed: %s", (long long)id, q.err.c_str());
+  if (q.state != kReqDone) return fail(HEOM_EINVAL, "request %lld is not finished", (long long)id);
+  if (pops_out) memcpy(pops_out, q.pops.data(), sizeof(double) * q.pops.size());
+  for (int64_t o = 0; o < q.nout; ++o) {
+    if (eta_out) eta_out[o] = q.el[2 * o];
+    if (loss_out) loss_out[o] = q.el[2 * o + 1];
+  }
+  if (times_out) {
+    times_out[0] = q.t_start - q.t_submit;
+    times_out[1] = q.t_done - q.t_submit;
+  }
+  return HEOM_OK;
+}
+
+int heom_server_release(heom_server* s, int64_t id) {
+  if (!s) return fail(HEOM_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return fail(HEOM_EINVAL, "unknown request %lld", (long long)id);
+  const int st = it->second->state;
+  if (st == kReqQueued || st == kReqRunning) return fail(HEOM_EINVAL, "request %lld is still active", (long long)id);
+  s->reqs.erase(it);
+  return HEOM_OK;
+}
+
+int heom_server_cancel(heom_server* s, int64_t id) {
+  if (!s) return fail(HEOM_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return fail(HEOM_EINVAL, "unknown request %lld", (long long)id);
+  if (it->second->state != kReqQueued)
+    return fail(HEOM_EINVAL, "request %lld is not queued (only queued requests can be cancelled)", (long long)id);
+  it->second->state = kReqCancelled;
+  for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+    if (*q == id) {
+      s->queue.erase(q);
+      break;
+    }
+  return HEOM_OK;
+}
+
+int heom_server_stats(heom_server* s, int64_t* queued, int64_t* running, int64_t* bytes_in_use) {
+  if (!s) return fail(HEOM_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  int64_t r = 0;
+  for (auto& sl : s->slots)
+    if (sl.req >= 0) ++r;
+  if (queued) *queued = (int64_t)s->queue.size();
+  if (running) *running = r;
+  if (bytes_in_use) *bytes_in_use = (int64_t)s->arena.in_use;
+  return HEOM_OK;
+}
+
+}  // extern "C"

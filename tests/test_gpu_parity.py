@@ -91,9 +91,9 @@ def test_random_instances_fp64(N, K, cplx, term):
     compare_states(g["state"], o, N, K, TOL64)
 
 
-@pytest.mark.parametrize("N,K", [(3, 3), (7, 3), (8, 2)])
-def test_random_instances_fp32(N, K):
-    w = workloads.random_instance(N, K, seed=7 + N, complex_h=True, terminator=1)
+@pytest.mark.parametrize("N,K,cplx,term", CASES)
+def test_random_instances_fp32(N, K, cplx, term):
+    w = workloads.random_instance(N, K, seed=7 + N + K, complex_h=cplx, terminator=term)
     g = run_gpu(w, "fp32")
     o = run_oracle(w)
     assert np.abs(g["pops"] - o["pops"]).max() < TOL32_POP
@@ -101,8 +101,8 @@ def test_random_instances_fp32(N, K):
 
 
 SHAPES = ([dict(mode=0, team_ctas=c, block_threads=b, node_threads=G) for c in (1, 2, 4, 8, 16)
-           for b in (128, 512) for G in (1, 2, 4, 8)]
-          + [dict(mode=1, team_ctas=1, block_threads=b, node_threads=G) for b in (128, 256) for G in (1, 8)])
+           for b in (128, 512) for G in (1, 2, 3, 8, 32)]
+          + [dict(mode=1, team_ctas=1, block_threads=b, node_threads=G) for b in (128, 256) for G in (1, 8, 28)])
 
 
 @pytest.fixture(scope="module")
@@ -254,7 +254,7 @@ def test_torch_caching_allocator_hook():
 def test_invalid_launch_shapes_rejected():
     w = workloads.dimer()
     with heom.Context(w["params"]) as c:
-        for bad in [dict(mode=2), dict(team_ctas=17), dict(block_threads=48), dict(node_threads=3)]:
+        for bad in [dict(mode=2), dict(team_ctas=17), dict(block_threads=48), dict(node_threads=33)]:
             with pytest.raises(heom.HeomError) as e:
                 c.set_launch(**bad)
             assert e.value.code == heom.EINVAL
