@@ -172,12 +172,16 @@ int heom_set_state(heom_ctx* ctx, const double* state_in, const double* extra);
 int heom_ctx_num_nodes(const heom_ctx* ctx, int64_t* out);
 
 /* Launch shape.  mode 0: one thread-block cluster of `team_ctas` CTAs
- * (1..16) per hierarchy with hardware cluster barriers between RK4 stages;
- * mode 1: the whole GPU per hierarchy (cooperative launch, software grid
- * barrier with a bounded wait).  block_threads: multiple of 32, 64..512
+ * (1..16) per hierarchy, state in device memory, hardware cluster barriers
+ * between RK4 stages; mode 1: the whole GPU per hierarchy (cooperative launch,
+ * software grid barrier with a bounded wait); mode 2 (HEOM_FP32_MIXED only):
+ * like mode 0 but the whole hierarchy lives in the cluster's distributed
+ * shared memory during the call (HEOM_EINVAL at propagate time if it does
+ * not fit in team_ctas CTAs).  block_threads: multiple of 32, 64..512
  * (64..256 for HEOM_FP64, whose kernels are compiled for that register budget);
- * node_threads: threads sharing one node's matrix (1, 2, 4 or 8).  Any
- * argument <= 0 keeps the current value. */
+ * node_threads: threads sharing one node's matrix, 1..32 (1 or 2 keep the
+ * node's matrix in registers).  A negative mode or a non-positive value keeps
+ * the current setting. */
 int heom_set_launch(heom_ctx* ctx, int32_t mode, int32_t team_ctas, int32_t block_threads, int32_t node_threads);
 int heom_get_launch(const heom_ctx* ctx, int32_t* mode, int32_t* team_ctas, int32_t* block_threads,
                     int32_t* node_threads);
@@ -220,8 +224,9 @@ int heom_batch_efficiency(heom_batch* b, double* eta_out, double* loss_out);
 int heom_batch_get_rho(heom_batch* b, int32_t i, double* rho_out);
 
 /* Launch shape of the batch's persistent launches (see heom_set_launch;
- * mode must be 0). */
-int heom_batch_set_launch(heom_batch* b, int32_t team_ctas, int32_t block_threads, int32_t node_threads);
+ * mode 0 or 2, negative keeps the current mode). */
+int heom_batch_set_launch(heom_batch* b, int32_t mode, int32_t team_ctas, int32_t block_threads,
+                          int32_t node_threads);
 
 void heom_batch_destroy(heom_batch* b);
 

@@ -54,6 +54,7 @@
 namespace heom {
 
 constexpr int kMaxSmallN = 8;
+constexpr int kMaxSites = 24;
 constexpr int kStatusTimeout = 1;
 
 // Per-instance device descriptor (host fills it; see heom_runtime.cu).
@@ -193,63 +194,155 @@ __device__ __forceinline__ bool team_barrier(const EngineArgs& A, unsigned& epoc
 
 // ------------------------------------------------------------ node views
 //
-// A view gives the unit code access to one node's packed matrix P (packed
-// element p = k*N + l) and to its links, with every index known at compile
-// time.  RegView loads the whole matrix into registers once (cheapest in
-// instructions when one thread computes many units of its node); LoadView
-// loads each element where a unit needs it (fewest instructions per unit when
-// many threads share a node).
+// A view gives the unit code everything it touches for one node n in one RK4
+// stage, with every index known at compile time:
+//   P<p>()        packed element p = k*N + l of the node's stage input
+//   Up<j>(), Dn<j>()  link handles of n + e_j, n - e_j (-1: no link)
+//   Nj<j>()       n_j
+//   G<p>(h)       packed element p of the linked node h's stage input
+//   Y<p>(), St<p>(v)  the node's y element, and the store of its stage output
+// Global views address the element-major arrays in device memory; shared
+// views address one thread-block cluster's distributed shared memory, where
+// each CTA holds a contiguous slice of the nodes and link handles are
+// shared::cluster addresses.  "Reg" views load the node's whole packed matrix
+// into registers once; "Load" views load each element where a unit uses it.
 
-template <int N, typename R>
-struct RegView {
-  R sg[N * N];
-  int up[N], dn[N];
-  R nj[N];
-  __device__ __forceinline__ RegView(const R* __restrict__ w, const int32_t* __restrict__ upt,
-                                     const int32_t* __restrict__ dnt, int Mp, int n) {
-#pragma unroll
-    for (int p = 0; p < N * N; ++p) sg[p] = w[p * Mp + n];
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      up[j] = upt[j * Mp + n];
-      const int d = dnt[j * Mp + n];
-      dn[j] = d < 0 ? -1 : (d & 0xFFFFFF);
-      nj[j] = d < 0 ? R(0) : R(d >> 24);
-    }
-  }
-  template <int p>
-  __device__ __forceinline__ R P() const { return sg[p]; }
-  template <int j>
-  __device__ __forceinline__ int Up() const { return up[j]; }
-  template <int j>
-  __device__ __forceinline__ int Dn() const { return dn[j]; }
-  template <int j>
-  __device__ __forceinline__ R Nj() const { return nj[j]; }
+template <typename R>
+struct GlobalArrays {
+  const R* __restrict__ win;
+  R* __restrict__ wout;
+  const R* __restrict__ y;
+  const int32_t* __restrict__ up;
+  const int32_t* __restrict__ dn;
+  int Mp;
 };
 
-template <int N, typename R>
-struct LoadView {
-  const R* __restrict__ w;
+template <int N, typename R, bool REG>
+struct GlobalView {
+  const R* __restrict__ win;  // column n of the input
+  const R* __restrict__ base;  // input, for gathers
+  R* __restrict__ wout;
+  const R* __restrict__ y;
   const int32_t* __restrict__ upt;
   const int32_t* __restrict__ dnt;
   int Mp;
-  __device__ __forceinline__ LoadView(const R* __restrict__ w_, const int32_t* __restrict__ upt_,
-                                      const int32_t* __restrict__ dnt_, int Mp_, int n)
-      : w(w_ + n), upt(upt_ + n), dnt(dnt_ + n), Mp(Mp_) {}
+  R sg[REG ? N * N : 1];
+  int upr[REG ? N : 1], dnr[REG ? N : 1];
+  __device__ __forceinline__ GlobalView(const GlobalArrays<R>& a, int n)
+      : win(a.win + n), base(a.win), wout(a.wout + n), y(a.y + n), upt(a.up + n), dnt(a.dn + n), Mp(a.Mp) {
+    if constexpr (REG) {
+#pragma unroll
+      for (int p = 0; p < N * N; ++p) sg[p] = win[p * Mp];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        upr[j] = upt[j * Mp];
+        dnr[j] = dnt[j * Mp];
+      }
+    }
+  }
   template <int p>
-  __device__ __forceinline__ R P() const { return w[p * Mp]; }
+  __device__ __forceinline__ R P() const {
+    if constexpr (REG) return sg[p];
+    else return win[p * Mp];
+  }
   template <int j>
-  __device__ __forceinline__ int Up() const { return upt[j * Mp]; }
+  __device__ __forceinline__ int Up() const {
+    if constexpr (REG) return upr[j];
+    else return upt[j * Mp];
+  }
+  template <int j>
+  __device__ __forceinline__ int DnRaw() const {
+    if constexpr (REG) return dnr[j];
+    else return dnt[j * Mp];
+  }
   template <int j>
   __device__ __forceinline__ int Dn() const {
-    const int d = dnt[j * Mp];
+    const int d = DnRaw<j>();
     return d < 0 ? -1 : (d & 0xFFFFFF);
   }
   template <int j>
   __device__ __forceinline__ R Nj() const {
-    const int d = dnt[j * Mp];
+    const int d = DnRaw<j>();
     return d < 0 ? R(0) : R(d >> 24);
   }
+  template <int p>
+  __device__ __forceinline__ R G(int h) const { return base[p * Mp + h]; }
+  template <int p>
+  __device__ __forceinline__ R Y() const { return y[p * Mp]; }
+  template <int p>
+  __device__ __forceinline__ void St(R v) const { wout[p * Mp] = v; }
+};
+
+__device__ __forceinline__ float ld_dsmem_f32(unsigned addr) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned map_to_rank(unsigned smem_addr, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory slice of one CTA: arrays [N*N][B] (floats), link tables
+// [N][B] of handles, n_j [N][B] (bytes), damping [B].  A handle is the
+// shared::cluster address of element (0, l) of the first array in the owning
+// CTA; element p of the array at byte offset o is at handle + o + 4*p*B,
+// because each CTA's shared memory is one contiguous range of the cluster
+// window and every CTA uses the same layout.
+struct SmemArrays {
+  const float* win;
+  float* wout;
+  const float* y;
+  const unsigned* up;
+  const unsigned* dn;
+  const unsigned char* nj;
+  const float* ngam;
+  unsigned win_off;  // byte offset of the stage input from the start of the dynamic shared memory
+  int B;
+};
+
+template <int N, bool REG>
+struct SmemView {
+  const float* win;
+  float* wout;
+  const float* y;
+  const unsigned* upt;
+  const unsigned* dnt;
+  const unsigned char* njt;
+  unsigned win_off;
+  int B;
+  float sg[REG ? N * N : 1];
+  __device__ __forceinline__ SmemView(const SmemArrays& a, int l)
+      : win(a.win + l), wout(a.wout + l), y(a.y + l), upt(a.up + l), dnt(a.dn + l), njt(a.nj + l),
+        win_off(a.win_off), B(a.B) {
+    if constexpr (REG) {
+#pragma unroll
+      for (int p = 0; p < N * N; ++p) sg[p] = win[p * B];
+    }
+  }
+  template <int p>
+  __device__ __forceinline__ float P() const {
+    if constexpr (REG) return sg[p];
+    else return win[p * B];
+  }
+  template <int j>
+  __device__ __forceinline__ int Up() const { return (int)upt[j * B]; }
+  template <int j>
+  __device__ __forceinline__ int Dn() const { return (int)dnt[j * B]; }
+  template <int j>
+  __device__ __forceinline__ float Nj() const { return (float)njt[j * B]; }
+  template <int p>
+  __device__ __forceinline__ float G(int h) const {
+    return ld_dsmem_f32((unsigned)h + win_off + (unsigned)(p * B * 4));
+  }
+  template <int p>
+  __device__ __forceinline__ float Y() const { return y[p * B]; }
+  template <int p>
+  __device__ __forceinline__ void St(float v) const { wout[p * B] = v; }
 };
 
 // S = Re sigma (symmetric), A = Im sigma (antisymmetric) from the packed view
@@ -266,20 +359,16 @@ __device__ __forceinline__ R Av(const V& v) {
 }
 
 template <typename R>
-struct StagePtrs {
-  const R* win;
-  R* wout;
-  const R* y;
-  double* out64;  // root output in double (mixed)
+struct StageCoef {
   R h;
   double hd;
+  double* out64;  // root output in double (mixed)
 };
 
 // Right-hand side of unit u (pair (a, b) or diagonal a) of one node.
 // Returns the real part in re and, for pairs, the imaginary part in im.
 template <int N, int u, typename R, bool CPLX, class V>
-__device__ __forceinline__ void unit_rhs(const V& v, const R* __restrict__ cf, const R* __restrict__ win, int Mp,
-                                         R ngam, bool term, R& re, R& im) {
+__device__ __forceinline__ void unit_rhs(const V& v, const R* __restrict__ cf, R ngam, bool term, R& re, R& im) {
   using L = CoefLayout<R>;
   constexpr int NP = N * (N - 1) / 2;
   re = R(0);
@@ -287,8 +376,9 @@ __device__ __forceinline__ void unit_rhs(const V& v, const R* __restrict__ cf, c
   if constexpr (u < NP) {
     constexpr int a = pair_a(N, u);
     constexpr int b = pair_b(N, u);
-    const R x = v.template P<a * N + b>();   // Re sigma_ab
-    const R yi = v.template P<b * N + a>();  // Im sigma_ab
+    constexpr int pab = a * N + b, pba = b * N + a;
+    const R x = v.template P<pab>();   // Re sigma_ab
+    const R yi = v.template P<pba>();  // Im sigma_ab
     // -i[J, sigma]: Re += [J, A]_ab, Im -= [J, S]_ab
     static_for<0, N>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
@@ -329,13 +419,13 @@ __device__ __forceinline__ void unit_rhs(const V& v, const R* __restrict__ cf, c
     // up-couplings i V_j^x sigma_{n+e_j}: j = a gives +i, j = b gives -i
     const int ua = v.template Up<a>();
     const int ub = v.template Up<b>();
-    if (ua >= 0) {
-      re -= win[(b * N + a) * Mp + ua];
-      im += win[(a * N + b) * Mp + ua];
+    if (ua != -1) {
+      re -= v.template G<pba>(ua);
+      im += v.template G<pab>(ua);
     }
-    if (ub >= 0) {
-      re += win[(b * N + a) * Mp + ub];
-      im -= win[(a * N + b) * Mp + ub];
+    if (ub != -1) {
+      re += v.template G<pba>(ub);
+      im -= v.template G<pab>(ub);
     }
     if (term) {
       // sigma_{n+e_j} ~ (n_j+1)/(ngam+gamma_j) theta_j sigma_n, then i V_j^x of it
@@ -347,23 +437,24 @@ __device__ __forceinline__ void unit_rhs(const V& v, const R* __restrict__ cf, c
     // down-couplings n_j theta_j sigma_{n-e_j}
     const int da = v.template Dn<a>();
     const int db = v.template Dn<b>();
-    if (da >= 0) {
+    if (da != -1) {
       const R n_a = v.template Nj<a>();
-      const R yr = win[(a * N + b) * Mp + da];
-      const R yy = win[(b * N + a) * Mp + da];
+      const R yr = v.template G<pab>(da);
+      const R yy = v.template G<pba>(da);
       re += n_a * (be_a * yr - al_a * yy);
       im += n_a * (al_a * yr + be_a * yy);
     }
-    if (db >= 0) {
+    if (db != -1) {
       const R n_b = v.template Nj<b>();
-      const R yr = win[(a * N + b) * Mp + db];
-      const R yy = win[(b * N + a) * Mp + db];
+      const R yr = v.template G<pab>(db);
+      const R yy = v.template G<pba>(db);
       re += n_b * (be_b * yr + al_b * yy);
       im += n_b * (be_b * yy - al_b * yr);
     }
   } else {
     constexpr int a = u - NP;
-    const R x = v.template P<a * N + a>();
+    constexpr int paa = a * N + a;
+    const R x = v.template P<paa>();
     static_for<0, N>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
       if constexpr (k != a) re += R(2) * cf[L::J(N) + a * N + k] * Av<N, k, a, V, R>(v);
@@ -376,60 +467,68 @@ __device__ __forceinline__ void unit_rhs(const V& v, const R* __restrict__ cf, c
     }
     re -= (ngam + R(2) * cf[L::ghalf(N) + a]) * x;
     const int da = v.template Dn<a>();
-    if (da >= 0) re += R(2) * v.template Nj<a>() * cf[L::beta(N) + a] * win[(a * N + a) * Mp + da];
+    if (da != -1) re += R(2) * v.template Nj<a>() * cf[L::beta(N) + a] * v.template G<paa>(da);
   }
 }
 
-// All units of node n that belong to the unit mask, one RK4 stage.
+// eta and loss: the extra rows of the augmented RK4 system, updated at the
+// last stage from the root's stage input x_mm; written to the outputs at
+// output steps.
+// Output steps are tracked with a counter (no 64-bit division in the loop):
+// ostep.now is true at steps whose end is an output row, ostep.row is that row.
+struct OutStep {
+  bool now;
+  int64_t row;
+};
+
+__device__ __forceinline__ void eta_update(const Inst& I, double e, double l, OutStep os) {
+  I.acc[0] += I.dt * e;
+  I.acc[1] += I.dt * l;
+  if (I.out_el && os.now) {
+    I.out_el[2 * os.row] = I.acc[0];
+    I.out_el[2 * os.row + 1] = I.acc[1];
+  }
+}
+
+// All units of one node that belong to the unit mask, one RK4 stage.
 template <int N, typename R, bool MIXED, bool CPLX, class V>
 __device__ __forceinline__ void node_units(const Inst& I, const R* __restrict__ cf, const double* __restrict__ cfd,
-                                           const StagePtrs<R>& P, const V& v, int s, int n, uint64_t umask,
-                                           int64_t step_done) {
+                                           const StageCoef<R>& P, const V& v, R ngam, int s, bool root,
+                                           uint64_t umask, OutStep os) {
   constexpr int NP = N * (N - 1) / 2;
   constexpr int U = NP + N;
-  const int Mp = I.Mpad;
-  const R* __restrict__ win = P.win;
-  R* __restrict__ wout = P.wout;
-  const R* __restrict__ yv = P.y;
-  const R ngam = static_cast<const R*>(I.ngam)[n];
-  const bool term = I.terminator && (v.template Up<0>() < 0);
-  const bool out_row = (s == 3) && (n == 0) && I.out_pops && ((step_done + 1) % I.out_every) == 0;
+  const bool term = I.terminator && (v.template Up<0>() == -1);
+  const bool out_row = (s == 3) && root && I.out_pops && os.now;
 
   // eta and loss (plain FP64 path; the mixed path does this in root_task)
-  if (!MIXED && s == 3 && n == 0 && (umask & 1ull)) {
+  if (!MIXED && s == 3 && root && (umask & 1ull)) {
     double e = 0.0, l = 0.0;
-#pragma unroll
-    for (int m = 0; m < N; ++m) {
-      const double x = (double)win[(m * N + m) * Mp];
+    static_for<0, N>([&](auto mc) {
+      constexpr int m = decltype(mc)::value;
+      const double x = (double)v.template P<m * N + m>();
       e += cfd[m] * x;
       l += cfd[N + m] * x;
-    }
-    I.acc[0] += I.dt * e;
-    I.acc[1] += I.dt * l;
-    if (I.out_el && ((step_done + 1) % I.out_every) == 0) {
-      const int64_t o = (step_done + 1) / I.out_every;
-      I.out_el[2 * o] = I.acc[0];
-      I.out_el[2 * o + 1] = I.acc[1];
-    }
+    });
+    eta_update(I, e, l, os);
   }
 
   static_for<0, U>([&](auto uc) {
     constexpr int u = decltype(uc)::value;
     if (!((umask >> u) & 1ull)) return;
     R re, im;
-    unit_rhs<N, u, R, CPLX>(v, cf, win, Mp, ngam, term, re, im);
+    unit_rhs<N, u, R, CPLX>(v, cf, ngam, term, re, im);
     if constexpr (u < NP) {
       constexpr int a = pair_a(N, u);
       constexpr int b = pair_b(N, u);
       constexpr int pr = a * N + b, pi = b * N + a;
-      wout[pr * Mp + n] = yv[pr * Mp + n] + P.h * re;
-      wout[pi * Mp + n] = yv[pi * Mp + n] + P.h * im;
+      v.template St<pr>(v.template Y<pr>() + P.h * re);
+      v.template St<pi>(v.template Y<pi>() + P.h * im);
     } else {
       constexpr int a = u - NP;
       constexpr int pd = a * N + a;
-      const R val = yv[pd * Mp + n] + P.h * re;
-      wout[pd * Mp + n] = val;
-      if (out_row) I.out_pops[((step_done + 1) / I.out_every) * N + a] = (double)val;
+      const R val = v.template Y<pd>() + P.h * re;
+      v.template St<pd>(val);
+      if (out_row) I.out_pops[os.row * N + a] = (double)val;
     }
   });
 }
@@ -437,18 +536,17 @@ __device__ __forceinline__ void node_units(const Inst& I, const R* __restrict__ 
 // Mixed precision: the root node (rho itself) is computed by one warp, one
 // unit per lane, and accumulated in double with all lanes active (FP64 runs
 // at 1/64 of the FP32 rate here, so it must not serialise on one lane).
-template <int N, bool CPLX>
+// own(p) reads the root's float stage input, up(j) gives the link handle of
+// e_j, gather(h, p) element p of a linked node, store(p, v) the float copy of
+// the root's stage output.
+template <int N, bool CPLX, class Own, class UpH, class Gather, class Store>
 __device__ __forceinline__ void root_task(const Inst& I, const float* __restrict__ cf, const double* __restrict__ cfd,
-                                          const StagePtrs<float>& P, int s, int lane, int64_t step_done) {
+                                          const StageCoef<float>& P, int s, int lane, OutStep os, Own own,
+                                          UpH up, Gather gather, Store store) {
   using L = CoefLayout<float>;
   constexpr int NP = N * (N - 1) / 2;
   constexpr int U = NP + N;
-  const int Mp = I.Mpad;
-  const float* __restrict__ win = P.win;  // float copy of the root sits at column 0
-  const bool out_step = ((step_done + 1) % I.out_every) == 0;
   if (s == 3) {
-    // eta and loss: the extra rows of the augmented RK4 system, from the
-    // stage-3 input of the root (in double)
     double e = 0.0, l = 0.0;
     if (lane < N) {
       const double x = I.w0a[lane * N + lane];
@@ -460,20 +558,11 @@ __device__ __forceinline__ void root_task(const Inst& I, const float* __restrict
       e += __shfl_down_sync(0xffffffffu, e, off);
       l += __shfl_down_sync(0xffffffffu, l, off);
     }
-    if (lane == 0) {
-      I.acc[0] += I.dt * e;
-      I.acc[1] += I.dt * l;
-      if (I.out_el && out_step) {
-        const int64_t o = (step_done + 1) / I.out_every;
-        I.out_el[2 * o] = I.acc[0];
-        I.out_el[2 * o + 1] = I.acc[1];
-      }
-    }
+    if (lane == 0) eta_update(I, e, l, os);
   }
-  auto Pk = [&](int k, int l) -> float { return win[(k * N + l) * Mp]; };
-  auto S = [&](int k, int l) -> float { return k <= l ? Pk(k, l) : Pk(l, k); };
-  auto A = [&](int k, int l) -> float { return k < l ? Pk(l, k) : (k > l ? -Pk(k, l) : 0.f); };
-  const bool term = I.terminator && I.up[0] < 0;  // depth 0: the root is the last level
+  auto S = [&](int k, int l) -> float { return k <= l ? own(k * N + l) : own(l * N + k); };
+  auto A = [&](int k, int l) -> float { return k < l ? own(l * N + k) : (k > l ? -own(k * N + l) : 0.f); };
+  const bool term = I.terminator && up(0) == -1;  // depth 0: the root is the last level
   for (int uu = lane; uu < U; uu += 32) {
     float re = 0.f, im = 0.f;
     int a, b;
@@ -482,7 +571,7 @@ __device__ __forceinline__ void root_task(const Inst& I, const float* __restrict
       a = 0;
       while (r >= N - 1 - a) { r -= N - 1 - a; ++a; }
       b = a + 1 + r;
-      const float x = Pk(a, b), yi = Pk(b, a);
+      const float x = own(a * N + b), yi = own(b * N + a);
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         if (k != a) {
@@ -512,14 +601,14 @@ __device__ __forceinline__ void root_task(const Inst& I, const float* __restrict
       const float c = cf[L::ghalf(N) + a] + cf[L::ghalf(N) + b];
       re += d * yi - c * x;
       im -= d * x + c * yi;
-      const int ua = I.up[a * Mp], ub = I.up[b * Mp];
-      if (ua >= 0) {
-        re -= win[(b * N + a) * Mp + ua];
-        im += win[(a * N + b) * Mp + ua];
+      const int ua = up(a), ub = up(b);
+      if (ua != -1) {
+        re -= gather(ua, b * N + a);
+        im += gather(ua, a * N + b);
       }
-      if (ub >= 0) {
-        re += win[(b * N + a) * Mp + ub];
-        im -= win[(a * N + b) * Mp + ub];
+      if (ub != -1) {
+        re += gather(ub, b * N + a);
+        im -= gather(ub, a * N + b);
       }
       if (term) {
         const float al_a = cf[L::alpha(N) + a], be_a = cf[L::beta(N) + a];
@@ -531,7 +620,7 @@ __device__ __forceinline__ void root_task(const Inst& I, const float* __restrict
       }
     } else {
       a = b = uu - NP;
-      const float x = Pk(a, a);
+      const float x = own(a * N + a);
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         if (k != a) {
@@ -545,14 +634,14 @@ __device__ __forceinline__ void root_task(const Inst& I, const float* __restrict
     const int pr = a * N + b;
     const double vr = I.y0[pr] + P.hd * (double)re;
     P.out64[pr] = vr;
-    P.wout[pr * Mp] = (float)vr;
+    store(pr, (float)vr);
     if (a != b) {
       const int pi = b * N + a;
       const double vi = I.y0[pi] + P.hd * (double)im;
       P.out64[pi] = vi;
-      P.wout[pi * Mp] = (float)vi;
-    } else if (s == 3 && I.out_pops && out_step) {
-      I.out_pops[((step_done + 1) / I.out_every) * N + a] = vr;
+      store(pi, (float)vi);
+    } else if (s == 3 && I.out_pops && os.now) {
+      I.out_pops[os.row * N + a] = vr;
     }
   }
 }
@@ -568,6 +657,32 @@ __device__ __forceinline__ void write_row0(const Inst& I) {
     I.out_el[1] = I.acc[1];
   }
 }
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <typename R>
+__device__ __forceinline__ void load_instance(const EngineArgs& A, int li, Inst& s_inst, unsigned char* s_coef) {
+  __syncthreads();
+  if (threadIdx.x == 0) s_inst = A.insts[A.team_list[li]];
+  __syncthreads();
+  const int nb = CoefLayout<R>::bytes(s_inst.N);
+  const unsigned char* src = static_cast<const unsigned char*>(s_inst.coef);
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s_coef[i] = src[i];
+  __syncthreads();
+}
+
+__device__ __forceinline__ void stage_select(int s, double dt, double& hd, int& in_sel, int& out_sel) {
+  // Horner RK4: 0: wa = y + h/4 L y; 1: wb = y + h/3 L wa; 2: wa = y + h/2 L wb; 3: y = y + h L wa
+  // selectors: 0 = y, 1 = wa, 2 = wb
+  if (s == 0) { hd = 0.25 * dt; in_sel = 0; out_sel = 1; }
+  else if (s == 1) { hd = dt / 3.0; in_sel = 1; out_sel = 2; }
+  else if (s == 2) { hd = 0.5 * dt; in_sel = 2; out_sel = 1; }
+  else { hd = dt; in_sel = 1; out_sel = 0; }
+}
+
+// ------------------------------------------------------ global-memory engine
 
 template <int N, typename R, bool MIXED, bool CPLX, bool REG>
 __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) heom_engine_kernel(EngineArgs A) {
@@ -600,60 +715,434 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) heom_engine_kernel
   unsigned epoch = 0;
 
   for (int li = A.team_first[team]; li < A.team_first[team + 1]; ++li) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_inst = A.insts[A.team_list[li]];
-    __syncthreads();
-    {
-      const int nb = CoefLayout<R>::bytes(N);
-      const unsigned char* src = static_cast<const unsigned char*>(s_inst.coef);
-      for (int i = threadIdx.x; i < nb; i += blockDim.x) s_coef[i] = src[i];
-    }
-    __syncthreads();
+    load_instance<R>(A, li, s_inst, s_coef);
     const Inst& I = s_inst;
     const R* cf = reinterpret_cast<const R*>(s_coef);
     const double* cfd = reinterpret_cast<const double*>(s_coef + CoefLayout<R>::dbl_offset(N));
+    const R* ngam = static_cast<const R*>(I.ngam);
     const int nblk = (I.M + 31) >> 5;
     const int items = nblk * G;
     const int nitems = items + (MIXED ? 1 : 0);  // the mixed path adds one root task
 
     if (warp == 0 && lane == 0) write_row0<N, R, MIXED>(I);
 
-    R* y = static_cast<R*>(I.y);
-    R* wa = static_cast<R*>(I.wa);
-    R* wb = static_cast<R*>(I.wb);
-    const double dt = I.dt;
+    R* arr[3] = {static_cast<R*>(I.y), static_cast<R*>(I.wa), static_cast<R*>(I.wb)};
+    double* arr64[3] = {I.y0, I.w0a, I.w0b};
+    int64_t next_out = I.out_every, orow = 1;
     for (int64_t t = 0; t < I.nsteps; ++t) {
+      const OutStep os{t + 1 == next_out, orow};
+      if (os.now) {
+        next_out += I.out_every;
+        ++orow;
+      }
 #pragma unroll 1
       for (int s = 0; s < 4; ++s) {
-        StagePtrs<R> P;
-        P.y = y;
-        if (s == 0) { P.win = y;  P.wout = wa; P.out64 = I.w0a; P.hd = 0.25 * dt; }
-        else if (s == 1) { P.win = wa; P.wout = wb; P.out64 = I.w0b; P.hd = dt / 3.0; }
-        else if (s == 2) { P.win = wb; P.wout = wa; P.out64 = I.w0a; P.hd = 0.5 * dt; }
-        else { P.win = wa; P.wout = y;  P.out64 = I.y0; P.hd = dt; }
+        StageCoef<R> P;
+        int in_sel, out_sel;
+        stage_select(s, I.dt, P.hd, in_sel, out_sel);
         P.h = (R)P.hd;
+        P.out64 = arr64[out_sel];
+        GlobalArrays<R> ga{arr[in_sel], arr[out_sel], arr[0], I.up, I.dn, I.Mpad};
         for (int it = warp; it < nitems; it += W) {
           if (MIXED && it == items) {
-            if constexpr (MIXED) root_task<N, CPLX>(I, cf, cfd, P, s, lane, t);
+            if constexpr (MIXED) {
+              const int Mp = I.Mpad;
+              const float* win = reinterpret_cast<const float*>(ga.win);
+              float* wout = reinterpret_cast<float*>(ga.wout);
+              root_task<N, CPLX>(
+                  I, reinterpret_cast<const float*>(cf), cfd, reinterpret_cast<const StageCoef<float>&>(P), s, lane,
+                  os, [&](int p) { return win[p * Mp]; }, [&](int j) { return (int)I.up[j * Mp]; },
+                  [&](int h, int p) { return win[p * Mp + h]; }, [&](int p, float v) { wout[p * Mp] = v; });
+            }
             continue;
           }
           const int nb = it / G;
           const int g = it - nb * G;
           const int n = (nb << 5) + lane;
           if (n >= I.M || (MIXED && n == 0)) continue;
-          const uint64_t um = s_umask[g];
-          if constexpr (REG) {
-            const RegView<N, R> v(P.win, I.up, I.dn, I.Mpad, n);
-            node_units<N, R, MIXED, CPLX>(I, cf, cfd, P, v, s, n, um, t);
-          } else {
-            const LoadView<N, R> v(P.win, I.up, I.dn, I.Mpad, n);
-            node_units<N, R, MIXED, CPLX>(I, cf, cfd, P, v, s, n, um, t);
+          const GlobalView<N, R, REG> v(ga, n);
+          node_units<N, R, MIXED, CPLX>(I, cf, cfd, P, v, ngam[n], s, n == 0, s_umask[g], os);
+        }
+        if (!team_barrier(A, epoch)) return;
+      }
+    }
+  }
+}
+
+// ------------------------------------------- distributed-shared-memory engine
+//
+// Mixed precision only.  One thread-block cluster of C CTAs holds a whole
+// hierarchy in its distributed shared memory: CTA r owns nodes
+// [r*B, r*B + B) and keeps y, wa and wb of those nodes, their link handles,
+// n_j and damping in its own shared memory.  Own elements are read from local
+// shared memory, neighbours with ld.shared::cluster; the stage barrier is the
+// hardware cluster barrier, whose release/acquire orders the shared-memory
+// writes of one stage before the reads of the next.  y is copied in from and
+// back to device memory once per call.
+
+// Dynamic shared memory of one CTA for a slice of B nodes.
+__host__ __device__ constexpr int smem_dyn_bytes(int N, int B) {
+  return (3 * N * N + 2 * N + 1) * 4 * B + N * B;
+}
+
+template <int N, bool CPLX, bool REG>
+__global__ void __launch_bounds__(512) heom_smem_kernel(EngineArgs A, int B) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ __align__(16) unsigned char s_coef[CoefLayout<float>::bytes(kMaxSmallN) + 64];
+  __shared__ Inst s_inst;
+  __shared__ uint64_t s_umask[32];
+  constexpr int U = N * (N - 1) / 2 + N;
+  constexpr int NN = N * N;
+
+  unsigned rank, C;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(C));
+  const int team = blockIdx.x / C;
+  const int wpc = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int G = A.G;
+  if (threadIdx.x < 32) {
+    uint64_t m = 0;
+    for (int u = 0; u < U; ++u)
+      if (u % G == (int)threadIdx.x) m |= 1ull << u;
+    s_umask[threadIdx.x] = m;
+  }
+  float* sy = reinterpret_cast<float*>(dsm);
+  float* swa = sy + NN * B;
+  float* swb = swa + NN * B;
+  unsigned* sup = reinterpret_cast<unsigned*>(swb + NN * B);
+  unsigned* sdn = sup + N * B;
+  float* sng = reinterpret_cast<float*>(sdn + N * B);
+  unsigned char* snj = reinterpret_cast<unsigned char*>(sng + B);
+  float* arr[3] = {sy, swa, swb};
+  const unsigned base = smem_u32(dsm);
+
+  for (int li = A.team_first[team]; li < A.team_first[team + 1]; ++li) {
+    load_instance<float>(A, li, s_inst, s_coef);
+    const Inst& I = s_inst;
+    const float* cf = reinterpret_cast<const float*>(s_coef);
+    const double* cfd = reinterpret_cast<const double*>(s_coef + CoefLayout<float>::dbl_offset(N));
+    const int Mp = I.Mpad;
+    const int n0 = (int)rank * B;
+    const int nloc = max(0, min(B, I.M - n0));
+    // fill this CTA's slice
+    const float* gy = static_cast<const float*>(I.y);
+    for (int idx = threadIdx.x; idx < NN * B; idx += blockDim.x) {
+      const int p = idx / B, l = idx - (idx / B) * B;
+      sy[idx] = l < nloc ? gy[p * Mp + n0 + l] : 0.f;
+    }
+    for (int idx = threadIdx.x; idx < N * B; idx += blockDim.x) {
+      const int j = idx / B, l = idx - (idx / B) * B;
+      unsigned hu = 0xFFFFFFFFu, hd = 0xFFFFFFFFu;
+      unsigned char nj = 0;
+      if (l < nloc) {
+        const int m = I.up[j * Mp + n0 + l];
+        if (m >= 0) hu = map_to_rank(base + (unsigned)(m % B) * 4u, (unsigned)(m / B));
+        const int d = I.dn[j * Mp + n0 + l];
+        if (d >= 0) {
+          const int md = d & 0xFFFFFF;
+          hd = map_to_rank(base + (unsigned)(md % B) * 4u, (unsigned)(md / B));
+          nj = (unsigned char)(d >> 24);
+        }
+      }
+      sup[idx] = hu;
+      sdn[idx] = hd;
+      snj[idx] = nj;
+    }
+    for (int l = threadIdx.x; l < B; l += blockDim.x)
+      sng[l] = l < nloc ? static_cast<const float*>(I.ngam)[n0 + l] : 0.f;
+    if (rank == 0 && threadIdx.x == 0) write_row0<N, float, true>(I);
+    cluster_sync_all();
+
+    const int nblk = (nloc + 31) >> 5;
+    const int items = nblk * G;
+    const int nitems = items + (rank == 0 ? 1 : 0);  // rank 0 also runs the root task
+    double* arr64[3] = {I.y0, I.w0a, I.w0b};
+    int64_t next_out = I.out_every, orow = 1;
+    for (int64_t t = 0; t < I.nsteps; ++t) {
+      const OutStep os{t + 1 == next_out, orow};
+      if (os.now) {
+        next_out += I.out_every;
+        ++orow;
+      }
+#pragma unroll 1
+      for (int s = 0; s < 4; ++s) {
+        StageCoef<float> P;
+        int in_sel, out_sel;
+        stage_select(s, I.dt, P.hd, in_sel, out_sel);
+        P.h = (float)P.hd;
+        P.out64 = arr64[out_sel];
+        SmemArrays sa{arr[in_sel], arr[out_sel], sy, sup, sdn, snj, sng,
+                      (unsigned)(in_sel * NN * B * 4), B};
+        for (int it = warp; it < nitems; it += wpc) {
+          if (it == items) {
+            const float* win = sa.win;
+            float* wout = sa.wout;
+            const unsigned woff = sa.win_off;
+            root_task<N, CPLX>(
+                I, cf, cfd, P, s, lane, os, [&](int p) { return win[p * B]; }, [&](int j) { return (int)sup[j * B]; },
+                [&](int h, int p) { return ld_dsmem_f32((unsigned)h + woff + (unsigned)(p * B * 4)); },
+                [&](int p, float v) { wout[p * B] = v; });
+            continue;
+          }
+          const int nb = it / G;
+          const int g = it - nb * G;
+          const int l = (nb << 5) + lane;
+          if (l >= nloc || (rank == 0 && l == 0)) continue;
+          const SmemView<N, REG> v(sa, l);
+          node_units<N, float, true, CPLX>(I, cf, cfd, P, v, sng[l], s, false, s_umask[g], os);
+        }
+        cluster_sync_all();
+      }
+    }
+    // write the slice of y back
+    float* gyw = static_cast<float*>(I.y);
+    for (int idx = threadIdx.x; idx < NN * B; idx += blockDim.x) {
+      const int p = idx / B, l = idx - (idx / B) * B;
+      if (l < nloc) gyw[p * Mp + n0 + l] = sy[idx];
+    }
+    cluster_sync_all();  // no CTA reuses or leaves its slice while others may still read it
+  }
+}
+
+}  // namespace heom
+
+namespace heom {
+
+// ------------------------------------------------------------ large-N engine
+//
+// Hierarchies with 9..24 sites (N is a run-time argument).  A CTA stages a
+// tile of 32 consecutive nodes' packed matrices in shared memory (element-
+// major, one lane per node, so every access is bank-conflict free); warp w
+// then computes the units u = w, w + nwarps, ... of all 32 nodes, reading the
+// node's own elements from shared memory and its neighbours' from device
+// memory.  Teams and barriers are those of the small-N engine.
+
+struct LargeUnit {
+  unsigned char a, b;
+};
+
+template <typename R, bool MIXED, bool CPLX>
+__global__ void __launch_bounds__(256) heom_large_kernel(EngineArgs A) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ Inst s_inst;
+  __shared__ LargeUnit s_units[kMaxSites * (kMaxSites + 1) / 2];
+
+  int team, rank, team_size;
+  if (A.mode == 0) {
+    team = blockIdx.x / A.team_ctas;
+    rank = blockIdx.x - team * A.team_ctas;
+    team_size = A.team_ctas;
+  } else {
+    team = 0;
+    rank = blockIdx.x;
+    team_size = gridDim.x;
+  }
+  const int nwarps = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  unsigned epoch = 0;
+
+  for (int li = A.team_first[team]; li < A.team_first[team + 1]; ++li) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_inst = A.insts[A.team_list[li]];
+    __syncthreads();
+    const Inst& I = s_inst;
+    const int N = I.N;
+    const int NN = N * N;
+    const int NP = N * (N - 1) / 2;
+    const int U = NP + N;
+    using L = CoefLayout<R>;
+    // shared memory: tile [NN][32] | coefficients
+    R* tile = reinterpret_cast<R*>(dsm);
+    unsigned char* cbytes = dsm + (size_t)NN * 32 * sizeof(R);
+    const int cb = L::bytes(N);
+    for (int i = threadIdx.x; i < cb; i += blockDim.x) cbytes[i] = static_cast<const unsigned char*>(I.coef)[i];
+    for (int u = threadIdx.x; u < U; u += blockDim.x) {
+      int a, b;
+      if (u < NP) {
+        int r = u;
+        a = 0;
+        while (r >= N - 1 - a) { r -= N - 1 - a; ++a; }
+        b = a + 1 + r;
+      } else {
+        a = b = u - NP;
+      }
+      s_units[u].a = (unsigned char)a;
+      s_units[u].b = (unsigned char)b;
+    }
+    __syncthreads();
+    const R* cf = reinterpret_cast<const R*>(cbytes);
+    const double* cfd = reinterpret_cast<const double*>(cbytes + L::dbl_offset(N));
+    const R* ngam = static_cast<const R*>(I.ngam);
+    const int Mp = I.Mpad;
+    const int ntiles = (I.M + 31) >> 5;
+    if (rank == 0 && threadIdx.x == 0) {
+      if (I.out_pops)
+        for (int a = 0; a < N; ++a)
+          I.out_pops[a] = MIXED ? I.y0[a * N + a] : (double)static_cast<const R*>(I.y)[(a * N + a) * Mp];
+      if (I.out_el) {
+        I.out_el[0] = I.acc[0];
+        I.out_el[1] = I.acc[1];
+      }
+    }
+    R* arr[3] = {static_cast<R*>(I.y), static_cast<R*>(I.wa), static_cast<R*>(I.wb)};
+    double* arr64[3] = {I.y0, I.w0a, I.w0b};
+    int64_t next_out = I.out_every, orow = 1;
+    for (int64_t t = 0; t < I.nsteps; ++t) {
+      const OutStep os{t + 1 == next_out, orow};
+      if (os.now) {
+        next_out += I.out_every;
+        ++orow;
+      }
+      const bool out_step = os.now;
+#pragma unroll 1
+      for (int s = 0; s < 4; ++s) {
+        double hd;
+        int in_sel, out_sel;
+        stage_select(s, I.dt, hd, in_sel, out_sel);
+        const R h = (R)hd;
+        const R* __restrict__ win = arr[in_sel];
+        R* __restrict__ wout = arr[out_sel];
+        const R* __restrict__ yv = arr[0];
+        double* out64 = arr64[out_sel];
+        for (int tl = rank; tl < ntiles; tl += team_size) {
+          const int n0 = tl << 5;
+          __syncthreads();
+          for (int i = threadIdx.x; i < NN * 32; i += blockDim.x) {
+            const int p = i >> 5, l = i & 31;
+            tile[i] = (n0 + l < I.M) ? win[p * Mp + n0 + l] : R(0);
+          }
+          __syncthreads();
+          const int n = n0 + lane;
+          const bool live = n < I.M;
+          const bool root = (n == 0);
+          int upa = -1, upb = -1;
+          const R ng = live ? ngam[n] : R(0);
+          const bool term = live && I.terminator && I.up[n] < 0;
+          if (!MIXED && s == 3 && root && warp == 0) {
+            double e = 0.0, l = 0.0;
+            for (int m = 0; m < N; ++m) {
+              const double x = (double)tile[(m * N + m) * 32];
+              e += cfd[m] * x;
+              l += cfd[N + m] * x;
+            }
+            eta_update(I, e, l, os);
+          }
+          if (MIXED && s == 3 && root && warp == 0) {
+            double e = 0.0, l = 0.0;
+            for (int m = 0; m < N; ++m) {
+              const double x = I.w0a[m * N + m];
+              e += cfd[m] * x;
+              l += cfd[N + m] * x;
+            }
+            eta_update(I, e, l, os);
+          }
+          auto P = [&](int k, int l) -> R { return tile[(k * N + l) * 32 + lane]; };
+          auto S = [&](int k, int l) -> R { return k <= l ? P(k, l) : P(l, k); };
+          auto Aim = [&](int k, int l) -> R { return k < l ? P(l, k) : (k > l ? -P(k, l) : R(0)); };
+          for (int u = warp; u < U && live; u += nwarps) {
+            const int a = s_units[u].a, b = s_units[u].b;
+            R re = R(0), im = R(0);
+            const int da_raw = I.dn[a * Mp + n];
+            const int da = da_raw < 0 ? -1 : (da_raw & 0xFFFFFF);
+            const R na = da_raw < 0 ? R(0) : R(da_raw >> 24);
+            if (a != b) {
+              const R x = P(a, b), yi = P(b, a);
+              for (int k = 0; k < N; ++k) {
+                const R jak = cf[L::J(N) + a * N + k];
+                const R jkb = cf[L::J(N) + k * N + b];
+                re += jak * Aim(k, b) - Aim(a, k) * jkb;
+                im += S(a, k) * jkb - jak * S(k, b);
+                if (CPLX) {
+                  const R iak = cf[L::Ji(N) + a * N + k];
+                  const R ikb = cf[L::Ji(N) + k * N + b];
+                  re += iak * S(k, b) - S(a, k) * ikb;
+                  im += iak * Aim(k, b) - Aim(a, k) * ikb;
+                }
+              }
+              const R d = cf[L::eps(N) + a] - cf[L::eps(N) + b];
+              const R c = ng + cf[L::ghalf(N) + a] + cf[L::ghalf(N) + b];
+              re += d * yi - c * x;
+              im -= d * x + c * yi;
+              const R al_a = cf[L::alpha(N) + a], be_a = cf[L::beta(N) + a];
+              const R al_b = cf[L::alpha(N) + b], be_b = cf[L::beta(N) + b];
+              upa = I.up[a * Mp + n];
+              upb = I.up[b * Mp + n];
+              if (upa >= 0) {
+                re -= win[(b * N + a) * Mp + upa];
+                im += win[(a * N + b) * Mp + upa];
+              }
+              if (upb >= 0) {
+                re += win[(b * N + a) * Mp + upb];
+                im -= win[(a * N + b) * Mp + upb];
+              }
+              if (term) {
+                const R ca = (na + R(1)) / (ng + cf[L::gam(N) + a]);
+                const int db_raw0 = I.dn[b * Mp + n];
+                const R nb0 = db_raw0 < 0 ? R(0) : R(db_raw0 >> 24);
+                const R cbf = (nb0 + R(1)) / (ng + cf[L::gam(N) + b]);
+                re += ca * (-al_a * x - be_a * yi) + cbf * (-al_b * x + be_b * yi);
+                im += ca * (-al_a * yi + be_a * x) + cbf * (-al_b * yi - be_b * x);
+              }
+              if (da >= 0) {
+                const R yr = win[(a * N + b) * Mp + da];
+                const R yy = win[(b * N + a) * Mp + da];
+                re += na * (be_a * yr - al_a * yy);
+                im += na * (al_a * yr + be_a * yy);
+              }
+              const int db_raw = I.dn[b * Mp + n];
+              if (db_raw >= 0) {
+                const int db = db_raw & 0xFFFFFF;
+                const R nb = R(db_raw >> 24);
+                const R yr = win[(a * N + b) * Mp + db];
+                const R yy = win[(b * N + a) * Mp + db];
+                re += nb * (be_b * yr + al_b * yy);
+                im += nb * (be_b * yy - al_b * yr);
+              }
+            } else {
+              const R x = P(a, a);
+              for (int k = 0; k < N; ++k) {
+                if (k == a) continue;
+                re += R(2) * cf[L::J(N) + a * N + k] * Aim(k, a);
+                if (CPLX) re += R(2) * cf[L::Ji(N) + a * N + k] * S(k, a);
+              }
+              re -= (ng + R(2) * cf[L::ghalf(N) + a]) * x;
+              if (da >= 0) re += R(2) * na * cf[L::beta(N) + a] * win[(a * N + a) * Mp + da];
+            }
+            // Horner update w = y + h r (root in double for mixed precision)
+            const int pr = a * N + b, pi = b * N + a;
+            if (MIXED && root) {
+              const double vr = I.y0[pr] + hd * (double)re;
+              out64[pr] = vr;
+              wout[pr * Mp] = (R)vr;
+              if (a != b) {
+                const double vi = I.y0[pi] + hd * (double)im;
+                out64[pi] = vi;
+                wout[pi * Mp] = (R)vi;
+              } else if (s == 3 && I.out_pops && out_step) {
+                I.out_pops[os.row * N + a] = vr;
+              }
+            } else {
+              const R vr = yv[pr * Mp + n] + h * re;
+              wout[pr * Mp + n] = vr;
+              if (a != b) {
+                wout[pi * Mp + n] = yv[pi * Mp + n] + h * im;
+              } else if (root && s == 3 && I.out_pops && out_step) {
+                I.out_pops[os.row * N + a] = (double)vr;
+              }
+            }
           }
         }
         if (!team_barrier(A, epoch)) return;
       }
     }
   }
+}
+
+__host__ __device__ constexpr int large_smem_bytes(int N, int rsize) {
+  return N * N * 32 * rsize + ((2 * N * N + 5 * N) * rsize + 7) / 8 * 8 + 2 * N * 8;
 }
 
 }  // namespace heom

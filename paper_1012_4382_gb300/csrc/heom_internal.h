@@ -12,6 +12,14 @@ const void* engine_kernel_f64_real(int N, bool reg);
 const void* engine_kernel_f64_cplx(int N, bool reg);
 const void* engine_kernel_f32_real(int N, bool reg);
 const void* engine_kernel_f32_cplx(int N, bool reg);
+// Large-N engine (9..24 sites).
+const void* large_kernel(bool fp64, bool cplx);
+// Distributed-shared-memory engine (mixed precision only).
+const void* smem_kernel_f32_real(int N, bool reg);
+const void* smem_kernel_f32_cplx(int N, bool reg);
+inline const void* smem_kernel(bool cplx, bool reg, int N) {
+  return cplx ? smem_kernel_f32_cplx(N, reg) : smem_kernel_f32_real(N, reg);
+}
 inline const void* engine_kernel(bool fp64, bool cplx, bool reg, int N) {
   if (fp64) return cplx ? engine_kernel_f64_cplx(N, reg) : engine_kernel_f64_real(N, reg);
   return cplx ? engine_kernel_f32_cplx(N, reg) : engine_kernel_f32_real(N, reg);

@@ -27,4 +27,5 @@ const void* engine_kernel_f32_cplx(int N, bool reg) {
   }
 }
 
+
 }  // namespace heom

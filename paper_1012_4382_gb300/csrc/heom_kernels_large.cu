@@ -1,0 +1,13 @@
+// Instantiations of the large-N (9..24 sites) engine kernel.
+#include "heom_engine.cuh"
+#include "heom_internal.h"
+
+namespace heom {
+
+const void* large_kernel(bool fp64, bool cplx) {
+  if (fp64) return cplx ? (const void*)heom_large_kernel<double, false, true>
+                        : (const void*)heom_large_kernel<double, false, false>;
+  return cplx ? (const void*)heom_large_kernel<float, true, true> : (const void*)heom_large_kernel<float, true, false>;
+}
+
+}  // namespace heom

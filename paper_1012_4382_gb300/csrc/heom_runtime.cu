@@ -237,7 +237,7 @@ struct Instance {
 };
 
 struct LaunchCfg {
-  int mode = 0;       // 0: cluster teams, 1: whole grid
+  int mode = 0;       // 0: cluster teams on device memory, 1: whole grid, 2: cluster teams on shared memory
   int team_ctas = 1;
   int block = 256;
   int G = 1;
@@ -329,8 +329,6 @@ int validate(const heom_params* p, int idx) {
     if (p->recomb_rate && (!(p->recomb_rate[a] >= 0.0) || !std::isfinite(p->recomb_rate[a])))
       return fail(HEOM_EINVAL, "params[%d]: recomb_rate[%d] must be finite and >= 0", idx, a);
   }
-  if (N > heom::kMaxSmallN)
-    return fail(HEOM_EUNSUPPORTED, "params[%d]: N=%d > %d sites needs the large-N engine", idx, N, heom::kMaxSmallN);
   return HEOM_OK;
 }
 
@@ -428,6 +426,17 @@ struct Engine {
     int64_t Mmax = 0;
     for (auto& in : inst)
       if (in->N == N) Mmax = std::max<int64_t>(Mmax, in->M);
+    if (N > heom::kMaxSmallN) {
+      c.block = 256;
+      c.G = 1;
+      if (count == 1 && Mmax >= 1024) {
+        c.mode = 1;
+      } else {
+        c.mode = 0;
+        c.team_ctas = count == 1 ? 8 : 2;
+      }
+      return c;
+    }
     if (count == 1) {
       if (prec == HEOM_FP64 && Mmax >= 256) {
         c.mode = 1;
@@ -444,12 +453,29 @@ struct Engine {
         int p2 = 1;
         while (p2 < ctas) p2 <<= 1;
         c.team_ctas = std::min(16, p2);
+        if (prec == HEOM_FP32_MIXED) {
+          // the hierarchy in the cluster's shared memory, ~128 nodes per CTA
+          int ct = 1;
+          while (ct < 16 && (ct * 128 < Mmax || heom::smem_dyn_bytes(N, smem_slice(Mmax, ct)) > max_dyn_smem())) ct <<= 1;
+          if (heom::smem_dyn_bytes(N, smem_slice(Mmax, ct)) <= max_dyn_smem()) {
+            c.mode = 2;
+            c.team_ctas = ct;
+            c.block = 512;
+            c.G = 4;
+          }
+        }
       }
     } else {
       c.mode = 0;
       c.block = 256;
       c.G = 1;
       c.team_ctas = 4;
+      if (prec == HEOM_FP32_MIXED && heom::smem_dyn_bytes(N, smem_slice(Mmax, 8)) <= max_dyn_smem()) {
+        c.mode = 2;
+        c.team_ctas = 8;
+        c.block = 256;
+        c.G = 2;
+      }
     }
     return c;
   }
@@ -601,6 +627,8 @@ struct Engine {
     struct Group {
       int N;
       int cplx;
+      int B = 0;       // nodes per CTA (mode 2)
+      int dyn = 0;     // dynamic shared memory per CTA (mode 2)
       LaunchCfg c;
       int nteams;
       std::vector<int32_t> first, list;
@@ -614,10 +642,24 @@ struct Engine {
       g.cplx = kv.first.second;
       g.c = cfg[g.N];
       std::vector<int>& ids = kv.second;
+      if (g.N > heom::kMaxSmallN) {
+        if (g.c.mode == 2) return fail(HEOM_EINVAL, "launch mode 2 supports at most %d sites", heom::kMaxSmallN);
+        g.dyn = heom::large_smem_bytes(g.N, (int)rsize());
+      } else if (g.c.mode == 2) {
+        int64_t Mmax = 0;
+        for (int id : ids) Mmax = std::max<int64_t>(Mmax, inst[id]->M);
+        g.B = smem_slice(Mmax, g.c.team_ctas);
+        g.dyn = heom::smem_dyn_bytes(g.N, g.B);
+        if (g.dyn > max_dyn_smem())
+          return fail(HEOM_EINVAL,
+                      "launch mode 2: %lld nodes of N=%d need %d bytes of shared memory per CTA with %d CTAs "
+                      "(at most %d); use more team CTAs or mode 0",
+                      (long long)Mmax, g.N, g.dyn, g.c.team_ctas, max_dyn_smem());
+      }
       if (g.c.mode == 1) {
         g.nteams = 1;
       } else {
-        int maxc = max_active_teams(g.N, g.cplx, g.c);
+        int maxc = max_active_teams(g.N, g.cplx, g.c, g.dyn);
         if (maxc < 1) return HEOM_ECUDA;
         g.nteams = std::max(1, std::min<int>((int)ids.size(), maxc));
       }
@@ -686,22 +728,38 @@ struct Engine {
       A.team_ctas = g.c.team_ctas;
       A.gsync = d_gsync.as<unsigned>();
       A.status = d_status.as<int>();
-      TRY(launch(g.N, g.cplx, g.c, g.nteams, A));
+      TRY(launch(g.N, g.cplx, g.c, g.nteams, A, g.B, g.dyn));
     }
     return HEOM_OK;
   }
 
   const void* kernel_for(int N, int cplx, const LaunchCfg& c) const {
+    if (N > heom::kMaxSmallN) return c.mode == 2 ? nullptr : heom::large_kernel(prec == HEOM_FP64, cplx != 0);
+    if (c.mode == 2) return prec == HEOM_FP64 ? nullptr : heom::smem_kernel(cplx != 0, c.G <= 2, N);
     return heom::engine_kernel(prec == HEOM_FP64, cplx != 0, c.G <= 2, N);
   }
 
-  int max_active_teams(int N, int cplx, const LaunchCfg& c) {
+  // Nodes per CTA when a cluster of `ctas` CTAs holds M nodes (mode 2).
+  static int smem_slice(int64_t M, int ctas) {
+    const int64_t per = (M + ctas - 1) / ctas;
+    return (int)((per + 31) / 32 * 32);
+  }
+  // Dynamic shared memory a CTA of the shared-memory engine may use.
+  int max_dyn_smem() const {
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    return optin - 4096;  // the kernel's static shared memory
+  }
+
+  int max_active_teams(int N, int cplx, const LaunchCfg& c, int dyn = 0) {
     const void* k = kernel_for(N, cplx, c);
-    if (!k) return fail(HEOM_EUNSUPPORTED, "no engine kernel for N=%d", N);
+    if (!k) return fail(HEOM_EUNSUPPORTED, "no engine kernel for N=%d (launch mode %d)", N, c.mode);
     if (c.team_ctas > 8) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    if (dyn > 0) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(c.team_ctas);
     lc.blockDim = dim3(c.block);
+    lc.dynamicSmemBytes = dyn;
     lc.stream = stream;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -722,23 +780,26 @@ struct Engine {
     return n;
   }
 
-  int launch(int N, int cplx, const LaunchCfg& c, int nteams, EngineArgs& A) {
+  int launch(int N, int cplx, const LaunchCfg& c, int nteams, EngineArgs& A, int B = 0, int dyn = 0) {
     const void* k = kernel_for(N, cplx, c);
-    if (!k) return fail(HEOM_EUNSUPPORTED, "no engine kernel for N=%d", N);
+    if (!k) return fail(HEOM_EUNSUPPORTED, "no engine kernel for N=%d (launch mode %d)", N, c.mode);
     if (c.mode == 1) {
       int per_sm = 0;
-      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, c.block, 0));
+      if (dyn > 0) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+      CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, c.block, dyn));
       if (per_sm < 1) return fail(HEOM_ECUDA, "block of %d threads cannot be resident", c.block);
       const int grid = per_sm * sms;
       CUDA_TRY(cudaMemsetAsync(A.gsync, 0, sizeof(unsigned), stream));
-      void* args[] = {&A};
-      CUDA_TRY(cudaLaunchCooperativeKernel(k, dim3(grid), dim3(c.block), args, 0, stream));
+      void* args[] = {&A, &B};
+      CUDA_TRY(cudaLaunchCooperativeKernel(k, dim3(grid), dim3(c.block), args, dyn, stream));
       return HEOM_OK;
     }
     if (c.team_ctas > 8) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    if (dyn > 0) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(nteams * c.team_ctas);
     lc.blockDim = dim3(c.block);
+    lc.dynamicSmemBytes = dyn;
     lc.stream = stream;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -747,7 +808,7 @@ struct Engine {
     at[0].val.clusterDim.z = 1;
     lc.attrs = at;
     lc.numAttrs = 1;
-    void* args[] = {&A};
+    void* args[] = {&A, &B};
     CUDA_TRY(cudaLaunchKernelExC(&lc, k, args));
     return HEOM_OK;
   }
@@ -993,7 +1054,11 @@ int heom_set_launch(heom_ctx* ctx, int32_t mode, int32_t team_ctas, int32_t bloc
   if (team_ctas > 0) n.team_ctas = team_ctas;
   if (block_threads > 0) n.block = block_threads;
   if (node_threads > 0) n.G = node_threads;
-  if (n.mode != 0 && n.mode != 1) return fail(HEOM_EINVAL, "mode must be 0 or 1");
+  if (n.mode < 0 || n.mode > 2) return fail(HEOM_EINVAL, "mode must be 0, 1 or 2");
+  if (n.mode == 2 && ctx->e.prec == HEOM_FP64) return fail(HEOM_EINVAL, "mode 2 (shared memory) needs HEOM_FP32_MIXED");
+  if (ctx->e.inst[0]->N > heom::kMaxSmallN && (n.mode == 2 || n.block > 256))
+    return fail(HEOM_EINVAL, "hierarchies with more than %d sites take modes 0 and 1 with at most 256 threads",
+                heom::kMaxSmallN);
   if (n.team_ctas < 1 || n.team_ctas > 16) return fail(HEOM_EINVAL, "team_ctas must be 1..16");
   const int maxb = ctx->e.max_block();
   if (n.block < 64 || n.block > maxb || n.block % 32)
@@ -1030,10 +1095,12 @@ int heom_autotune(heom_ctx* ctx, int64_t trial_steps, double* best_us_per_step) 
   CUDA_TRY(cudaMemcpyAsync(sr.p, in.root64.p, in.root64.bytes, cudaMemcpyDeviceToDevice, e.stream));
   CUDA_TRY(cudaMemcpyAsync(sa.p, in.acc.p, in.acc.bytes, cudaMemcpyDeviceToDevice, e.stream));
   std::vector<LaunchCfg> cands;
+  const bool large = in.N > heom::kMaxSmallN;
   for (int G : {1, 2, 4, 8, 16, 32}) {
+    if (large && G > 1) break;
     for (int block : {128, 256, 512})
       for (int ctas : {1, 2, 4, 8, 16}) {
-        if (block > e.max_block()) continue;
+        if (block > e.max_block() || (large && block != 256)) continue;
         LaunchCfg c;
         c.mode = 0;
         c.team_ctas = ctas;
@@ -1044,12 +1111,26 @@ int heom_autotune(heom_ctx* ctx, int64_t trial_steps, double* best_us_per_step) 
         cands.push_back(c);
       }
     for (int block : {128, 256}) {
+      if (large && block != 256) continue;
       LaunchCfg c;
       c.mode = 1;
       c.block = block;
       c.G = G;
       cands.push_back(c);
     }
+    if (e.prec == HEOM_FP32_MIXED && !large)
+      for (int block : {256, 512})
+        for (int ctas : {1, 2, 4, 8, 16}) {
+          LaunchCfg c;
+          c.mode = 2;
+          c.team_ctas = ctas;
+          c.block = block;
+          c.G = G;
+          if (heom::smem_dyn_bytes(in.N, Engine::smem_slice(in.M, ctas)) > e.max_dyn_smem()) continue;
+          const int64_t units = ((Engine::smem_slice(in.M, ctas) + 31) / 32) * G;
+          if (block / 32 > 4 * units && ctas > 1) continue;
+          cands.push_back(c);
+        }
   }
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
@@ -1060,7 +1141,9 @@ int heom_autotune(heom_ctx* ctx, int64_t trial_steps, double* best_us_per_step) 
   const double dt = 1.0;
   for (const LaunchCfg& c : cands) {
     e.cfg[in.N] = c;
-    if (c.mode == 0 && e.max_active_teams(in.N, in.complex_h, c) < 1) {
+    const int dyn = large ? heom::large_smem_bytes(in.N, (int)e.rsize())
+                          : (c.mode == 2 ? heom::smem_dyn_bytes(in.N, Engine::smem_slice(in.M, c.team_ctas)) : 0);
+    if (c.mode != 1 && e.max_active_teams(in.N, in.complex_h, c, dyn) < 1) {
       t_err.clear();
       continue;
     }
@@ -1147,11 +1230,14 @@ int heom_batch_get_rho(heom_batch* b, int32_t i, double* rho_out) {
   return b->e.get_states(i, 1, rho_out, true);
 }
 
-int heom_batch_set_launch(heom_batch* b, int32_t team_ctas, int32_t block_threads, int32_t node_threads) {
+int heom_batch_set_launch(heom_batch* b, int32_t mode, int32_t team_ctas, int32_t block_threads,
+                          int32_t node_threads) {
   if (!b) return fail(HEOM_EINVAL, "batch is NULL");
+  if (mode >= 0 && mode != 0 && mode != 2) return fail(HEOM_EINVAL, "batch launch mode must be 0 or 2");
+  if (mode == 2 && b->e.prec == HEOM_FP64) return fail(HEOM_EINVAL, "mode 2 (shared memory) needs HEOM_FP32_MIXED");
   for (auto& kv : b->e.cfg) {
     LaunchCfg n = kv.second;
-    n.mode = 0;
+    if (mode >= 0) n.mode = mode;
     if (team_ctas > 0) n.team_ctas = team_ctas;
     if (block_threads > 0) n.block = block_threads;
     if (node_threads > 0) n.G = node_threads;
@@ -1254,6 +1340,8 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
                                      int64_t out_every, double* d_pops, double* d_eta_loss, double* d_rho_out,
                                      void* cuda_stream) {
   TRY(validate(params, 0));
+  if (params->N > heom::kMaxSmallN)
+    return fail(HEOM_EINVAL, "the allocation-free entry point takes at most %d sites", heom::kMaxSmallN);
   if (!d_rho0) return fail(HEOM_EINVAL, "d_rho0 is NULL");
   if (nsteps < 0) return fail(HEOM_EINVAL, "nsteps < 0");
   if (out_every < 1) return fail(HEOM_EINVAL, "out_every must be >= 1");
@@ -1688,6 +1776,7 @@ int heom_server_submit(heom_server* s, const heom_params* params, const double* 
                        int64_t out_every, int64_t* request_id) {
   if (!s || !request_id) return fail(HEOM_EINVAL, "server or request_id is NULL");
   TRY(validate(params, 0));
+  if (params->N > heom::kMaxSmallN) return fail(HEOM_EUNSUPPORTED, "the server takes at most %d sites", heom::kMaxSmallN);
   TRY(validate_rho(rho0, params->N));
   if (nsteps < 0) return fail(HEOM_EINVAL, "nsteps < 0");
   if (out_every < 1) return fail(HEOM_EINVAL, "out_every must be >= 1");

@@ -95,7 +95,7 @@ def lib() -> ctypes.CDLL:
             "heom_batch_synchronize": [vp],
             "heom_batch_efficiency": [vp, _dp, _dp],
             "heom_batch_get_rho": [vp, ctypes.c_int32, _dp],
-            "heom_batch_set_launch": [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
+            "heom_batch_set_launch": [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -395,5 +395,6 @@ class Batch:
         _check(lib().heom_batch_get_rho(self._h, int(i), _ptr(out)))
         return _uncplx(out, (self.Ns[i], self.Ns[i]))
 
-    def set_launch(self, team_ctas=0, block_threads=0, node_threads=0):
-        _check(lib().heom_batch_set_launch(self._h, int(team_ctas), int(block_threads), int(node_threads)))
+    def set_launch(self, mode=-1, team_ctas=0, block_threads=0, node_threads=0):
+        _check(lib().heom_batch_set_launch(self._h, int(mode), int(team_ctas), int(block_threads),
+                                           int(node_threads)))

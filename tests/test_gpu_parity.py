@@ -100,6 +100,39 @@ def test_random_instances_fp32(N, K, cplx, term):
     assert np.abs(g["eta"] - o["eta"]).max() < TOL32_ETA
 
 
+LARGE = [(9, 2, False, 0), (10, 2, True, 1), (12, 2, False, 1), (16, 1, True, 0), (24, 2, False, 0),
+         (24, 1, True, 1)]
+
+
+@pytest.mark.parametrize("N,K,cplx,term", LARGE)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_large_site_counts(N, K, cplx, term, precision):
+    w = workloads.random_instance(N, K, seed=300 + N + K, complex_h=cplx, terminator=term)
+    w["nsteps"], w["out_every"] = 30, 10
+    g = run_gpu(w, precision)
+    o = run_oracle(w, want_state=precision == "fp64")
+    tp, te = (TOL64, TOL64) if precision == "fp64" else (TOL32_POP, TOL32_ETA)
+    assert np.abs(g["pops"] - o["pops"]).max() < tp
+    assert np.abs(g["eta"] - o["eta"]).max() < te
+    if precision == "fp64":
+        compare_states(g["state"], o, N, K, TOL64)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_large_trimer_full_size_first_steps(precision):
+    """The 24-site trimer at depth 4 (20 475 nodes), full hierarchy, first steps
+    element by element against the oracle (which takes seconds per step here)."""
+    w = workloads.large_trimer(nsteps=3)
+    w["out_every"] = 1
+    g = run_gpu(w, precision)
+    o = run_oracle(w, want_state=precision == "fp64")
+    tp = TOL64 if precision == "fp64" else TOL32_POP
+    assert np.abs(g["pops"] - o["pops"]).max() < tp
+    assert np.abs(g["trace"] - 1.0).max() < (1e-12 if precision == "fp64" else 1e-6)
+    if precision == "fp64":
+        compare_states(g["state"], o, 24, 4, TOL64)
+
+
 SHAPES = ([dict(mode=0, team_ctas=c, block_threads=b, node_threads=G) for c in (1, 2, 4, 8, 16)
            for b in (128, 512) for G in (1, 2, 3, 8, 32)]
           + [dict(mode=1, team_ctas=1, block_threads=b, node_threads=G) for b in (128, 256) for G in (1, 8, 28)])
@@ -123,11 +156,20 @@ def test_launch_shapes_fp64(shape, k4_reference):
     assert np.abs(g["eta"] - o["eta"]).max() < TOL64
 
 
-@pytest.mark.parametrize("shape", SHAPES[::3], ids=lambda s: "m%d_c%d_b%d_g%d" % (
+SHAPES32 = SHAPES[::3] + [dict(mode=2, team_ctas=c, block_threads=b, node_threads=G) for c in (1, 2, 4, 8, 16)
+                          for b in (256, 512) for G in (1, 2, 5, 8, 32)]
+
+
+@pytest.mark.parametrize("shape", SHAPES32, ids=lambda s: "m%d_c%d_b%d_g%d" % (
     s["mode"], s["team_ctas"], s["block_threads"], s["node_threads"]))
 def test_launch_shapes_fp32(shape, k4_reference):
     w, o = k4_reference
-    g = run_gpu(w, "fp32", launch=shape)
+    try:
+        g = run_gpu(w, "fp32", launch=shape)
+    except heom.HeomError as e:
+        # the shared-memory mode refuses hierarchies that do not fit its CTAs
+        assert shape["mode"] == 2 and e.code == heom.EINVAL and "shared memory" in str(e)
+        return
     assert np.abs(g["pops"] - o["pops"]).max() < TOL32_POP
     assert np.abs(g["eta"] - o["eta"]).max() < TOL32_ETA
 
@@ -258,6 +300,21 @@ def test_invalid_launch_shapes_rejected():
             with pytest.raises(heom.HeomError) as e:
                 c.set_launch(**bad)
             assert e.value.code == heom.EINVAL
+
+
+def test_shared_memory_mode_rejects_hierarchies_that_do_not_fit():
+    w = workloads.fmo_trap(K=6, nsteps=10)
+    with heom.Context(w["params"], "fp32") as c:
+        c.set_launch(mode=2, team_ctas=1)
+        with pytest.raises(heom.HeomError) as e:
+            c.propagate(1.0, 10, 10)
+        assert e.value.code == heom.EINVAL
+        c.set_launch(mode=2, team_ctas=16)
+        c.propagate(1.0, 10, 10)
+    with heom.Context(w["params"], "fp64") as c:
+        with pytest.raises(heom.HeomError) as e:
+            c.set_launch(mode=2)
+        assert e.value.code == heom.EINVAL
 
 
 def test_autotune_keeps_state_and_result():
