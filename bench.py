@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-scan measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-trace measurement")
+    ap.add_argument("--serving-requests", type=int, default=400,
+                    help="requests replayed from the serving trace (the full trace has 2000)")
     ap.add_argument("--cpu-sample-steps", type=int, default=0, help="RK4 steps of the oracle sample (0: auto)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes (profiling runs)")
@@ -348,6 +351,8 @@ def main():
     }
     if rank == 0 and not args.no_batched:
         line["batched"] = bench_batched(heom, torch, stream)
+    if rank == 0 and not args.no_serving:
+        line["serving"] = bench_serving(args.serving_requests)
     if rank == 0:
         n_sample = args.cpu_sample_steps or 25
         if not args.no_cpu:
@@ -383,6 +388,18 @@ def bench_batched(heom, torch, stream):
     return {"workload": "256 x N=7 trap, K~U{4..8}, lambda~U(2,200), T~U(77,300), 5 ps, fp32 mixed",
             "solves_per_s": len(ws) / (ms * 1e-3), "node_rhs_per_s": nodes * 4.0 * nsteps / (ms * 1e-3),
             "ms": ms, "total_nodes": nodes, "eta_mean": float(np.mean(eta))}
+
+
+def bench_serving(count):
+    """Serving: Poisson arrivals at 200 requests/s, N ~ U{2..8}, depth ~ U{3..8},
+    1-20 ps at 1 fs, mixed precision, continuous batching with memory
+    admission; latency from scheduled arrival to completion."""
+    from paper_1012_4382_gb300 import serving
+    tr = workloads.serving_trace(count=count)
+    r = serving.run_trace(tr, "fp32", device_bytes=16 << 30, streams=8, time_limit_s=120.0)
+    r["workload"] = ("Poisson 200 req/s, N~U{2..8}, K~U{3..8}, 1-20 ps at 1 fs, fp32 mixed; first %d requests "
+                     "of the seeded trace" % count)
+    return r
 
 
 if __name__ == "__main__":

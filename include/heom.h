@@ -61,8 +61,10 @@ extern "C" {
 
 /* precision of the propagation */
 #define HEOM_FP64 0         /* every array and every operation in double precision */
-#define HEOM_FP32_MIXED 1   /* auxiliary matrices and right-hand side in float; rho itself,
-                               its RK4 accumulation, populations and eta in double */
+#define HEOM_FP32_MIXED 1   /* auxiliary matrices and right-hand side in float; rho's RK4
+                               accumulation and the eta and loss integrals in float-float
+                               (about 48-bit significand; FP64 runs at 1/64 of the FP32 rate
+                               on GB300); populations, eta and loss returned in double */
 
 /* truncation of the hierarchy at |n| = K (the paper only says "truncate") */
 #define HEOM_TERM_NONE 0    /* sigma_{n+e_j} = 0 beyond the last level */
@@ -232,36 +234,41 @@ void heom_batch_destroy(heom_batch* b);
 
 /* -------------------------------------------------------------- serving */
 
-/* Continuous batching of propagation requests (the paper's FMO runs are
- * single solves; the benchmark spec's serving workload drives this):
- * requests of any size (N <= 8) are queued by heom_server_submit and admitted
- * by heom_server_progress in arrival order while one of `slots` CUDA streams
- * is free and the request's device state fits in `device_bytes`, a budget the
- * server allocates once at creation.  Each admitted request runs as its own
- * persistent launch (one thread-block cluster), so requests that arrive while
- * others run overlap with them on the device; finished requests give their
- * slot and memory back at the next progress call.  Node tables are cached per
- * (N, K) for the server's lifetime.  Calls are serialised by an internal
- * mutex; heom_server_progress never blocks on the device.
+/* Continuous batching of propagation requests (N <= 8).  The server owns a
+ * device-memory budget (device_bytes, allocated once), a pinned host buffer
+ * for results (host_bytes) and `streams` CUDA streams.  heom_server_submit
+ * queues a request; each heom_server_progress call
+ *   - marks finished every running request whose thread block has ended (the
+ *     kernel writes its populations and eta rows straight into pinned host
+ *     memory and then raises a flag there),
+ *   - retires launches whose device work has ended, returning their memory
+ *     and stream, and
+ *   - admits the queued requests that fit in the budget, in arrival order,
+ *     into one new launch on a free stream: one thread block per request.
+ * So requests that arrive while others run start at the next progress call
+ * and overlap with them on the device, and each completes as soon as its own
+ * block is done.  Node tables are cached per (N, K).  Calls are serialised by
+ * an internal mutex; heom_server_progress never blocks on the device.
  * Request states: 0 queued, 1 running, 2 done, 3 cancelled, 4 failed. */
 typedef struct heom_server heom_server;
-int heom_server_create(size_t device_bytes, int32_t slots, heom_server** out);
+int heom_server_create(size_t device_bytes, size_t host_bytes, int32_t streams, heom_server** out);
 
 /* Queues one propagation from rho0 (host N*N complex Hermitian) of nsteps
  * steps of dt_fs with outputs every out_every steps.  HEOM_ENOMEM if the
- * request can never fit in the budget; HEOM_EINVAL for malformed input.
+ * request can never fit in the budgets; HEOM_EINVAL for malformed input.
  * params and rho0 are copied. */
 int heom_server_submit(heom_server* s, const heom_params* params, const double* rho0, double dt_fs, int64_t nsteps,
                        int64_t out_every, int64_t* request_id);
 
-/* Retires finished requests and admits queued ones; completed (may be NULL)
- * receives the number retired by this call. */
+/* Retires finished requests and launches and admits queued requests;
+ * completed (may be NULL) receives the number of requests finished by this
+ * call. */
 int heom_server_progress(heom_server* s, int32_t* completed);
 int heom_server_status(heom_server* s, int64_t request_id, int32_t* state);
 
 /* Results of a finished request: pops_out[nout*N], eta_out[nout],
  * loss_out[nout] (each may be NULL), times_out[2] = seconds from submission
- * to admission and to completion as seen by heom_server_progress. */
+ * to launch and to the progress call that saw it finish. */
 int heom_server_result(heom_server* s, int64_t request_id, double* pops_out, double* eta_out, double* loss_out,
                        double* times_out);
 
@@ -272,7 +279,7 @@ int heom_server_release(heom_server* s, int64_t request_id);
 int heom_server_cancel(heom_server* s, int64_t request_id);
 int heom_server_stats(heom_server* s, int64_t* queued, int64_t* running, int64_t* bytes_in_use);
 
-/* Waits for all running requests' device work, then frees everything. */
+/* Waits for all device work of the server, then frees everything. */
 void heom_server_destroy(heom_server* s);
 
 /* --------------------------------------------- allocation-free propagation */

@@ -41,8 +41,9 @@
 // at compile time.  Between RK4 stages the team synchronises with a hardware
 // cluster barrier (release/acquire at cluster scope) or a software grid
 // barrier with a bounded wait.  In mixed precision the root node rho is
-// handled by one warp per stage (root_task) so that its double-precision
-// accumulation runs with all 32 lanes active.
+// split into one work item per unit, each run by one lane of its own warp,
+// so that its double-precision accumulations (FP64 runs at 1/64 of the FP32
+// rate on this GPU) proceed in parallel rather than in one serial chain.
 #pragma once
 
 #include <cstdint>
@@ -66,17 +67,25 @@ struct Inst {
   void* y;             // [N*N][Mpad] packed state, element-major (R)
   void* wa;            // stage buffers, same layout
   void* wb;
-  double* y0;          // [N*N] packed root node in double (mixed precision only)
-  double* w0a;
-  double* w0b;
+  // mixed precision: the root node rho in float-float, N*N (hi, lo) float
+  // pairs per buffer (y0, wa0, wb0); its hi parts are also kept in column 0 of
+  // y, wa, wb for the neighbours
+  void* y0;
+  void* w0a;
+  void* w0b;
   const void* coef;    // flat coefficient block, see CoefLayout below
   const void* ngam;    // [Mpad] sum_j n_j gamma_j per node (R)
-  double* acc;         // [2] eta and loss integrals
+  double* acc;         // [2] eta and loss integrals (read at the start of a call, written at its end)
+  void* parts;         // [32] partial (eta, loss) sums per unit group: float-float x2 (mixed) or double x2
   double* out_pops;    // [nout][N] populations (may be null)
   double* out_el;      // [nout][2] eta, loss (may be null)
+  int* done;           // set to 1 (system-wide release) when the instance is finished (may be null)
   int64_t nsteps;
   int64_t out_every;
   double dt;
+  double hd[4];        // Horner steps h/4, h/3, h/2, h
+  float hh[4], hl[4];  // the same as float-float pairs (hi, lo)
+  float ec[4 * kMaxSites];  // per site a: h*Gamma_RC,a (hi, lo), h*Gamma_phot,a (hi, lo)
 };
 
 // Coefficient block (host writes it with the same layout):
@@ -358,11 +367,129 @@ __device__ __forceinline__ R Av(const V& v) {
   else return R(0);
 }
 
+// ------------------------------------------------------------ float-float
+//
+// FP64 runs at 1/64 of the FP32 rate on this GPU (a double-precision warp
+// instruction occupies a sub-partition's FP64 unit for 64 cycles whatever the
+// number of active lanes), so the mixed-precision kernels keep rho's RK4
+// accumulation and the eta integral in float-float: an unevaluated sum
+// hi + lo of two floats, carried with the error-free transformations TwoSum
+// (Knuth) and TwoProduct-by-FMA (Dekker/Ogita-Rump-Oishi).  Each operation
+// below is exact up to a relative 2^-48; no double-precision instruction runs
+// in the stage loop.
+
+struct FF {
+  float h, l;
+};
+
+// y + (ah + al) * r
+__device__ __forceinline__ FF ff_axpy(FF y, float ah, float al, float r) {
+  const float p = ah * r;
+  const float e = fmaf(ah, r, -p) + al * r;  // error of the product, plus the low part of a
+  const float s = y.h + p;                    // TwoSum(y.h, p) = (s, t)
+  const float bp = s - y.h;
+  float t = (y.h - (s - bp)) + (p - bp);
+  t += y.l + e;
+  const float h = s + t;                      // FastTwoSum renormalisation
+  return FF{h, t - (h - s)};
+}
+
+// a + b
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.h + b.h;
+  const float bp = s - a.h;
+  float t = (a.h - (s - bp)) + (b.h - bp);
+  t += a.l + b.l;
+  const float h = s + t;
+  return FF{h, t - (h - s)};
+}
+
+// (ch + cl) * (x.h + x.l)
+__device__ __forceinline__ FF ff_mul(float ch, float cl, FF x) {
+  const float p = ch * x.h;
+  const float e = fmaf(ch, x.h, -p) + (ch * x.l + cl * x.h);
+  const float h = p + e;
+  return FF{h, e - (h - p)};
+}
+
+__device__ __forceinline__ double ff_to_double(FF a) { return (double)a.h + (double)a.l; }
+
+// Running eta and loss sums of one thread (the owner of some of the root's
+// diagonal units): float-float in the mixed kernels, double in the FP64 ones.
+template <typename R>
+struct EtaAcc;
+template <>
+struct EtaAcc<float> {
+  FF e{0.f, 0.f}, l{0.f, 0.f};
+  // contribution of diagonal a of the root's stage-3 input x: h Gamma_a x
+  __device__ __forceinline__ void add(const Inst& I, int a, FF x) {
+    e = ff_add(e, ff_mul(I.ec[4 * a], I.ec[4 * a + 1], x));
+    l = ff_add(l, ff_mul(I.ec[4 * a + 2], I.ec[4 * a + 3], x));
+  }
+  __device__ __forceinline__ void store(const Inst& I, int slot) const {
+    float* p = static_cast<float*>(I.parts) + 4 * slot;
+    p[0] = e.h;
+    p[1] = e.l;
+    p[2] = l.h;
+    p[3] = l.l;
+  }
+};
+template <>
+struct EtaAcc<double> {
+  double e = 0.0, l = 0.0;
+  __device__ __forceinline__ void add(const Inst& I, const double* cfd, int N, int a, double x) {
+    e += I.dt * cfd[a] * x;
+    l += I.dt * cfd[N + a] * x;
+  }
+  __device__ __forceinline__ void store(const Inst& I, int slot) const {
+    double* p = static_cast<double*>(I.parts) + 2 * slot;
+    p[0] = e;
+    p[1] = l;
+  }
+};
+
+// eta and loss at the current step: the value at the start of the call plus
+// every owner's running sum (read through L2: the owners wrote them before
+// the last stage barrier).
+template <typename R>
+__device__ __forceinline__ void eta_total(const Inst& I, int nslots, double acc0, double acc1, double& e, double& l) {
+  if constexpr (sizeof(R) == 4) {
+    FF se{0.f, 0.f}, sl{0.f, 0.f};
+    const float* p = static_cast<const float*>(I.parts);
+    for (int k = 0; k < nslots; ++k) {
+      se = ff_add(se, FF{__ldcg(p + 4 * k), __ldcg(p + 4 * k + 1)});
+      sl = ff_add(sl, FF{__ldcg(p + 4 * k + 2), __ldcg(p + 4 * k + 3)});
+    }
+    e = acc0 + ff_to_double(se);
+    l = acc1 + ff_to_double(sl);
+  } else {
+    double se = 0.0, sl = 0.0;
+    const double* p = static_cast<const double*>(I.parts);
+    for (int k = 0; k < nslots; ++k) {
+      se += __ldcg(p + 2 * k);
+      sl += __ldcg(p + 2 * k + 1);
+    }
+    e = acc0 + se;
+    l = acc1 + sl;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void eta_write_row(const Inst& I, int nslots, double acc0, double acc1, int64_t row) {
+  if (!I.out_el) return;
+  double e, l;
+  eta_total<R>(I, nslots, acc0, acc1, e, l);
+  I.out_el[2 * row] = e;
+  I.out_el[2 * row + 1] = l;
+}
+
 template <typename R>
 struct StageCoef {
-  R h;
-  double hd;
-  double* out64;  // root output in double (mixed)
+  R h;         // Horner step of this stage (R precision)
+  float hl;    // low part of the float-float step (mixed root)
+  FF* root_in;   // mixed: the root's float-float stage input
+  FF* root_out;  // mixed: the root's float-float stage output
+  const FF* root_y;  // mixed: the root's float-float y
 };
 
 // Right-hand side of unit u (pair (a, b) or diagonal a) of one node.
@@ -471,46 +598,27 @@ __device__ __forceinline__ void unit_rhs(const V& v, const R* __restrict__ cf, R
   }
 }
 
-// eta and loss: the extra rows of the augmented RK4 system, updated at the
-// last stage from the root's stage input x_mm; written to the outputs at
-// output steps.
 // Output steps are tracked with a counter (no 64-bit division in the loop):
-// ostep.now is true at steps whose end is an output row, ostep.row is that row.
+// now is true at steps whose end is an output row, row is that row.
 struct OutStep {
   bool now;
   int64_t row;
 };
 
-__device__ __forceinline__ void eta_update(const Inst& I, double e, double l, OutStep os) {
-  I.acc[0] += I.dt * e;
-  I.acc[1] += I.dt * l;
-  if (I.out_el && os.now) {
-    I.out_el[2 * os.row] = I.acc[0];
-    I.out_el[2 * os.row + 1] = I.acc[1];
-  }
-}
-
-// All units of one node that belong to the unit mask, one RK4 stage.
+// All units of one node that belong to the unit mask, one RK4 stage.  For
+// the root node of the mixed path the Horner update w = y + h r runs in
+// float-float on the root's own buffers, and the hi part is stored for the
+// neighbours.  At the last stage the owner of the root's diagonal unit a adds
+// h Gamma_a x_aa to its running eta and loss sums (the extra rows of the
+// augmented RK4 system, x being the stage input).
 template <int N, typename R, bool MIXED, bool CPLX, class V>
 __device__ __forceinline__ void node_units(const Inst& I, const R* __restrict__ cf, const double* __restrict__ cfd,
                                            const StageCoef<R>& P, const V& v, R ngam, int s, bool root,
-                                           uint64_t umask, OutStep os) {
+                                           uint64_t umask, OutStep os, EtaAcc<R>& ea) {
   constexpr int NP = N * (N - 1) / 2;
   constexpr int U = NP + N;
   const bool term = I.terminator && (v.template Up<0>() == -1);
   const bool out_row = (s == 3) && root && I.out_pops && os.now;
-
-  // eta and loss (plain FP64 path; the mixed path does this in root_task)
-  if (!MIXED && s == 3 && root && (umask & 1ull)) {
-    double e = 0.0, l = 0.0;
-    static_for<0, N>([&](auto mc) {
-      constexpr int m = decltype(mc)::value;
-      const double x = (double)v.template P<m * N + m>();
-      e += cfd[m] * x;
-      l += cfd[N + m] * x;
-    });
-    eta_update(I, e, l, os);
-  }
 
   static_for<0, U>([&](auto uc) {
     constexpr int u = decltype(uc)::value;
@@ -521,129 +629,40 @@ __device__ __forceinline__ void node_units(const Inst& I, const R* __restrict__ 
       constexpr int a = pair_a(N, u);
       constexpr int b = pair_b(N, u);
       constexpr int pr = a * N + b, pi = b * N + a;
-      v.template St<pr>(v.template Y<pr>() + P.h * re);
-      v.template St<pi>(v.template Y<pi>() + P.h * im);
+      if (MIXED && root) {
+        if constexpr (MIXED) {
+          const FF wr = ff_axpy(P.root_y[pr], P.h, P.hl, re);
+          const FF wi = ff_axpy(P.root_y[pi], P.h, P.hl, im);
+          P.root_out[pr] = wr;
+          P.root_out[pi] = wi;
+          v.template St<pr>(wr.h);
+          v.template St<pi>(wi.h);
+        }
+      } else {
+        v.template St<pr>(v.template Y<pr>() + P.h * re);
+        v.template St<pi>(v.template Y<pi>() + P.h * im);
+      }
     } else {
       constexpr int a = u - NP;
       constexpr int pd = a * N + a;
-      const R val = v.template Y<pd>() + P.h * re;
-      v.template St<pd>(val);
-      if (out_row) I.out_pops[os.row * N + a] = (double)val;
+      if (MIXED && root) {
+        if constexpr (MIXED) {
+          if (s == 3) ea.add(I, a, P.root_in[pd]);
+          const FF w = ff_axpy(P.root_y[pd], P.h, P.hl, re);
+          P.root_out[pd] = w;
+          v.template St<pd>(w.h);
+          if (out_row) I.out_pops[os.row * N + a] = ff_to_double(w);
+        }
+      } else {
+        if constexpr (!MIXED) {
+          if (root && s == 3) ea.add(I, cfd, N, a, (double)v.template P<pd>());
+        }
+        const R vv = v.template Y<pd>() + P.h * re;
+        v.template St<pd>(vv);
+        if (out_row) I.out_pops[os.row * N + a] = (double)vv;
+      }
     }
   });
-}
-
-// Mixed precision: the root node (rho itself) is computed by one warp, one
-// unit per lane, and accumulated in double with all lanes active (FP64 runs
-// at 1/64 of the FP32 rate here, so it must not serialise on one lane).
-// own(p) reads the root's float stage input, up(j) gives the link handle of
-// e_j, gather(h, p) element p of a linked node, store(p, v) the float copy of
-// the root's stage output.
-template <int N, bool CPLX, class Own, class UpH, class Gather, class Store>
-__device__ __forceinline__ void root_task(const Inst& I, const float* __restrict__ cf, const double* __restrict__ cfd,
-                                          const StageCoef<float>& P, int s, int lane, OutStep os, Own own,
-                                          UpH up, Gather gather, Store store) {
-  using L = CoefLayout<float>;
-  constexpr int NP = N * (N - 1) / 2;
-  constexpr int U = NP + N;
-  if (s == 3) {
-    double e = 0.0, l = 0.0;
-    if (lane < N) {
-      const double x = I.w0a[lane * N + lane];
-      e = cfd[lane] * x;
-      l = cfd[N + lane] * x;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      e += __shfl_down_sync(0xffffffffu, e, off);
-      l += __shfl_down_sync(0xffffffffu, l, off);
-    }
-    if (lane == 0) eta_update(I, e, l, os);
-  }
-  auto S = [&](int k, int l) -> float { return k <= l ? own(k * N + l) : own(l * N + k); };
-  auto A = [&](int k, int l) -> float { return k < l ? own(l * N + k) : (k > l ? -own(k * N + l) : 0.f); };
-  const bool term = I.terminator && up(0) == -1;  // depth 0: the root is the last level
-  for (int uu = lane; uu < U; uu += 32) {
-    float re = 0.f, im = 0.f;
-    int a, b;
-    if (uu < NP) {
-      int r = uu;
-      a = 0;
-      while (r >= N - 1 - a) { r -= N - 1 - a; ++a; }
-      b = a + 1 + r;
-      const float x = own(a * N + b), yi = own(b * N + a);
-#pragma unroll
-      for (int k = 0; k < N; ++k) {
-        if (k != a) {
-          const float jak = cf[L::J(N) + a * N + k];
-          re += jak * A(k, b);
-          im -= jak * S(k, b);
-        }
-        if (k != b) {
-          const float jkb = cf[L::J(N) + k * N + b];
-          re -= A(a, k) * jkb;
-          im += S(a, k) * jkb;
-        }
-        if (CPLX) {
-          if (k != a) {
-            const float jak = cf[L::Ji(N) + a * N + k];
-            re += jak * S(k, b);
-            im += jak * A(k, b);
-          }
-          if (k != b) {
-            const float jkb = cf[L::Ji(N) + k * N + b];
-            re -= S(a, k) * jkb;
-            im -= A(a, k) * jkb;
-          }
-        }
-      }
-      const float d = cf[L::eps(N) + a] - cf[L::eps(N) + b];
-      const float c = cf[L::ghalf(N) + a] + cf[L::ghalf(N) + b];
-      re += d * yi - c * x;
-      im -= d * x + c * yi;
-      const int ua = up(a), ub = up(b);
-      if (ua != -1) {
-        re -= gather(ua, b * N + a);
-        im += gather(ua, a * N + b);
-      }
-      if (ub != -1) {
-        re += gather(ub, b * N + a);
-        im -= gather(ub, a * N + b);
-      }
-      if (term) {
-        const float al_a = cf[L::alpha(N) + a], be_a = cf[L::beta(N) + a];
-        const float al_b = cf[L::alpha(N) + b], be_b = cf[L::beta(N) + b];
-        const float ca = 1.f / cf[L::gam(N) + a];
-        const float cb = 1.f / cf[L::gam(N) + b];
-        re += ca * (-al_a * x - be_a * yi) + cb * (-al_b * x + be_b * yi);
-        im += ca * (-al_a * yi + be_a * x) + cb * (-al_b * yi - be_b * x);
-      }
-    } else {
-      a = b = uu - NP;
-      const float x = own(a * N + a);
-#pragma unroll
-      for (int k = 0; k < N; ++k) {
-        if (k != a) {
-          re += 2.f * cf[L::J(N) + a * N + k] * A(k, a);
-          if (CPLX) re += 2.f * cf[L::Ji(N) + a * N + k] * S(k, a);
-        }
-      }
-      re -= 2.f * cf[L::ghalf(N) + a] * x;
-    }
-    // accumulate in double: w = y0 + h r
-    const int pr = a * N + b;
-    const double vr = I.y0[pr] + P.hd * (double)re;
-    P.out64[pr] = vr;
-    store(pr, (float)vr);
-    if (a != b) {
-      const int pi = b * N + a;
-      const double vi = I.y0[pi] + P.hd * (double)im;
-      P.out64[pi] = vi;
-      store(pi, (float)vi);
-    } else if (s == 3 && I.out_pops && os.now) {
-      I.out_pops[os.row * N + a] = vr;
-    }
-  }
 }
 
 // Row 0 of the outputs (the state at the start of the call).
@@ -651,7 +670,8 @@ template <int N, typename R, bool MIXED>
 __device__ __forceinline__ void write_row0(const Inst& I) {
   if (I.out_pops)
     for (int a = 0; a < N; ++a)
-      I.out_pops[a] = MIXED ? I.y0[a * N + a] : (double)static_cast<const R*>(I.y)[(a * N + a) * I.Mpad];
+      I.out_pops[a] = MIXED ? ff_to_double(static_cast<const FF*>(I.y0)[a * N + a])
+                            : (double)static_cast<const R*>(I.y)[(a * N + a) * I.Mpad];
   if (I.out_el) {
     I.out_el[0] = I.acc[0];
     I.out_el[1] = I.acc[1];
@@ -660,6 +680,15 @@ __device__ __forceinline__ void write_row0(const Inst& I) {
 
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Marks an instance finished for a host that polls its flag (host-mapped
+// memory): every output write of the team happened before the team barrier
+// that precedes this call; the system-scope fence orders them before the flag.
+__device__ __forceinline__ void signal_done(const Inst& I) {
+  if (!I.done) return;
+  __threadfence_system();
+  *reinterpret_cast<volatile int*>(I.done) = 1;
 }
 
 template <typename R>
@@ -673,14 +702,37 @@ __device__ __forceinline__ void load_instance(const EngineArgs& A, int li, Inst&
   __syncthreads();
 }
 
-__device__ __forceinline__ void stage_select(int s, double dt, double& hd, int& in_sel, int& out_sel) {
-  // Horner RK4: 0: wa = y + h/4 L y; 1: wb = y + h/3 L wa; 2: wa = y + h/2 L wb; 3: y = y + h L wa
-  // selectors: 0 = y, 1 = wa, 2 = wb
-  if (s == 0) { hd = 0.25 * dt; in_sel = 0; out_sel = 1; }
-  else if (s == 1) { hd = dt / 3.0; in_sel = 1; out_sel = 2; }
-  else if (s == 2) { hd = 0.5 * dt; in_sel = 2; out_sel = 1; }
-  else { hd = dt; in_sel = 1; out_sel = 0; }
+// Horner RK4: 0: wa = y + h/4 L y; 1: wb = y + h/3 L wa; 2: wa = y + h/2 L wb; 3: y = y + h L wa.
+// Buffer selectors: 0 = y, 1 = wa, 2 = wb.
+__device__ __forceinline__ void stage_buffers(int s, int& in_sel, int& out_sel) {
+  in_sel = (s == 0) ? 0 : (s == 2 ? 2 : 1);
+  out_sel = (s == 1) ? 2 : (s == 3 ? 0 : 1);
 }
+
+template <typename R>
+__device__ __forceinline__ StageCoef<R> stage_coef(const Inst& I, int s, int in_sel, int out_sel) {
+  StageCoef<R> P;
+  if constexpr (sizeof(R) == 4) {
+    P.h = I.hh[s];
+    P.hl = I.hl[s];
+  } else {
+    P.h = I.hd[s];
+    P.hl = 0.f;
+  }
+  FF* roots[3] = {static_cast<FF*>(I.y0), static_cast<FF*>(I.w0a), static_cast<FF*>(I.w0b)};
+  P.root_in = roots[in_sel];
+  P.root_out = roots[out_sel];
+  P.root_y = roots[0];
+  return P;
+}
+
+// The owner threads of the root's diagonal units publish their running sums
+// (after the last stage of output steps and of the final step); one thread
+// writes the eta row one stage later, once the team barrier has ordered them.
+struct EtaRows {
+  int64_t pending = -1;
+  double acc0 = 0.0, acc1 = 0.0;
+};
 
 // ------------------------------------------------------ global-memory engine
 
@@ -690,6 +742,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) heom_engine_kernel
   __shared__ Inst s_inst;
   __shared__ uint64_t s_umask[32];
   constexpr int U = N * (N - 1) / 2 + N;
+  constexpr int NP = N * (N - 1) / 2;
 
   int team, rank, team_size;
   if (A.mode == 0) {
@@ -712,6 +765,21 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) heom_engine_kernel
       if (u % G == (int)threadIdx.x) m |= 1ull << u;
     s_umask[threadIdx.x] = m;
   }
+  // this thread's parts slot: the smallest group g whose root item it runs
+  // and that owns a diagonal unit (-1: none)
+  int slot = -1;
+  if (lane == 0)
+    for (int g = 0; g < G; ++g)
+      if (g % W == warp) {
+        bool diag = false;
+        for (int a = 0; a < N; ++a) diag |= ((NP + a) % G) == g;
+        if (diag) {
+          slot = g;
+          break;
+        }
+      }
+  const bool lead = (warp == 0 && lane == 0);
+  const int nslots = G < 32 ? G : 32;
   unsigned epoch = 0;
 
   for (int li = A.team_first[team]; li < A.team_first[team + 1]; ++li) {
@@ -722,12 +790,17 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) heom_engine_kernel
     const R* ngam = static_cast<const R*>(I.ngam);
     const int nblk = (I.M + 31) >> 5;
     const int items = nblk * G;
-    const int nitems = items + (MIXED ? 1 : 0);  // the mixed path adds one root task
-
-    if (warp == 0 && lane == 0) write_row0<N, R, MIXED>(I);
+    EtaAcc<R> ea;
+    EtaRows rows;
+    rows.acc0 = I.acc[0];
+    rows.acc1 = I.acc[1];
+    if (lead) {
+      write_row0<N, R, MIXED>(I);
+      for (int k = 0; k < nslots; ++k) ea.store(I, k);  // zero every running-sum slot of this instance
+    }
+    if (!team_barrier(A, epoch)) return;
 
     R* arr[3] = {static_cast<R*>(I.y), static_cast<R*>(I.wa), static_cast<R*>(I.wb)};
-    double* arr64[3] = {I.y0, I.w0a, I.w0b};
     int64_t next_out = I.out_every, orow = 1;
     for (int64_t t = 0; t < I.nsteps; ++t) {
       const OutStep os{t + 1 == next_out, orow};
@@ -737,35 +810,38 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) heom_engine_kernel
       }
 #pragma unroll 1
       for (int s = 0; s < 4; ++s) {
-        StageCoef<R> P;
+        if (s == 0 && rows.pending >= 0) {
+          if (lead) eta_write_row<R>(I, nslots, rows.acc0, rows.acc1, rows.pending);
+          rows.pending = -1;
+        }
         int in_sel, out_sel;
-        stage_select(s, I.dt, P.hd, in_sel, out_sel);
-        P.h = (R)P.hd;
-        P.out64 = arr64[out_sel];
+        stage_buffers(s, in_sel, out_sel);
+        const StageCoef<R> P = stage_coef<R>(I, s, in_sel, out_sel);
         GlobalArrays<R> ga{arr[in_sel], arr[out_sel], arr[0], I.up, I.dn, I.Mpad};
-        for (int it = warp; it < nitems; it += W) {
-          if (MIXED && it == items) {
-            if constexpr (MIXED) {
-              const int Mp = I.Mpad;
-              const float* win = reinterpret_cast<const float*>(ga.win);
-              float* wout = reinterpret_cast<float*>(ga.wout);
-              root_task<N, CPLX>(
-                  I, reinterpret_cast<const float*>(cf), cfd, reinterpret_cast<const StageCoef<float>&>(P), s, lane,
-                  os, [&](int p) { return win[p * Mp]; }, [&](int j) { return (int)I.up[j * Mp]; },
-                  [&](int h, int p) { return win[p * Mp + h]; }, [&](int p, float v) { wout[p * Mp] = v; });
-            }
-            continue;
-          }
+        for (int it = warp; it < items; it += W) {
           const int nb = it / G;
           const int g = it - nb * G;
           const int n = (nb << 5) + lane;
-          if (n >= I.M || (MIXED && n == 0)) continue;
+          if (n >= I.M) continue;
           const GlobalView<N, R, REG> v(ga, n);
-          node_units<N, R, MIXED, CPLX>(I, cf, cfd, P, v, ngam[n], s, n == 0, s_umask[g], os);
+          node_units<N, R, MIXED, CPLX>(I, cf, cfd, P, v, ngam[n], s, n == 0, s_umask[g], os, ea);
         }
+        if (s == 3 && slot >= 0 && (os.now || t + 1 == I.nsteps)) ea.store(I, slot);
         if (!team_barrier(A, epoch)) return;
       }
+      if (os.now) rows.pending = os.row;
     }
+    if (lead) {
+      if (rows.pending >= 0) eta_write_row<R>(I, nslots, rows.acc0, rows.acc1, rows.pending);
+      if (I.nsteps > 0) {
+        double e, l;
+        eta_total<R>(I, nslots, rows.acc0, rows.acc1, e, l);
+        I.acc[0] = e;
+        I.acc[1] = l;
+      }
+    }
+    if (!team_barrier(A, epoch)) return;
+    if (lead) signal_done(I);
   }
 }
 
@@ -792,6 +868,7 @@ __global__ void __launch_bounds__(512) heom_smem_kernel(EngineArgs A, int B) {
   __shared__ Inst s_inst;
   __shared__ uint64_t s_umask[32];
   constexpr int U = N * (N - 1) / 2 + N;
+  constexpr int NP = N * (N - 1) / 2;
   constexpr int NN = N * N;
 
   unsigned rank, C;
@@ -808,6 +885,19 @@ __global__ void __launch_bounds__(512) heom_smem_kernel(EngineArgs A, int B) {
       if (u % G == (int)threadIdx.x) m |= 1ull << u;
     s_umask[threadIdx.x] = m;
   }
+  int slot = -1;
+  if (rank == 0 && lane == 0)
+    for (int g = 0; g < G; ++g)
+      if (g % wpc == warp) {
+        bool diag = false;
+        for (int a = 0; a < N; ++a) diag |= ((NP + a) % G) == g;
+        if (diag) {
+          slot = g;
+          break;
+        }
+      }
+  const bool lead = (rank == 0 && threadIdx.x == 0);
+  const int nslots = G < 32 ? G : 32;
   float* sy = reinterpret_cast<float*>(dsm);
   float* swa = sy + NN * B;
   float* swb = swa + NN * B;
@@ -852,13 +942,18 @@ __global__ void __launch_bounds__(512) heom_smem_kernel(EngineArgs A, int B) {
     }
     for (int l = threadIdx.x; l < B; l += blockDim.x)
       sng[l] = l < nloc ? static_cast<const float*>(I.ngam)[n0 + l] : 0.f;
-    if (rank == 0 && threadIdx.x == 0) write_row0<N, float, true>(I);
+    EtaAcc<float> ea;
+    EtaRows rows;
+    rows.acc0 = I.acc[0];
+    rows.acc1 = I.acc[1];
+    if (lead) {
+      write_row0<N, float, true>(I);
+      for (int k = 0; k < nslots; ++k) ea.store(I, k);  // zero every running-sum slot of this instance
+    }
     cluster_sync_all();
 
     const int nblk = (nloc + 31) >> 5;
     const int items = nblk * G;
-    const int nitems = items + (rank == 0 ? 1 : 0);  // rank 0 also runs the root task
-    double* arr64[3] = {I.y0, I.w0a, I.w0b};
     int64_t next_out = I.out_every, orow = 1;
     for (int64_t t = 0; t < I.nsteps; ++t) {
       const OutStep os{t + 1 == next_out, orow};
@@ -868,32 +963,35 @@ __global__ void __launch_bounds__(512) heom_smem_kernel(EngineArgs A, int B) {
       }
 #pragma unroll 1
       for (int s = 0; s < 4; ++s) {
-        StageCoef<float> P;
+        if (s == 0 && rows.pending >= 0) {
+          if (lead) eta_write_row<float>(I, nslots, rows.acc0, rows.acc1, rows.pending);
+          rows.pending = -1;
+        }
         int in_sel, out_sel;
-        stage_select(s, I.dt, P.hd, in_sel, out_sel);
-        P.h = (float)P.hd;
-        P.out64 = arr64[out_sel];
+        stage_buffers(s, in_sel, out_sel);
+        const StageCoef<float> P = stage_coef<float>(I, s, in_sel, out_sel);
         SmemArrays sa{arr[in_sel], arr[out_sel], sy, sup, sdn, snj, sng,
                       (unsigned)(in_sel * NN * B * 4), B};
-        for (int it = warp; it < nitems; it += wpc) {
-          if (it == items) {
-            const float* win = sa.win;
-            float* wout = sa.wout;
-            const unsigned woff = sa.win_off;
-            root_task<N, CPLX>(
-                I, cf, cfd, P, s, lane, os, [&](int p) { return win[p * B]; }, [&](int j) { return (int)sup[j * B]; },
-                [&](int h, int p) { return ld_dsmem_f32((unsigned)h + woff + (unsigned)(p * B * 4)); },
-                [&](int p, float v) { wout[p * B] = v; });
-            continue;
-          }
+        for (int it = warp; it < items; it += wpc) {
           const int nb = it / G;
           const int g = it - nb * G;
           const int l = (nb << 5) + lane;
-          if (l >= nloc || (rank == 0 && l == 0)) continue;
+          if (l >= nloc) continue;
           const SmemView<N, REG> v(sa, l);
-          node_units<N, float, true, CPLX>(I, cf, cfd, P, v, sng[l], s, false, s_umask[g], os);
+          node_units<N, float, true, CPLX>(I, cf, cfd, P, v, sng[l], s, rank == 0 && l == 0, s_umask[g], os, ea);
         }
+        if (s == 3 && slot >= 0 && (os.now || t + 1 == I.nsteps)) ea.store(I, slot);
         cluster_sync_all();
+      }
+      if (os.now) rows.pending = os.row;
+    }
+    if (lead) {
+      if (rows.pending >= 0) eta_write_row<float>(I, nslots, rows.acc0, rows.acc1, rows.pending);
+      if (I.nsteps > 0) {
+        double e, l;
+        eta_total<float>(I, nslots, rows.acc0, rows.acc1, e, l);
+        I.acc[0] = e;
+        I.acc[1] = l;
       }
     }
     // write the slice of y back
@@ -903,12 +1001,9 @@ __global__ void __launch_bounds__(512) heom_smem_kernel(EngineArgs A, int B) {
       if (l < nloc) gyw[p * Mp + n0 + l] = sy[idx];
     }
     cluster_sync_all();  // no CTA reuses or leaves its slice while others may still read it
+    if (lead) signal_done(I);
   }
 }
-
-}  // namespace heom
-
-namespace heom {
 
 // ------------------------------------------------------------ large-N engine
 //
@@ -942,6 +1037,8 @@ __global__ void __launch_bounds__(256) heom_large_kernel(EngineArgs A) {
   const int nwarps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  const int slot = (rank == 0 && lane == 0) ? warp : -1;  // tile 0 is on rank 0; warp w owns units w, w + nwarps, ...
+  const bool lead = (rank == 0 && threadIdx.x == 0);
   unsigned epoch = 0;
 
   for (int li = A.team_first[team]; li < A.team_first[team + 1]; ++li) {
@@ -978,17 +1075,24 @@ __global__ void __launch_bounds__(256) heom_large_kernel(EngineArgs A) {
     const R* ngam = static_cast<const R*>(I.ngam);
     const int Mp = I.Mpad;
     const int ntiles = (I.M + 31) >> 5;
-    if (rank == 0 && threadIdx.x == 0) {
+    EtaAcc<R> ea;
+    EtaRows rows;
+    rows.acc0 = I.acc[0];
+    rows.acc1 = I.acc[1];
+    if (lead) {
       if (I.out_pops)
         for (int a = 0; a < N; ++a)
-          I.out_pops[a] = MIXED ? I.y0[a * N + a] : (double)static_cast<const R*>(I.y)[(a * N + a) * Mp];
+          I.out_pops[a] = MIXED ? ff_to_double(static_cast<const FF*>(I.y0)[a * N + a])
+                                : (double)static_cast<const R*>(I.y)[(a * N + a) * Mp];
       if (I.out_el) {
         I.out_el[0] = I.acc[0];
         I.out_el[1] = I.acc[1];
       }
     }
+    if (lead)
+      for (int k = 0; k < nwarps; ++k) ea.store(I, k);  // zero every running-sum slot of this instance
+    if (!team_barrier(A, epoch)) return;
     R* arr[3] = {static_cast<R*>(I.y), static_cast<R*>(I.wa), static_cast<R*>(I.wb)};
-    double* arr64[3] = {I.y0, I.w0a, I.w0b};
     int64_t next_out = I.out_every, orow = 1;
     for (int64_t t = 0; t < I.nsteps; ++t) {
       const OutStep os{t + 1 == next_out, orow};
@@ -996,17 +1100,19 @@ __global__ void __launch_bounds__(256) heom_large_kernel(EngineArgs A) {
         next_out += I.out_every;
         ++orow;
       }
-      const bool out_step = os.now;
 #pragma unroll 1
       for (int s = 0; s < 4; ++s) {
-        double hd;
+        if (s == 0 && rows.pending >= 0) {
+          if (lead) eta_write_row<R>(I, nwarps, rows.acc0, rows.acc1, rows.pending);
+          rows.pending = -1;
+        }
         int in_sel, out_sel;
-        stage_select(s, I.dt, hd, in_sel, out_sel);
-        const R h = (R)hd;
+        stage_buffers(s, in_sel, out_sel);
+        const StageCoef<R> P = stage_coef<R>(I, s, in_sel, out_sel);
+        const R h = P.h;
         const R* __restrict__ win = arr[in_sel];
         R* __restrict__ wout = arr[out_sel];
         const R* __restrict__ yv = arr[0];
-        double* out64 = arr64[out_sel];
         for (int tl = rank; tl < ntiles; tl += team_size) {
           const int n0 = tl << 5;
           __syncthreads();
@@ -1018,30 +1124,11 @@ __global__ void __launch_bounds__(256) heom_large_kernel(EngineArgs A) {
           const int n = n0 + lane;
           const bool live = n < I.M;
           const bool root = (n == 0);
-          int upa = -1, upb = -1;
           const R ng = live ? ngam[n] : R(0);
           const bool term = live && I.terminator && I.up[n] < 0;
-          if (!MIXED && s == 3 && root && warp == 0) {
-            double e = 0.0, l = 0.0;
-            for (int m = 0; m < N; ++m) {
-              const double x = (double)tile[(m * N + m) * 32];
-              e += cfd[m] * x;
-              l += cfd[N + m] * x;
-            }
-            eta_update(I, e, l, os);
-          }
-          if (MIXED && s == 3 && root && warp == 0) {
-            double e = 0.0, l = 0.0;
-            for (int m = 0; m < N; ++m) {
-              const double x = I.w0a[m * N + m];
-              e += cfd[m] * x;
-              l += cfd[N + m] * x;
-            }
-            eta_update(I, e, l, os);
-          }
-          auto P = [&](int k, int l) -> R { return tile[(k * N + l) * 32 + lane]; };
-          auto S = [&](int k, int l) -> R { return k <= l ? P(k, l) : P(l, k); };
-          auto Aim = [&](int k, int l) -> R { return k < l ? P(l, k) : (k > l ? -P(k, l) : R(0)); };
+          auto Pk = [&](int k, int l) -> R { return tile[(k * N + l) * 32 + lane]; };
+          auto S = [&](int k, int l) -> R { return k <= l ? Pk(k, l) : Pk(l, k); };
+          auto Aim = [&](int k, int l) -> R { return k < l ? Pk(l, k) : (k > l ? -Pk(k, l) : R(0)); };
           for (int u = warp; u < U && live; u += nwarps) {
             const int a = s_units[u].a, b = s_units[u].b;
             R re = R(0), im = R(0);
@@ -1049,7 +1136,7 @@ __global__ void __launch_bounds__(256) heom_large_kernel(EngineArgs A) {
             const int da = da_raw < 0 ? -1 : (da_raw & 0xFFFFFF);
             const R na = da_raw < 0 ? R(0) : R(da_raw >> 24);
             if (a != b) {
-              const R x = P(a, b), yi = P(b, a);
+              const R x = Pk(a, b), yi = Pk(b, a);
               for (int k = 0; k < N; ++k) {
                 const R jak = cf[L::J(N) + a * N + k];
                 const R jkb = cf[L::J(N) + k * N + b];
@@ -1068,8 +1155,8 @@ __global__ void __launch_bounds__(256) heom_large_kernel(EngineArgs A) {
               im -= d * x + c * yi;
               const R al_a = cf[L::alpha(N) + a], be_a = cf[L::beta(N) + a];
               const R al_b = cf[L::alpha(N) + b], be_b = cf[L::beta(N) + b];
-              upa = I.up[a * Mp + n];
-              upb = I.up[b * Mp + n];
+              const int upa = I.up[a * Mp + n];
+              const int upb = I.up[b * Mp + n];
               if (upa >= 0) {
                 re -= win[(b * N + a) * Mp + upa];
                 im += win[(a * N + b) * Mp + upa];
@@ -1078,11 +1165,11 @@ __global__ void __launch_bounds__(256) heom_large_kernel(EngineArgs A) {
                 re += win[(b * N + a) * Mp + upb];
                 im -= win[(a * N + b) * Mp + upb];
               }
+              const int db_raw = I.dn[b * Mp + n];
+              const R nb = db_raw < 0 ? R(0) : R(db_raw >> 24);
               if (term) {
                 const R ca = (na + R(1)) / (ng + cf[L::gam(N) + a]);
-                const int db_raw0 = I.dn[b * Mp + n];
-                const R nb0 = db_raw0 < 0 ? R(0) : R(db_raw0 >> 24);
-                const R cbf = (nb0 + R(1)) / (ng + cf[L::gam(N) + b]);
+                const R cbf = (nb + R(1)) / (ng + cf[L::gam(N) + b]);
                 re += ca * (-al_a * x - be_a * yi) + cbf * (-al_b * x + be_b * yi);
                 im += ca * (-al_a * yi + be_a * x) + cbf * (-al_b * yi - be_b * x);
               }
@@ -1092,17 +1179,15 @@ __global__ void __launch_bounds__(256) heom_large_kernel(EngineArgs A) {
                 re += na * (be_a * yr - al_a * yy);
                 im += na * (al_a * yr + be_a * yy);
               }
-              const int db_raw = I.dn[b * Mp + n];
               if (db_raw >= 0) {
                 const int db = db_raw & 0xFFFFFF;
-                const R nb = R(db_raw >> 24);
                 const R yr = win[(a * N + b) * Mp + db];
                 const R yy = win[(b * N + a) * Mp + db];
                 re += nb * (be_b * yr + al_b * yy);
                 im += nb * (be_b * yy - al_b * yr);
               }
             } else {
-              const R x = P(a, a);
+              const R x = Pk(a, a);
               for (int k = 0; k < N; ++k) {
                 if (k == a) continue;
                 re += R(2) * cf[L::J(N) + a * N + k] * Aim(k, a);
@@ -1111,33 +1196,52 @@ __global__ void __launch_bounds__(256) heom_large_kernel(EngineArgs A) {
               re -= (ng + R(2) * cf[L::ghalf(N) + a]) * x;
               if (da >= 0) re += R(2) * na * cf[L::beta(N) + a] * win[(a * N + a) * Mp + da];
             }
-            // Horner update w = y + h r (root in double for mixed precision)
+            // Horner update w = y + h r (root in float-float for mixed precision)
             const int pr = a * N + b, pi = b * N + a;
             if (MIXED && root) {
-              const double vr = I.y0[pr] + hd * (double)re;
-              out64[pr] = vr;
-              wout[pr * Mp] = (R)vr;
-              if (a != b) {
-                const double vi = I.y0[pi] + hd * (double)im;
-                out64[pi] = vi;
-                wout[pi * Mp] = (R)vi;
-              } else if (s == 3 && I.out_pops && out_step) {
-                I.out_pops[os.row * N + a] = vr;
+              if constexpr (MIXED) {
+                if (a == b && s == 3) ea.add(I, a, P.root_in[pr]);
+                const FF wr = ff_axpy(P.root_y[pr], P.h, P.hl, re);
+                P.root_out[pr] = wr;
+                wout[pr * Mp] = wr.h;
+                if (a != b) {
+                  const FF wi = ff_axpy(P.root_y[pi], P.h, P.hl, im);
+                  P.root_out[pi] = wi;
+                  wout[pi * Mp] = wi.h;
+                } else if (s == 3 && I.out_pops && os.now) {
+                  I.out_pops[os.row * N + a] = ff_to_double(wr);
+                }
               }
             } else {
+              if constexpr (!MIXED) {
+                if (root && a == b && s == 3) ea.add(I, cfd, N, a, (double)Pk(a, a));
+              }
               const R vr = yv[pr * Mp + n] + h * re;
               wout[pr * Mp + n] = vr;
               if (a != b) {
                 wout[pi * Mp + n] = yv[pi * Mp + n] + h * im;
-              } else if (root && s == 3 && I.out_pops && out_step) {
+              } else if (root && s == 3 && I.out_pops && os.now) {
                 I.out_pops[os.row * N + a] = (double)vr;
               }
             }
           }
         }
+        if (s == 3 && slot >= 0 && (os.now || t + 1 == I.nsteps)) ea.store(I, slot);
         if (!team_barrier(A, epoch)) return;
       }
+      if (os.now) rows.pending = os.row;
     }
+    if (lead) {
+      if (rows.pending >= 0) eta_write_row<R>(I, nwarps, rows.acc0, rows.acc1, rows.pending);
+      if (I.nsteps > 0) {
+        double e, l;
+        eta_total<R>(I, nwarps, rows.acc0, rows.acc1, e, l);
+        I.acc[0] = e;
+        I.acc[1] = l;
+      }
+    }
+    if (!team_barrier(A, epoch)) return;
+    if (lead) signal_done(I);
   }
 }
 

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <set>
 #include <cmath>
 #include <deque>
 #include <cstdarg>
@@ -141,8 +142,14 @@ struct PinnedBuf {
 
 // ------------------------------------------------------------- utilities
 
+// The root node of the mixed path is kept in float-float (hi, lo) pairs.
+__device__ __forceinline__ float2 to_ff(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
 template <typename R>
-__global__ void set_root_kernel(R* y, int Mpad, double* y0, const double* rho, int N, double* acc) {
+__global__ void set_root_kernel(R* y, int Mpad, float2* y0, const double* rho, int N, double* acc) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < N * N) {
     const int a = p / N, b = p - (p / N) * N;
@@ -154,7 +161,7 @@ __global__ void set_root_kernel(R* y, int Mpad, double* y0, const double* rho, i
     else
       v = rho[2 * (a * N + a)];
     y[(size_t)p * Mpad] = (R)v;
-    if (y0) y0[p] = v;
+    if (y0) y0[p] = to_ff(v);
   }
   if (p == 0) {
     acc[0] = 0.0;
@@ -164,7 +171,7 @@ __global__ void set_root_kernel(R* y, int Mpad, double* y0, const double* rho, i
 
 // packed element-major state -> full complex matrices [M][N][N]
 template <typename R>
-__global__ void unpack_state_kernel(const R* y, int Mpad, int64_t M, int N, const double* y0, double* out) {
+__global__ void unpack_state_kernel(const R* y, int Mpad, int64_t M, int N, const float2* y0, double* out) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int NN = N * N;
   if (idx >= M * NN) return;
@@ -172,7 +179,7 @@ __global__ void unpack_state_kernel(const R* y, int Mpad, int64_t M, int N, cons
   const int e = (int)(idx - n * NN);
   const int a = e / N, b = e - (e / N) * N;
   auto P = [&](int k, int l) -> double {
-    if (n == 0 && y0) return y0[k * N + l];
+    if (n == 0 && y0) return (double)y0[k * N + l].x + (double)y0[k * N + l].y;
     return (double)y[(size_t)(k * N + l) * Mpad + n];
   };
   double re, im;
@@ -191,7 +198,7 @@ __global__ void unpack_state_kernel(const R* y, int Mpad, int64_t M, int N, cons
 }
 
 template <typename R>
-__global__ void pack_state_kernel(const double* in, R* y, int Mpad, int64_t M, int N, double* y0) {
+__global__ void pack_state_kernel(const double* in, R* y, int Mpad, int64_t M, int N, float2* y0) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int NN = N * N;
   if (idx >= M * NN) return;
@@ -207,7 +214,7 @@ __global__ void pack_state_kernel(const double* in, R* y, int Mpad, int64_t M, i
   else
     v = m[2 * (a * N + a)];
   y[(size_t)p * Mpad + n] = (R)v;
-  if (n == 0 && y0) y0[p] = v;
+  if (n == 0 && y0) y0[p] = to_ff(v);
 }
 
 int launch_blocks(int64_t work, int threads) { return (int)((work + threads - 1) / threads); }
@@ -332,6 +339,24 @@ int validate(const heom_params* p, int idx) {
   return HEOM_OK;
 }
 
+// Horner steps and the eta/loss step factors of one call, in double and as
+// float-float pairs (the mixed kernels run no double-precision arithmetic).
+void fill_steps(Inst& d, double dt, const double* rates /* trap[N], recomb[N] in 1/fs */) {
+  const double h[4] = {0.25 * dt, dt / 3.0, 0.5 * dt, dt};
+  for (int s = 0; s < 4; ++s) {
+    d.hd[s] = h[s];
+    d.hh[s] = (float)h[s];
+    d.hl[s] = (float)(h[s] - (double)d.hh[s]);
+  }
+  for (int a = 0; a < d.N; ++a) {
+    const double et = dt * rates[a], el = dt * rates[d.N + a];
+    d.ec[4 * a] = (float)et;
+    d.ec[4 * a + 1] = (float)(et - (double)d.ec[4 * a]);
+    d.ec[4 * a + 2] = (float)el;
+    d.ec[4 * a + 3] = (float)(el - (double)d.ec[4 * a + 2]);
+  }
+}
+
 int validate_rho(const double* rho, int N) {
   if (!rho) return fail(HEOM_EINVAL, "rho0 is NULL");
   for (int a = 0; a < N; ++a)
@@ -359,6 +384,10 @@ struct Engine {
   std::map<int, LaunchCfg> cfg;  // per N
   bool pageable_args = false;     // stage launch descriptors from pageable memory (servers)
   std::vector<unsigned char> h_args_pageable;
+  // per-instance output destinations and cadences (servers); empty = contiguous buffers
+  std::vector<double*> ovr_pops, ovr_el;
+  std::vector<int*> ovr_done;
+  std::vector<int64_t> ovr_every;
   DevBuf d_args, d_status, d_gsync, d_out;
   PinnedBuf h_args;
   cudaEvent_t args_done = nullptr;
@@ -466,15 +495,14 @@ struct Engine {
         }
       }
     } else {
+      // many hierarchies: small teams so that every instance runs at once
       c.mode = 0;
-      c.block = 256;
-      c.G = 1;
-      c.team_ctas = 4;
-      if (prec == HEOM_FP32_MIXED && heom::smem_dyn_bytes(N, smem_slice(Mmax, 8)) <= max_dyn_smem()) {
+      c.block = max_block();
+      c.G = 2;
+      c.team_ctas = 2;
+      if (prec == HEOM_FP32_MIXED && heom::smem_dyn_bytes(N, smem_slice(Mmax, 1)) <= max_dyn_smem()) {
         c.mode = 2;
-        c.team_ctas = 8;
-        c.block = 256;
-        c.G = 2;
+        c.team_ctas = 1;
       }
     }
     return c;
@@ -540,7 +568,8 @@ struct Engine {
     TRY(in->y.alloc(arr, hooks));
     TRY(in->wa.alloc(arr, hooks));
     TRY(in->wb.alloc(arr, hooks));
-    TRY(in->root64.alloc(3 * sizeof(double) * p.N * p.N, hooks));
+    // three root buffers of N*N float-float pairs, then the 32 (eta, loss) partial-sum slots
+    TRY(in->root64.alloc(3 * 8 * p.N * p.N + 32 * 16, hooks));
     TRY(in->coef.alloc(in->coef_host.size(), hooks));
     TRY(in->acc.alloc(4 * sizeof(double), hooks));
     TRY(in->stage.alloc(2 * sizeof(double) * p.N * p.N, hooks));
@@ -552,10 +581,12 @@ struct Engine {
     return HEOM_OK;
   }
 
-  double* root_ptr(const Instance& in, int which) const {
+  // root buffer `which` (0: y0, 1: wa0, 2: wb0) of the mixed path, N*N float2
+  float2* root_ptr(const Instance& in, int which) const {
     if (prec == HEOM_FP64) return nullptr;
-    return in.root64.as<double>() + (size_t)which * in.N * in.N;
+    return in.root64.as<float2>() + (size_t)which * in.N * in.N;
   }
+  void* parts_ptr(const Instance& in) const { return in.root64.as<unsigned char>() + (size_t)3 * 8 * in.N * in.N; }
 
   int set_rho0_device(int i, const double* d_rho) {
     Instance& in = *inst[i];
@@ -611,6 +642,10 @@ struct Engine {
       d.y0 = root_ptr(in, 0);
       d.w0a = root_ptr(in, 1);
       d.w0b = root_ptr(in, 2);
+      d.parts = parts_ptr(in);
+      fill_steps(d, dt[i], reinterpret_cast<const double*>(in.coef_host.data() +
+                                                           (prec == HEOM_FP64 ? CoefLayout<double>::dbl_offset(in.N)
+                                                                              : CoefLayout<float>::dbl_offset(in.N))));
       d.coef = in.coef.p;
       d.ngam = in.ngam.p;
       d.acc = in.acc.as<double>();
@@ -618,6 +653,12 @@ struct Engine {
       d.out_el = d_el ? d_el + 2 * row_off : nullptr;
       d.nsteps = nsteps[i];
       d.out_every = out_every;
+      if (!ovr_pops.empty()) {
+        d.out_pops = ovr_pops[i];
+        d.out_el = ovr_el[i];
+        d.done = ovr_done[i];
+        d.out_every = ovr_every[i];
+      }
       d.dt = dt[i];
       const int64_t nout = nout_of(nsteps[i], out_every);
       pop_off += nout * in.N;
@@ -1361,7 +1402,7 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
   const size_t o_coef = align256(o_acc + 4 * sizeof(double));
   const size_t coef_bytes = fp64 ? CoefLayout<double>::bytes(N) : CoefLayout<float>::bytes(N);
   const size_t o_root = align256(o_coef + coef_bytes);
-  const size_t o_up = align256(o_root + 3 * sizeof(double) * N * N);
+  const size_t o_up = align256(o_root + 3 * 8 * N * N + 32 * 16);
   const size_t tab_bytes = sizeof(int32_t) * (size_t)N * Mpad;
   const size_t o_dn = align256(o_up + tab_bytes);
   const size_t o_ngam = align256(o_dn + tab_bytes);
@@ -1421,10 +1462,11 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
   d.y = base + o_y;
   d.wa = base + o_wa;
   d.wb = base + o_wb;
-  double* root = reinterpret_cast<double*>(base + o_root);
+  float2* root = reinterpret_cast<float2*>(base + o_root);
   d.y0 = fp64 ? nullptr : root;
   d.w0a = fp64 ? nullptr : root + N * N;
   d.w0b = fp64 ? nullptr : root + 2 * N * N;
+  d.parts = base + o_root + 3 * 8 * N * N;
   d.coef = base + o_coef;
   d.ngam = base + o_ngam;
   d.acc = reinterpret_cast<double*>(base + o_acc);
@@ -1433,6 +1475,8 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
   d.nsteps = nsteps;
   d.out_every = out_every;
   d.dt = dt_fs;
+  fill_steps(d, dt_fs, reinterpret_cast<const double*>(h_coef + (fp64 ? CoefLayout<double>::dbl_offset(N)
+                                                                       : CoefLayout<float>::dbl_offset(N))));
   const int32_t team[4] = {0, 1, 0, 0};  // team_first = {0, 1}, team_list = {0}
 
   // one team (a thread-block cluster) for the single hierarchy
@@ -1481,8 +1525,8 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
     set_root_kernel<double><<<launch_blocks(NN, 128), 128, 0, stream>>>(static_cast<double*>(d.y), Mpad, nullptr,
                                                                        d_rho0, N, d.acc);
   else
-    set_root_kernel<float><<<launch_blocks(NN, 128), 128, 0, stream>>>(static_cast<float*>(d.y), Mpad, d.y0, d_rho0,
-                                                                      N, d.acc);
+    set_root_kernel<float><<<launch_blocks(NN, 128), 128, 0, stream>>>(static_cast<float*>(d.y), Mpad,
+                                                                      static_cast<float2*>(d.y0), d_rho0, N, d.acc);
   CUDA_TRY(cudaGetLastError());
 
   EngineArgs A;
@@ -1503,7 +1547,8 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
                                                                              nullptr, d_rho_out);
     else
       unpack_state_kernel<float><<<launch_blocks(NN, 128), 128, 0, stream>>>(static_cast<float*>(d.y), Mpad, 1, N,
-                                                                            d.y0, d_rho_out);
+                                                                            static_cast<const float2*>(d.y0),
+                                                                            d_rho_out);
     CUDA_TRY(cudaGetLastError());
   }
   return HEOM_OK;
@@ -1512,31 +1557,37 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
 // ------------------------------------------------------------------ server
 //
 // Continuous batching of propagation requests of different sizes.  The server
-// owns one device buffer (its memory budget) and a pool of slots, each a CUDA
-// stream.  heom_server_progress() retires requests whose work has finished
-// (their memory goes back to the budget, their slot is free) and admits queued
-// requests in arrival order while a slot is free and their state fits in the
-// budget.  Each admitted request runs as its own persistent launch (one
-// thread-block cluster) on its slot's stream, so requests that arrive while
-// others run overlap with them on the device.  Node tables are cached per
-// (N, K) for the server's lifetime; the state stays resident until retirement.
+// owns one device buffer (its device-memory budget), one pinned host buffer
+// for results, and a few CUDA streams.  Each heom_server_progress() call
+//   * marks finished every running request whose done flag the GPU has set
+//     (its populations and eta rows are written straight into pinned host
+//     memory by the kernel, so they are complete at that point),
+//   * retires every launch whose device work has ended (its device memory goes
+//     back to the budget, its stream is free), and
+//   * admits the queued requests, in arrival order, that fit in the budget into
+//     one new launch on a free stream: one thread block per request, all of them
+//     running concurrently with each other and with earlier launches.
+// So requests that arrive while others run are admitted at the next progress
+// call and overlap with them on the device; each request completes on its own
+// as soon as its block finishes.  Node tables are cached per (N, K).
 
 namespace {
 
-// First-fit allocator over one device buffer, with coalescing on release.
+// First-fit allocator over one contiguous buffer, with coalescing on release.
 struct Arena {
-  DevBuf buf;
+  unsigned char* base = nullptr;
+  size_t bytes = 0;
   std::map<size_t, size_t> free_blocks;  // offset -> size
   std::map<size_t, size_t> used_blocks;  // offset -> size
   size_t in_use = 0;
 
-  int init(size_t bytes) {
-    TRY(buf.alloc(bytes, Hooks()));
+  void init(void* b, size_t n) {
+    base = static_cast<unsigned char*>(b);
+    bytes = n;
     free_blocks.clear();
     used_blocks.clear();
-    free_blocks[0] = buf.bytes;
+    free_blocks[0] = n;
     in_use = 0;
-    return HEOM_OK;
   }
   void* alloc(size_t n) {
     n = (n + 255) / 256 * 256;
@@ -1547,13 +1598,13 @@ struct Arena {
       if (sz > n) free_blocks[off + n] = sz - n;
       used_blocks[off] = n;
       in_use += n;
-      return static_cast<unsigned char*>(buf.p) + off;
+      return base + off;
     }
     return nullptr;
   }
   void release(void* p) {
     if (!p) return;
-    const size_t off = static_cast<size_t>(static_cast<unsigned char*>(p) - static_cast<unsigned char*>(buf.p));
+    const size_t off = static_cast<size_t>(static_cast<unsigned char*>(p) - base);
     auto u = used_blocks.find(off);
     if (u == used_blocks.end()) return;
     size_t start = off, size = u->second;
@@ -1594,31 +1645,35 @@ struct Request {
   double dt = 1.0;
   int64_t nsteps = 0, out_every = 1, nout = 1;
   size_t need = 0;
-  std::unique_ptr<Engine> eng;
-  void* d_out = nullptr;
-  int slot = -1;
+  unsigned char* host = nullptr;  // pinned: pops [nout*N], (eta, loss) [nout*2], done flag
+  int launch = -1;                // index of the launch running it
+  bool released = false;          // released by the caller while its launch still runs
   std::vector<double> pops, el;
   double t_submit = 0, t_start = 0, t_done = 0;
   std::string err;
+  size_t host_bytes() const { return sizeof(double) * (size_t)nout * (p.N + 2) + 64; }
+  double* h_pops() const { return reinterpret_cast<double*>(host); }
+  double* h_el() const { return reinterpret_cast<double*>(host) + nout * p.N; }
+  int* h_done() const { return reinterpret_cast<int*>(host + sizeof(double) * (size_t)nout * (p.N + 2)); }
 };
 
-struct Slot {
+struct Launch {
   cudaStream_t s = nullptr;
   cudaEvent_t done = nullptr;
-  PinnedBuf host;
-  int64_t req = -1;
+  std::unique_ptr<Engine> eng;
+  std::vector<int64_t> reqs;
+  bool busy = false;
 };
 
 // Device bytes a request needs, rounded like the arena rounds (tables counted
 // when they are not cached yet).
-size_t request_bytes(const heom_params& p, int64_t nout, bool tables_cached) {
+size_t request_bytes(const heom_params& p, bool tables_cached) {
   auto r = [](size_t v) { return (v + 255) / 256 * 256; };
   const size_t rs = p.precision == HEOM_FP64 ? 8 : 4;
   const int64_t M = heom::num_nodes(p.N, p.K);
   const size_t Mpad = (size_t)((M + 31) / 32 * 32);
   const size_t NN = (size_t)p.N * p.N;
-  size_t b = 3 * r(NN * Mpad * rs) + r(Mpad * rs) + r(3 * 8 * NN) + r(4096) + r(4 * 8) + r(2 * 8 * NN) + 2 * r(16) +
-             r(2 * (sizeof(Inst) + 64)) + r(8 * (size_t)nout * (p.N + 2));
+  size_t b = 3 * r(NN * Mpad * rs) + r(Mpad * rs) + r(3 * 8 * NN + 32 * 16) + r(4096) + r(4 * 8) + r(2 * 8 * NN);
   if (!tables_cached) b += 2 * r(4 * (size_t)p.N * Mpad);
   return b;
 }
@@ -1627,9 +1682,12 @@ size_t request_bytes(const heom_params& p, int64_t nout, bool tables_cached) {
 
 struct heom_server {
   std::mutex mu;
-  Arena arena;
+  DevBuf dev;
+  Arena arena;   // device budget
+  void* host_mem = nullptr;
+  Arena harena;  // pinned host results
   Hooks hooks;
-  std::vector<Slot> slots;
+  std::vector<Launch> launches;
   std::map<int64_t, std::unique_ptr<Request>> reqs;
   std::deque<int64_t> queue;
   int64_t next_id = 1;
@@ -1637,105 +1695,157 @@ struct heom_server {
   int device = 0;
 
   ~heom_server() {
-    for (auto& s : slots)
-      if (s.s) cudaStreamSynchronize(s.s);
-    reqs.clear();     // engines give their blocks back to the arena
+    for (auto& l : launches)
+      if (l.s) cudaStreamSynchronize(l.s);
+    for (auto& l : launches) l.eng.reset();  // engines give their blocks back to the arena
     tables.reset();
-    for (auto& s : slots) {
-      if (s.done) cudaEventDestroy(s.done);
-      if (s.s) cudaStreamDestroy(s.s);
+    for (auto& l : launches) {
+      if (l.done) cudaEventDestroy(l.done);
+      if (l.s) cudaStreamDestroy(l.s);
     }
+    if (host_mem) cudaFreeHost(host_mem);
   }
 
-  LaunchCfg launch_for(int N, int64_t M) const {
+  // One thread block per request; the hierarchy lives in the block's shared
+  // memory when every request of the group fits.
+  static LaunchCfg launch_for(const Engine& e, int N, int64_t Mmax) {
     LaunchCfg c;
     c.mode = 0;
-    c.block = 256;
-    c.G = N >= 4 ? 8 : 2;
-    const int64_t units = ((M + 31) / 32) * c.G;
-    int ctas = (int)std::min<int64_t>(8, std::max<int64_t>(1, units / 16));
-    int p2 = 1;
-    while (p2 < ctas) p2 <<= 1;
-    c.team_ctas = std::min(8, p2);
+    c.team_ctas = 1;
+    c.block = e.max_block();
+    c.G = 2;
+    if (e.prec == HEOM_FP32_MIXED && N <= heom::kMaxSmallN &&
+        heom::smem_dyn_bytes(N, Engine::smem_slice(Mmax, 1)) <= e.max_dyn_smem())
+      c.mode = 2;
     return c;
   }
 
-  int start(Request& q, int si) {
-    Slot& sl = slots[si];
+  int start_launch(int li, const std::vector<int64_t>& ids) {
+    Launch& L = launches[li];
     auto eng = std::make_unique<Engine>();
     eng->pageable_args = true;
-    int rc = eng->init(&q.p, 1, sl.s, &hooks, tables);
+    std::vector<heom_params> ps;
+    for (int64_t id : ids) ps.push_back(reqs[id]->p);
+    int rc = eng->init(ps.data(), (int)ps.size(), L.s, &hooks, tables);
     if (rc != HEOM_OK) return rc;
-    eng->cfg[q.p.N] = launch_for(q.p.N, eng->inst[0]->M);
-    TRY(eng->set_rho0_host(0, q.rho0.data()));
-    const size_t out_bytes = sizeof(double) * (size_t)q.nout * (q.p.N + 2);
-    q.d_out = arena.alloc(out_bytes);
-    if (!q.d_out) return fail(HEOM_ENOMEM, "server budget exhausted (outputs)");
-    double* d_pops = static_cast<double*>(q.d_out);
-    double* d_el = d_pops + q.nout * q.p.N;
-    rc = eng->propagate(&q.dt, &q.nsteps, q.out_every, d_pops, d_el);
+    std::map<int, int64_t> mmax;
+    for (auto& in : eng->inst) mmax[in->N] = std::max<int64_t>(mmax[in->N], in->M);
+    for (auto& kv : mmax) eng->cfg[kv.first] = launch_for(*eng, kv.first, kv.second);
+    std::vector<double> dts;
+    std::vector<int64_t> steps;
+    for (size_t k = 0; k < ids.size(); ++k) {
+      Request& q = *reqs[ids[k]];
+      TRY(eng->set_rho0_host((int)k, q.rho0.data()));
+      *q.h_done() = 0;
+      eng->ovr_pops.push_back(q.h_pops());
+      eng->ovr_el.push_back(q.h_el());
+      eng->ovr_done.push_back(q.h_done());
+      eng->ovr_every.push_back(q.out_every);
+      dts.push_back(q.dt);
+      steps.push_back(q.nsteps);
+    }
+    rc = eng->propagate(dts.data(), steps.data(), 1, nullptr, nullptr);
     if (rc != HEOM_OK) return rc;
-    TRY(sl.host.ensure(out_bytes));
-    CUDA_TRY(cudaMemcpyAsync(sl.host.p, q.d_out, out_bytes, cudaMemcpyDeviceToHost, sl.s));
-    CUDA_TRY(cudaEventRecord(sl.done, sl.s));
-    q.eng = std::move(eng);
-    q.slot = si;
-    q.state = kReqRunning;
-    q.t_start = now_s();
-    sl.req = q.id;
+    CUDA_TRY(cudaEventRecord(L.done, L.s));
+    const double t = now_s();
+    for (int64_t id : ids) {
+      Request& q = *reqs[id];
+      q.state = kReqRunning;
+      q.launch = li;
+      q.t_start = t;
+    }
+    L.eng = std::move(eng);
+    L.reqs = ids;
+    L.busy = true;
     return HEOM_OK;
   }
 
   int progress(int32_t* completed) {
     int done = 0;
-    for (size_t si = 0; si < slots.size(); ++si) {
-      Slot& sl = slots[si];
-      if (sl.req < 0) continue;
-      cudaError_t e = cudaEventQuery(sl.done);
-      if (e == cudaErrorNotReady) continue;
-      Request& q = *reqs[sl.req];
-      if (e != cudaSuccess) {
-        q.state = kReqFailed;
-        q.err = cudaGetErrorString(e);
-        cudaGetLastError();
-      } else {
-        const double* h = static_cast<const double*>(sl.host.p);
-        q.pops.assign(h, h + q.nout * q.p.N);
-        q.el.assign(h + q.nout * q.p.N, h + q.nout * (q.p.N + 2));
-        q.state = kReqDone;
-      }
-      q.t_done = now_s();
-      q.eng.reset();
-      arena.release(q.d_out);
-      q.d_out = nullptr;
-      q.slot = -1;
-      sl.req = -1;
-      ++done;
-    }
-    // admit in arrival order while a slot is free and the state fits
-    while (!queue.empty()) {
-      int si = -1;
-      for (size_t k = 0; k < slots.size(); ++k)
-        if (slots[k].req < 0) {
-          si = (int)k;
-          break;
+    // requests whose block has finished
+    for (auto& L : launches) {
+      if (!L.busy) continue;
+      for (int64_t id : L.reqs) {
+        Request& q = *reqs[id];
+        if (q.state != kReqRunning) continue;
+        if (*reinterpret_cast<volatile int*>(q.h_done()) != 0) {
+          q.pops.assign(q.h_pops(), q.h_pops() + q.nout * q.p.N);
+          q.el.assign(q.h_el(), q.h_el() + 2 * q.nout);
+          q.state = kReqDone;
+          q.t_done = now_s();
+          ++done;
         }
-      if (si < 0) break;
-      Request& q = *reqs[queue.front()];
-      const bool cached = tables->count(std::make_pair(q.p.N, q.p.K)) != 0;
-      if (arena.in_use + request_bytes(q.p, q.nout, cached) > arena.buf.bytes) break;
-      int rc = start(q, si);
-      if (rc != HEOM_OK) {
-        q.eng.reset();
-        if (q.d_out) arena.release(q.d_out);
-        q.d_out = nullptr;
-        if (rc == HEOM_ENOMEM) break;  // wait for memory to free up
-        q.state = kReqFailed;
-        q.err = t_err;
-        queue.pop_front();
-        continue;
       }
-      queue.pop_front();
+    }
+    // launches whose device work has ended
+    for (auto& L : launches) {
+      if (!L.busy) continue;
+      cudaError_t e = cudaEventQuery(L.done);
+      if (e == cudaErrorNotReady) continue;
+      if (e != cudaSuccess) cudaGetLastError();
+      for (int64_t id : L.reqs) {
+        Request& q = *reqs[id];
+        if (q.state == kReqRunning) {  // finished without a flag: the launch failed
+          q.state = kReqFailed;
+          q.err = e != cudaSuccess ? cudaGetErrorString(e) : "launch ended before the request finished";
+          q.t_done = now_s();
+          ++done;
+        }
+        harena.release(q.host);
+        q.host = nullptr;
+        q.launch = -1;
+      }
+      for (int64_t id : L.reqs)
+        if (reqs[id]->released) reqs.erase(id);
+      L.eng.reset();
+      L.reqs.clear();
+      L.busy = false;
+    }
+    // admit queued requests into one launch on a free stream
+    int li = -1;
+    for (size_t k = 0; k < launches.size(); ++k)
+      if (!launches[k].busy) {
+        li = (int)k;
+        break;
+      }
+    if (li >= 0 && !queue.empty()) {
+      std::vector<int64_t> ids;
+      size_t budget = arena.in_use;
+      std::set<std::pair<int, int>> new_tables;
+      while (!queue.empty()) {
+        Request& q = *reqs[queue.front()];
+        const auto key = std::make_pair(q.p.N, q.p.K);
+        const bool cached = tables->count(key) != 0 || new_tables.count(key) != 0;
+        const size_t need = request_bytes(q.p, cached) + 8192;
+        if (budget + need > arena.bytes) break;
+        if (!ids.empty() && reqs[ids[0]]->p.precision != q.p.precision) break;
+        q.host = static_cast<unsigned char*>(harena.alloc(q.host_bytes()));
+        if (!q.host) break;
+        budget += need;
+        new_tables.insert(key);
+        ids.push_back(q.id);
+        queue.pop_front();
+      }
+      if (!ids.empty()) {
+        const int rc = start_launch(li, ids);
+        if (rc != HEOM_OK) {
+          // put them back at the head of the queue (in order) and report
+          Launch& L = launches[li];
+          L.eng.reset();
+          for (auto it = ids.rbegin(); it != ids.rend(); ++it) {
+            Request& q = *reqs[*it];
+            harena.release(q.host);
+            q.host = nullptr;
+            if (rc == HEOM_ENOMEM) {
+              queue.push_front(*it);
+            } else {
+              q.state = kReqFailed;
+              q.err = t_err;
+            }
+          }
+          if (rc != HEOM_ENOMEM) return rc;
+        }
+      }
     }
     if (completed) *completed = done;
     return HEOM_OK;
@@ -1744,11 +1854,12 @@ struct heom_server {
 
 extern "C" {
 
-int heom_server_create(size_t device_bytes, int32_t slots, heom_server** out) {
+int heom_server_create(size_t device_bytes, size_t host_bytes, int32_t streams, heom_server** out) {
   if (!out) return fail(HEOM_EINVAL, "out is NULL");
   *out = nullptr;
-  if (slots < 1 || slots > 1024) return fail(HEOM_EINVAL, "slots must be 1..1024");
+  if (streams < 1 || streams > 64) return fail(HEOM_EINVAL, "streams must be 1..64");
   if (device_bytes < (1u << 20)) return fail(HEOM_EINVAL, "device_bytes must be at least 1 MiB");
+  if (host_bytes < (1u << 16)) return fail(HEOM_EINVAL, "host_bytes must be at least 64 KiB");
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev < 1) {
@@ -1757,14 +1868,17 @@ int heom_server_create(size_t device_bytes, int32_t slots, heom_server** out) {
   }
   auto s = std::make_unique<heom_server>();
   CUDA_TRY(cudaGetDevice(&s->device));
-  TRY(s->arena.init(device_bytes));
+  TRY(s->dev.alloc(device_bytes, Hooks()));
+  s->arena.init(s->dev.p, s->dev.bytes);
+  CUDA_TRY(cudaHostAlloc(&s->host_mem, host_bytes, cudaHostAllocMapped | cudaHostAllocPortable));
+  s->harena.init(s->host_mem, host_bytes);
   s->hooks.alloc = arena_alloc_hook;
   s->hooks.release = arena_free_hook;
   s->hooks.user = &s->arena;
-  s->slots.resize(slots);
-  for (auto& sl : s->slots) {
-    CUDA_TRY(cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking));
-    CUDA_TRY(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+  s->launches.resize(streams);
+  for (auto& l : s->launches) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&l.s, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming));
   }
   *out = s.release();
   return HEOM_OK;
@@ -1800,10 +1914,12 @@ int heom_server_submit(heom_server* s, const heom_params* params, const double* 
   q->nsteps = nsteps;
   q->out_every = out_every;
   q->nout = nsteps / out_every + 1;
-  q->need = request_bytes(q->p, q->nout, false);
-  if (q->need > s->arena.buf.bytes)
-    return fail(HEOM_ENOMEM, "request needs %zu device bytes; the server's budget is %zu", q->need,
-                s->arena.buf.bytes);
+  q->need = request_bytes(q->p, false) + 8192;
+  if (q->need > s->arena.bytes)
+    return fail(HEOM_ENOMEM, "request needs %zu device bytes; the server's budget is %zu", q->need, s->arena.bytes);
+  if (q->host_bytes() > s->harena.bytes)
+    return fail(HEOM_ENOMEM, "request needs %zu bytes of pinned host memory for its results; the server has %zu",
+                q->host_bytes(), s->harena.bytes);
   q->id = s->next_id++;
   q->t_submit = now_s();
   *request_id = q->id;
@@ -1825,7 +1941,7 @@ int heom_server_status(heom_server* s, int64_t id, int32_t* state) {
   if (!s || !state) return fail(HEOM_EINVAL, "server or state is NULL");
   std::lock_guard<std::mutex> lk(s->mu);
   auto it = s->reqs.find(id);
-  if (it == s->reqs.end()) return fail(HEOM_EINVAL, "unknown request %lld", (long long)id);
+  if (it == s->reqs.end() || it->second->released) return fail(HEOM_EINVAL, "unknown request %lld", (long long)id);
   *state = it->second->state;
   return HEOM_OK;
 }
@@ -1855,10 +1971,14 @@ int heom_server_release(heom_server* s, int64_t id) {
   if (!s) return fail(HEOM_EINVAL, "server is NULL");
   std::lock_guard<std::mutex> lk(s->mu);
   auto it = s->reqs.find(id);
-  if (it == s->reqs.end()) return fail(HEOM_EINVAL, "unknown request %lld", (long long)id);
+  if (it == s->reqs.end() || it->second->released) return fail(HEOM_EINVAL, "unknown request %lld", (long long)id);
   const int st = it->second->state;
   if (st == kReqQueued || st == kReqRunning) return fail(HEOM_EINVAL, "request %lld is still active", (long long)id);
-  s->reqs.erase(it);
+  if (it->second->host) {
+    it->second->released = true;  // its launch still runs; forgotten when the launch retires
+  } else {
+    s->reqs.erase(it);
+  }
   return HEOM_OK;
 }
 
@@ -1882,8 +2002,8 @@ int heom_server_stats(heom_server* s, int64_t* queued, int64_t* running, int64_t
   if (!s) return fail(HEOM_EINVAL, "server is NULL");
   std::lock_guard<std::mutex> lk(s->mu);
   int64_t r = 0;
-  for (auto& sl : s->slots)
-    if (sl.req >= 0) ++r;
+  for (auto& kv : s->reqs)
+    if (kv.second->state == kReqRunning) ++r;
   if (queued) *queued = (int64_t)s->queue.size();
   if (running) *running = r;
   if (bytes_in_use) *bytes_in_use = (int64_t)s->arena.in_use;

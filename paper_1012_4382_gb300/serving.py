@@ -26,7 +26,7 @@ def _lib():
         i64 = ctypes.c_int64
         dp = ctypes.POINTER(ctypes.c_double)
         sig = {
-            "heom_server_create": [ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(vp)],
+            "heom_server_create": [ctypes.c_size_t, ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(vp)],
             "heom_server_submit": [vp, ctypes.POINTER(heom._Params), dp, ctypes.c_double, i64, i64,
                                    ctypes.POINTER(i64)],
             "heom_server_progress": [vp, ctypes.POINTER(ctypes.c_int32)],
@@ -47,11 +47,13 @@ def _lib():
 
 
 class Server:
-    """Continuous-batching server: a device-memory budget and `slots` streams."""
+    """Continuous-batching server: a device-memory budget, a pinned host
+    buffer for results and `streams` CUDA streams (concurrent launches)."""
 
-    def __init__(self, device_bytes: int = 4 << 30, slots: int = 32):
+    def __init__(self, device_bytes: int = 4 << 30, host_bytes: int = 64 << 20, streams: int = 8):
         self._h = ctypes.c_void_p()
-        heom._check(_lib().heom_server_create(int(device_bytes), int(slots), ctypes.byref(self._h)))
+        heom._check(_lib().heom_server_create(int(device_bytes), int(host_bytes), int(streams),
+                                              ctypes.byref(self._h)))
         self._info = {}
 
     def close(self):
@@ -114,11 +116,11 @@ class Server:
         return {"queued": q.value, "running": r.value, "bytes_in_use": b.value}
 
 
-def run_trace(trace, precision="fp32", device_bytes=8 << 30, slots=64, keep_results=False, time_limit_s=None):
+def run_trace(trace, precision="fp32", device_bytes=8 << 30, streams=8, keep_results=False, time_limit_s=None):
     """Replays `trace` (dicts with arrival_s, params, rho0, dt, nsteps,
     out_every) against a fresh server in real time.  Latency of a request =
     time from its scheduled arrival to the progress call that saw it finish."""
-    srv = Server(device_bytes, slots)
+    srv = Server(device_bytes, 256 << 20, streams)
     order = sorted(range(len(trace)), key=lambda i: trace[i]["arrival_s"])
     t0 = time.perf_counter()
     nxt = 0
@@ -172,7 +174,7 @@ def run_trace(trace, precision="fp32", device_bytes=8 << 30, slots=64, keep_resu
         "mean_latency_s": float(np.mean(lat)),
         "wall_s": wall,
         "max_concurrent": max_running,
-        "slots": slots,
+        "streams": streams,
         "device_bytes": device_bytes,
     }
     if keep_results:

@@ -41,12 +41,12 @@ def _drain(srv, ids, timeout=120.0):
 def test_results_alone_equal_results_in_the_mix(precision):
     reqs = _requests()
     alone = []
-    with serving.Server(device_bytes=1 << 30, slots=1) as srv:
+    with serving.Server(device_bytes=1 << 30, streams=1) as srv:
         for w in reqs:
             i = srv.submit(w["params"], w["rho0"], w["dt"], w["nsteps"], w["out_every"], precision)
             _drain(srv, [i])
             alone.append(srv.result(i))
-    with serving.Server(device_bytes=1 << 30, slots=8) as srv:
+    with serving.Server(device_bytes=1 << 30, streams=8) as srv:
         ids = [srv.submit(w["params"], w["rho0"], w["dt"], w["nsteps"], w["out_every"], precision) for w in reqs]
         seen_running = 0
         t0 = time.time()
@@ -72,7 +72,7 @@ def test_admission_waits_for_memory():
     need = max(heom.num_nodes(w["params"]["N"], w["params"]["K"]) for w in reqs)
     # a budget that holds roughly one of the larger requests at a time
     budget = max(1 << 20, int(need * 64 * 4 * 3 * 1.6) + (1 << 18))
-    with serving.Server(device_bytes=budget, slots=8) as srv:
+    with serving.Server(device_bytes=budget, streams=8) as srv:
         ids = []
         for w in reqs:
             try:
@@ -87,7 +87,7 @@ def test_admission_waits_for_memory():
 
 def test_rejections_and_cancellation():
     w = workloads.fmo_trap(K=8)
-    with serving.Server(device_bytes=1 << 20, slots=2) as srv:
+    with serving.Server(device_bytes=1 << 20, streams=2) as srv:
         with pytest.raises(heom.HeomError) as e:  # can never fit in 1 MiB
             srv.submit(w["params"], w["rho0"], 1.0, 100, 10)
         assert e.value.code == heom.ENOMEM
@@ -117,6 +117,6 @@ def test_trace_replay_reports_latency():
     tr = workloads.serving_trace(count=40, rate_per_s=400.0)
     for w in tr:
         w["nsteps"] = min(w["nsteps"], 1500)
-    r = serving.run_trace(tr, "fp32", device_bytes=2 << 30, slots=16)
+    r = serving.run_trace(tr, "fp32", device_bytes=2 << 30, streams=8)
     assert r["completed"] == 40
     assert 0 < r["p50_latency_s"] <= r["p99_latency_s"]
