@@ -67,6 +67,10 @@ def _load():
             lib.oracle_propagate.restype = ctypes.c_int
             lib.oracle_propagate.argtypes = [ctypes.POINTER(_Params), dp, ctypes.c_double, ctypes.c_longlong,
                                              ctypes.c_longlong, dp, dp, dp, dp, dp, dp]
+            lib.oracle_propagate_ex.restype = ctypes.c_int
+            lib.oracle_propagate_ex.argtypes = [ctypes.POINTER(_Params), dp, ctypes.c_double, ctypes.c_longlong,
+                                                ctypes.c_longlong, ctypes.c_double, dp, dp, dp, dp, dp, dp, dp,
+                                                ctypes.POINTER(ctypes.c_longlong)]
             lib.oracle_num_threads.restype = ctypes.c_int
             lib.oracle_set_threads.argtypes = [ctypes.c_int]
             _lib = lib
@@ -146,15 +150,19 @@ def rhs(params: dict, state: np.ndarray) -> np.ndarray:
     return out
 
 
-def propagate(params: dict, rho0, dt_fs: float, nsteps: int, out_every: int = 1, want_state: bool = False) -> dict:
-    """Classic RK4 propagation; see oracle_propagate in heom_oracle.c.
+def propagate(params: dict, rho0, dt_fs: float, nsteps: int, out_every: int = 1, want_state: bool = False,
+              stop_trace: float = 0.0) -> dict:
+    """Classic RK4 propagation; see oracle_propagate_ex in heom_oracle.c.
 
     ``params`` keys: N, K, H (N x N complex, cm^-1), lam, gam (cm^-1, scalar or
     per site), T (K), trap, recomb (ps^-1 per site, optional), terminator
     (0/1), add_reorg (0/1).
     Returns a dict with pops [nout, N], trace [nout], eta [nout], loss [nout],
+    tmean [nout] (trapping time <t> up to each row, fs), steps_done,
     rho [N, N] complex, and with ``want_state`` the full final state
-    [nodes, N+2, N+2] plus the node multi-indices.
+    [nodes, N+2, N+2] plus the node multi-indices.  ``stop_trace`` > 0 ends
+    the run after the first step whose site population is below it (rows
+    after the stop are NaN).
     """
     keep = _Keep(params)
     N, K = int(params["N"]), int(params["K"])
@@ -163,17 +171,22 @@ def propagate(params: dict, rho0, dt_fs: float, nsteps: int, out_every: int = 1,
     trace = np.zeros(nout)
     eta = np.zeros(nout)
     loss = np.zeros(nout)
+    tmean = np.zeros(nout)
+    done = ctypes.c_longlong(0)
     rho = np.zeros((N, N), dtype=np.complex128)
     r0 = _cplx_interleaved(rho0, N)
     state = None
     if want_state:
         state = np.zeros((num_nodes(N, K), N + 2, N + 2), dtype=np.complex128)
-    rc = _load().oracle_propagate(ctypes.byref(keep.c), _dptr(r0), float(dt_fs), int(nsteps), int(out_every),
-                                  _dptr(pops), _dptr(trace), _dptr(eta), _dptr(loss), _dptr(rho.view(np.float64)),
-                                  _dptr(state.view(np.float64)) if state is not None else _dptr(None))
+    rc = _load().oracle_propagate_ex(ctypes.byref(keep.c), _dptr(r0), float(dt_fs), int(nsteps), int(out_every),
+                                     float(stop_trace), _dptr(pops), _dptr(trace), _dptr(eta), _dptr(loss),
+                                     _dptr(tmean), _dptr(rho.view(np.float64)),
+                                     _dptr(state.view(np.float64)) if state is not None else _dptr(None),
+                                     ctypes.byref(done))
     if rc != 0:
         raise RuntimeError("oracle_propagate failed (bad input or out of memory)")
-    out = {"pops": pops, "trace": trace, "eta": eta, "loss": loss, "rho": rho}
+    out = {"pops": pops, "trace": trace, "eta": eta, "loss": loss, "tmean": tmean, "steps_done": done.value,
+           "rho": rho}
     if want_state:
         out["state"] = state
         out["multi"] = multi_indices(N, K)

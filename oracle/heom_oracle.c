@@ -33,7 +33,14 @@
  *     |n| = N_max (end of App. A2);
  *   * classic 4th-order Runge-Kutta in time (App. B);
  *   * the efficiency eta = <RC| rho |RC> (Eq. eta) read off the RC element of
- *     rho itself, and the radiative loss read off <0| rho |0>.
+ *     rho itself, and the radiative loss read off <0| rho |0>;
+ *   * the trapping time <t> = int_0^t t' d<RC|rho|RC>/dt' dt' (Eq.
+ *     trappingtime), evaluated as t eta(t) - int_0^t eta dt' (integration by
+ *     parts, exact for the integrals), where xi = int eta dt is one more
+ *     component of the RK4 system (xi' = <RC|rho|RC>);
+ *   * the stop rule of Sec. "Trapping time": propagation ends at t_max, the
+ *     first step at which the population left on the sites has dropped below
+ *     a threshold (1e-5 in the paper).
  *
  * Readings of the paper taken here (each one is also listed in the design notes):
  *   * damping sign: lab8 prints "+ sum n_m gamma_m" inside the bracket; the
@@ -429,13 +436,19 @@ int oracle_rhs(const oracle_params* p, const double* state_in, double* state_out
  *   trace_out [nout]    sum_m Re <m|rho|m>        (may be NULL)
  *   eta_out   [nout]    Re <RC|rho|RC>            (may be NULL)
  *   loss_out  [nout]    Re <0|rho|0>              (may be NULL)
+ *   tmean_out [nout]    trapping time <t> up to that step, fs (may be NULL)
  * and at the end:
  *   rho_out   [N*N complex] site block of rho     (may be NULL)
  *   state_out [nodes*(N+2)^2 complex] every node  (may be NULL)
+ *   steps_done            steps taken             (may be NULL)
+ * stop_trace > 0 ends the propagation after the first step whose site
+ * population sum_m Re <m|rho|m> is below stop_trace (t_max); output rows of
+ * later steps are set to NaN.
  * Returns 0 on success, -1 on bad input or allocation failure. */
-int oracle_propagate(const oracle_params* p, const double* rho0, double dt_fs, long long nsteps, long long out_every,
-                     double* pops_out, double* trace_out, double* eta_out, double* loss_out, double* rho_out,
-                     double* state_out) {
+int oracle_propagate_ex(const oracle_params* p, const double* rho0, double dt_fs, long long nsteps,
+                        long long out_every, double stop_trace, double* pops_out, double* trace_out,
+                        double* eta_out, double* loss_out, double* tmean_out, double* rho_out, double* state_out,
+                        long long* steps_done) {
   if (!rho0 || nsteps < 0 || out_every < 1 || !(dt_fs > 0)) return -1;
   model m;
   if (model_build(&m, p) != 0) return -1;
@@ -457,34 +470,51 @@ int oracle_propagate(const oracle_params* p, const double* rho0, double dt_fs, l
     for (int b = 0; b < N; ++b) y[a * D + b] = rho0[2 * (a * N + b)] + I * rho0[2 * (a * N + b) + 1];
 
   const double h = dt_fs;
-  long long o = 0;
-  for (long long step = 0; step <= nsteps; ++step) {
+  const size_t rc = (size_t)(N + 1) * D + (N + 1); /* <RC|rho|RC> in node 0 */
+  double xi = 0.0;                                 /* int_0^t <RC|rho|RC> dt' */
+  long long o = 0, step;
+  const long long nout = nsteps / out_every + 1;
+  for (step = 0; step <= nsteps; ++step) {
+    double tr = 0.0;
+    for (int a = 0; a < N; ++a) tr += creal(y[a * D + a]);
     if (step % out_every == 0) {
-      double tr = 0.0;
-      for (int a = 0; a < N; ++a) {
-        double pa = creal(y[a * D + a]);
-        if (pops_out) pops_out[o * N + a] = pa;
-        tr += pa;
-      }
+      for (int a = 0; a < N; ++a)
+        if (pops_out) pops_out[o * N + a] = creal(y[a * D + a]);
       if (trace_out) trace_out[o] = tr;
-      if (eta_out) eta_out[o] = creal(y[(N + 1) * D + (N + 1)]);
+      if (eta_out) eta_out[o] = creal(y[rc]);
       if (loss_out) loss_out[o] = creal(y[N * D + N]);
+      if (tmean_out) tmean_out[o] = (double)step * h * creal(y[rc]) - xi;
       ++o;
     }
     if (step == nsteps) break;
+    if (step > 0 && stop_trace > 0 && tr < stop_trace) break;
     size_t e;
     /* k1 = f(y) */
+    double xk = creal(y[rc]);
     rhs_all(&m, y, k, scratch);
     for (e = 0; e < total; ++e) { acc[e] = y[e] + (h / 6.0) * k[e]; z[e] = y[e] + (h / 2.0) * k[e]; }
     /* k2 = f(y + h/2 k1) */
+    xk += 2.0 * creal(z[rc]);
     rhs_all(&m, z, k, scratch);
     for (e = 0; e < total; ++e) { acc[e] += (h / 3.0) * k[e]; z[e] = y[e] + (h / 2.0) * k[e]; }
     /* k3 = f(y + h/2 k2) */
+    xk += 2.0 * creal(z[rc]);
     rhs_all(&m, z, k, scratch);
     for (e = 0; e < total; ++e) { acc[e] += (h / 3.0) * k[e]; z[e] = y[e] + h * k[e]; }
     /* k4 = f(y + h k3) */
+    xk += creal(z[rc]);
     rhs_all(&m, z, k, scratch);
     for (e = 0; e < total; ++e) y[e] = acc[e] + (h / 6.0) * k[e];
+    xi += (h / 6.0) * xk;
+  }
+  if (steps_done) *steps_done = step < nsteps ? step : nsteps;
+  for (; o < nout; ++o) { /* rows after the stop */
+    for (int a = 0; a < N; ++a)
+      if (pops_out) pops_out[o * N + a] = NAN;
+    if (trace_out) trace_out[o] = NAN;
+    if (eta_out) eta_out[o] = NAN;
+    if (loss_out) loss_out[o] = NAN;
+    if (tmean_out) tmean_out[o] = NAN;
   }
   if (rho_out)
     for (int a = 0; a < N; ++a)
@@ -496,4 +526,12 @@ int oracle_propagate(const oracle_params* p, const double* rho0, double dt_fs, l
   free(y); free(k); free(z); free(acc); free(scratch);
   model_free(&m);
   return 0;
+}
+
+/* The same without the trapping time and the stop rule. */
+int oracle_propagate(const oracle_params* p, const double* rho0, double dt_fs, long long nsteps, long long out_every,
+                     double* pops_out, double* trace_out, double* eta_out, double* loss_out, double* rho_out,
+                     double* state_out) {
+  return oracle_propagate_ex(p, rho0, dt_fs, nsteps, out_every, 0.0, pops_out, trace_out, eta_out, loss_out, NULL,
+                             rho_out, state_out, NULL);
 }

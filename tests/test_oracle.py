@@ -135,6 +135,63 @@ def test_single_site_trap_and_decay_closed_form():
     assert np.abs(r["loss"] - gr / (gt + gr) * (1 - np.exp(-g * t))).max() < 1e-12
 
 
+def test_trapping_time_single_site_closed_form():
+    """Eq. trappingtime for one site: d eta/dt = G_t exp(-g t), so
+    <t>(T) = G_t / g^2 (1 - exp(-g T) (1 + g T)), g = G_t + G_r (fs^-1)."""
+    gt, gr = 0.8, 0.05
+    p = dict(N=1, K=2, H=np.array([[12345.0]]), lam=35.0, gam=106.0, T=300.0,
+             trap=np.array([gt]), recomb=np.array([gr]))
+    r = oracle.propagate(p, np.array([[1.0]]), 1.0, 6000, 250)
+    t = np.arange(r["tmean"].shape[0]) * 250.0
+    g, G = (gt + gr) * 1e-3, gt * 1e-3
+    exact = G / g**2 * (1.0 - np.exp(-g * t) * (1.0 + g * t))
+    assert r["tmean"][0] == 0.0
+    assert np.abs(r["tmean"] - exact).max() < 1e-9 * exact.max()
+    # the running value tends to the mean trapping time G_t / g^2 times eta(inf)
+    assert abs(r["tmean"][-1] - G / g**2) < 0.05 * G / g**2
+
+
+def test_trapping_time_nonhermitian_dimer_quadrature():
+    """Without a bath the trapped flux is sum_m Gamma_m |psi_m(t)|^2 with
+    psi(t) = expm(-i H_eff t) psi(0); <t> by Gauss-Legendre quadrature of
+    t times that flux must match the oracle's value within the RK4 error."""
+    H = np.array([[0.0, 80.0], [80.0, 120.0]], dtype=complex)
+    trap = np.array([0.0, 1.5])
+    p = dict(N=2, K=2, H=H, lam=0.0, gam=106.0, T=300.0, trap=trap)
+    T = 2000.0
+    r = oracle.propagate(p, workloads.pure_state(2, 0), 0.5, int(T / 0.5), int(T / 0.5))
+    heff = H * W - 0.5j * np.diag(trap * 1e-3)
+    x, wq = np.polynomial.legendre.leggauss(64)
+    total = 0.0
+    for k in range(40):  # 40 panels of 50 fs
+        a, b = k * T / 40, (k + 1) * T / 40
+        for xi, wi in zip(x, wq):
+            t = 0.5 * (b - a) * xi + 0.5 * (a + b)
+            psi = expm(-1j * heff * t) @ np.array([1.0, 0.0])
+            total += 0.5 * (b - a) * wi * t * np.sum(trap * 1e-3 * np.abs(psi) ** 2)
+    assert abs(r["tmean"][-1] - total) < 1e-6 * total
+
+
+def test_stop_rule_ends_at_t_max():
+    """Sec. "Trapping time": propagation stops once the site population is
+    below the threshold.  For one site RK4 multiplies the population by
+    P(-g h) = 1 - x + x^2/2 - x^3/6 + x^4/24 (x = g h) per step, so the stop
+    step is known exactly; later output rows are NaN."""
+    gt = 5.0
+    p = dict(N=1, K=1, H=np.array([[0.0]]), lam=35.0, gam=106.0, T=300.0, trap=np.array([gt]))
+    x = gt * 1e-3 * 2.0
+    f = 1 - x + x**2 / 2 - x**3 / 6 + x**4 / 24
+    s_stop = int(np.ceil(np.log(1e-5) / np.log(f)))
+    assert f ** s_stop < 1e-5 <= f ** (s_stop - 1)
+    r = oracle.propagate(p, np.array([[1.0]]), 2.0, 5000, 1, stop_trace=1e-5)
+    assert r["steps_done"] == s_stop
+    assert np.isfinite(r["pops"][: s_stop + 1]).all() and np.isnan(r["pops"][s_stop + 1:]).all()
+    assert abs(r["pops"][s_stop, 0] - f ** s_stop) < 1e-15
+    full = oracle.propagate(p, np.array([[1.0]]), 2.0, 5000, 1)
+    assert full["steps_done"] == 5000
+    assert np.array_equal(full["tmean"][: s_stop + 1], r["tmean"][: s_stop + 1])
+
+
 def test_nonhermitian_dimer_without_bath():
     """lambda = 0 with a trap: a pure state evolves with the non-Hermitian
     H_eff = H - (i/2) diag(Gamma), so rho(t) = psi psi^+ with
