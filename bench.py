@@ -4,8 +4,11 @@ One "step" is one complete solve of the FMO-like N = 7 trap workload
 (depth 6, 1716 hierarchy nodes, dt = 1 fs for 10 ps = 10 000 RK4 steps, seeded
 synthetic Hamiltonian) through the library's C ABI.  The headline value is
 node-RHS evaluations per second (nodes x 4 RK4 stages x steps / time) of the
-mixed-precision path (float auxiliaries, double rho and eta); the plain FP64
-path is timed beside it on the same input.
+mixed-precision path (float right-hand sides, float-float accumulation of
+rho_0, populations and eta); the plain FP64 path is timed beside it on the
+same input.  Beside it: the batched scan (256 instances in one launch) against
+plain FP64 solves of the same instances, the serving trace, and the 24-site
+large hierarchy (HBM-resident) with its own bandwidth roofline.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Multi-GPU (N > 1) runs are replicas launched by torchrun: every rank solves
@@ -23,6 +26,9 @@ import threading
 import time
 
 import numpy as np
+
+# the serving measurement runs up to 32 concurrent launches on separate streams
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -44,6 +50,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-scan measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-trace measurement")
+    ap.add_argument("--no-large", action="store_true", help="skip the 24-site large-hierarchy measurement")
     ap.add_argument("--serving-requests", type=int, default=400,
                     help="requests replayed from the serving trace (the full trace has 2000)")
     ap.add_argument("--cpu-sample-steps", type=int, default=0, help="RK4 steps of the oracle sample (0: auto)")
@@ -170,11 +177,69 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def traffic_from_profile(name):
+    """DRAM bytes per launch recorded in profiles/<name> by an ncu capture,
+    or None when the engine source changed since (its sha256 differs)."""
+    import hashlib
+    try:
+        rec = {}
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            for ln in f:
+                if ":" in ln and ln.split(":", 1)[0].strip() in ("traffic_bytes_per_launch", "engine_sha256"):
+                    k, v = ln.split(":", 1)
+                    rec[k.strip()] = v.strip().strip("`")
+        with open(os.path.join(ROOT, "paper_1012_4382_gb300", "csrc", "heom_engine.cuh"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        if rec.get("engine_sha256") != sha:
+            return None
+        return float(rec["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def l2_copy_gbs(torch, dev):
+    """Copy bandwidth over an L2-resident pair of 16 MiB buffers (read + write
+    bytes / time, CUDA events, best of 5 runs of 100 copies)."""
+    n = (16 << 20) // 4
+    a = torch.ones(n, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    for _ in range(20):
+        b.copy_(a)
+    best = 0.0
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(100):
+            b.copy_(a)
+        e1.record()
+        e1.synchronize()
+        best = max(best, 2.0 * 4 * n * 100 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    return best
+
+
 def algorithmic_bytes_per_node_step(N, elem_bytes):
     """Horner-form RK4 over Hermitian-packed nodes: stage 0 reads y and writes
     wa; stages 1-3 read the stage input and y and write the output, so a node
     moves 11 packed arrays of N*N reals per step."""
     return 11 * N * N * elem_bytes
+
+
+def flops_per_node_stage(N, complex_h=False):
+    """Multiply-adds of one node's right-hand side in the Hermitian-packed
+    form, times 2: per off-diagonal pair the commutator with the real part
+    of H (4N - 6; twice that with an imaginary part) plus 12 for damping,
+    trap, up- and down-couplings; per diagonal 2(N - 1) + 3."""
+    pair = (4 * N - 6) * (2 if complex_h else 1) + 12
+    diag = 2 * (N - 1) + 3
+    return 2.0 * (N * (N - 1) // 2 * pair + N * diag)
+
+
+def fp64_peak_tflops(sm_mhz):
+    """FP64 FMA peak from unit counts: a double-precision warp instruction
+    occupies a sub-partition for 64 cycles, so an SM retires 4 x 32 / 64 = 2
+    FMAs (4 flops) per cycle; 152 SMs."""
+    return 152 * 4.0 * sm_mhz * 1e6 / 1e12
 
 
 def oracle_sample(w, steps):
@@ -251,23 +316,29 @@ def main():
     d_pops = torch.empty(nout * N, dtype=torch.float64, device=dev)
     d_el = torch.empty(2 * nout, dtype=torch.float64, device=dev)
 
+    kernel_ms = []
+
     def timed_device(ctx, steps, warm):
-        """Per-solve device time (ms) with inputs resident; L2 flushed between solves."""
+        """Per-solve device time (ms) with inputs resident; L2 flushed between
+        solves.  The propagation launch alone is timed too (kernel_ms)."""
         times = []
         with torch.cuda.stream(stream):
             for i in range(warm + steps):
                 flush.zero_()
                 e0 = torch.cuda.Event(enable_timing=True)
+                em = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 ctx.set_rho0_device(rho0_dev)
+                em.record(stream)
                 ctx.propagate_device(dt, nsteps, out_every, d_pops, d_el)
                 e1.record(stream)
                 if i >= warm:
-                    times.append((e0, e1))
+                    times.append((e0, em, e1))
         stream.synchronize()
         ctx.synchronize()
-        return [a.elapsed_time(b) for a, b in times]
+        kernel_ms[:] = [b.elapsed_time(c) for a, b, c in times]
+        return [a.elapsed_time(c) for a, b, c in times]
 
     results = {}
     for prec in ("fp32", "fp64"):
@@ -288,6 +359,7 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     per = timed_device(ctx, args.steps, 0)
+    per_kernel = list(kernel_ms)
     torch.cuda.synchronize()
     barrier(world)
     wall = time.perf_counter() - t0
@@ -316,20 +388,22 @@ def main():
     ctx64 = results["fp64"]["ctx"]
     timed_device(ctx64, 0, 1)
     per64 = timed_device(ctx64, max(1, args.steps // 2), 0)
+    per64_kernel = list(kernel_ms)
     fp64_value = units_per_solve * len(per64) / (sum(per64) * 1e-3)
     pops64 = d_pops.view(nout, N).cpu().numpy()
     eta64 = d_el.view(nout, 2)[:, 0].cpu().numpy()
 
     # ---- roofline of the dominant kernel (the persistent engine launch)
-    launch_ms = statistics.mean(per)
+    launch_ms = statistics.mean(per_kernel)
     bytes_per_launch = algorithmic_bytes_per_node_step(N, 4) * nodes * nsteps
     achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
+    l2_gbs = l2_copy_gbs(torch, dev)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (f64 rho, populations and eta)", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32 (float-float rho_0, populations and eta)", "data": "synthetic",
         "config": {"workload": WORKLOAD, "global_batch": world, "seq_len": None,
                    "parallelism": "replicas x%d" % world,
                    "l2": "flushed (256 MB write) before every solve; the 1.0 MB state is L2-resident within a solve",
@@ -340,17 +414,31 @@ def main():
         "wall_s": wall,
         "fp64_path": {"value": fp64_value, "unit": UNIT, "ms_per_solve": statistics.mean(per64),
                       "launch": results["fp64"]["launch"],
+                      "roofline": {"bound": "alu", "unit": "TFLOP/s",
+                                   "achieved": flops_per_node_stage(N) * nodes * 4 * nsteps
+                                   / (statistics.mean(per64_kernel) * 1e-3) / 1e12,
+                                   "peak": fp64_peak_tflops(2070.0),
+                                   "frac": flops_per_node_stage(N) * nodes * 4 * nsteps
+                                   / (statistics.mean(per64_kernel) * 1e-3) / 1e12 / fp64_peak_tflops(2070.0),
+                                   "peak_kind": "derived: 152 SMs x 4 FP64 flops/cycle x 2070 MHz",
+                                   "kernel": kernel_name(results["fp64"]["launch"], N, "f64")},
                       "mixed_vs_fp64_speedup": value / world / fp64_value,
                       "max_abs_pop_diff_vs_mixed": float(np.abs(pops64 - pops_gpu).max()),
                       "abs_eta_diff_vs_mixed": float(abs(eta64[-1] - eta_gpu[-1]))},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "heom_engine_kernel<7, float, mixed>",
-                     "algorithmic_bytes_per_launch": bytes_per_launch},
+                     "traffic": traffic_from_profile("engine_fmo7_k6_mixed.md"), "peak_kind": peak_kind,
+                     "kernel": kernel_name(results["fp32"]["launch"], N, "f32"),
+                     "launch_ms": launch_ms,
+                     "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "l2_copy_gbs_measured": l2_gbs, "frac_of_l2_copy": achieved / l2_gbs,
+                     "note": "the 1 MB working set is L2-resident: the launch is bound by the latency of its "
+                             "40 000 dependent stages, not by a bandwidth"},
         "eta_10ps": float(eta_gpu[-1]),
     }
     if rank == 0 and not args.no_batched:
         line["batched"] = bench_batched(heom, torch, stream)
+    if rank == 0 and not args.no_large:
+        line["large"] = bench_large(heom, torch, stream, peak, peak_kind)
     if rank == 0 and not args.no_serving:
         line["serving"] = bench_serving(args.serving_requests)
     if rank == 0:
@@ -361,6 +449,63 @@ def main():
     for v in results.values():
         v["ctx"].close()
     barrier(world)
+
+
+def kernel_name(launch, N, prec):
+    mode = launch.get("mode") if isinstance(launch, dict) else None
+    if N > 8:
+        return "heom_large_kernel<%s>" % prec
+    if mode == 2:
+        return "heom_smem_kernel<%d> (distributed shared memory)" % N
+    return "heom_engine_kernel<%d, %s>%s" % (N, prec, " (cooperative grid)" if mode == 1 else "")
+
+
+def bench_large(heom, torch, stream, peak, peak_kind):
+    """24-site trimer, depth 4 (20 475 nodes of 24 x 24): the state is larger
+    than L2, so every stage streams it from HBM.  Times the full 2 ps (2000
+    steps) in FP64 and mixed precision; roofline of the FP64 launch."""
+    w = workloads.large_trimer()
+    p = w["params"]
+    N = p["N"]
+    nodes = heom.num_nodes(N, p["K"])
+    nout = w["nsteps"] // w["out_every"] + 1
+    rho0 = torch.from_numpy(np.ascontiguousarray(w["rho0"])).to(torch.cuda.current_device())
+    d_pops = torch.empty(nout * N, dtype=torch.float64, device=rho0.device)
+    d_el = torch.empty(2 * nout, dtype=torch.float64, device=rho0.device)
+    out = {"workload": "24-site trimer (3 x 8-site blocks), K=4, 20475 nodes, dt=1 fs for 2 ps, no trap"}
+    for prec, esize in (("fp64", 8), ("fp32", 4)):
+        flops = flops_per_node_stage(N) * nodes * 4 * w["nsteps"]
+        ctx = heom.Context(p, prec, stream=stream)
+        ms = []
+        with torch.cuda.stream(stream):
+            for i in range(2):
+                ctx.set_rho0_device(rho0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.propagate_device(w["dt"], w["nsteps"], w["out_every"], d_pops, d_el)
+                e1.record(stream)
+                ms.append((e0, e1))
+        stream.synchronize()
+        t = ms[-1][0].elapsed_time(ms[-1][1])
+        byts = algorithmic_bytes_per_node_step(N, esize) * nodes * w["nsteps"]
+        ach = byts / (t * 1e-3) / 1e9
+        rl = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+              "peak_kind": peak_kind, "traffic": traffic_from_profile("large_trimer_%s.md" % prec),
+              "kernel": "heom_large_kernel<%s>" % prec, "algorithmic_bytes_per_launch": byts}
+        if prec == "fp64":
+            # FP64 runs at 1/64 of the FP32 rate: the arithmetic, not HBM, bounds this launch
+            fp = fp64_peak_tflops(2070.0)
+            tf = flops / (t * 1e-3) / 1e12
+            rl = {"bound": "alu", "achieved": tf, "peak": fp, "unit": "TFLOP/s", "frac": tf / fp,
+                  "peak_kind": "derived: 152 SMs x 4 FP64 flops/cycle x 2070 MHz",
+                  "traffic": rl["traffic"], "kernel": rl["kernel"], "algorithmic_flops_per_launch": flops,
+                  "hbm": {"achieved": ach, "peak": peak, "frac": ach / peak}}
+        out[prec] = {"ms_per_solve": t, "node_rhs_per_s": nodes * 4.0 * w["nsteps"] / (t * 1e-3),
+                     "launch": ctx.get_launch(), "roofline": rl,
+                     "pop0_end": float(d_pops.view(nout, N)[-1, 0].item())}
+        ctx.close()
+    return out
 
 
 def bench_batched(heom, torch, stream):
@@ -384,10 +529,42 @@ def bench_batched(heom, torch, stream):
     b.synchronize()
     ms = e0.elapsed_time(e1)
     eta, _ = b.efficiency()
+    launch = b.get_launch() if hasattr(b, "get_launch") else None
     b.close()
+    # plain FP64 path: one instance per launch with the default shape; one
+    # instance of each depth is timed (the time depends on the depth only) and
+    # the 256 solves are summed by depth
+    byK = {}
+    for i, w in enumerate(ws):
+        byK.setdefault(w["params"]["K"], []).append(i)
+    plain_ms = 0.0
+    eta_err = 0.0
+    for K, ids in sorted(byK.items()):
+        w = ws[ids[0]]
+        ctx = heom.Context(w["params"], "fp64", stream=stream)
+        ctx.set_rho0(w["rho0"])
+        with torch.cuda.stream(stream):
+            ctx.propagate_device(1.0, 20, 20)
+        ctx.set_rho0(w["rho0"])
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            f0.record(stream)
+            ctx.propagate_device(1.0, nsteps, nsteps)
+            f1.record(stream)
+        ctx.synchronize()
+        plain_ms += f0.elapsed_time(f1) * len(ids)
+        e64, _ = ctx.efficiency()
+        eta_err = max(eta_err, abs(e64 - eta[ids[0]]))
+        ctx.close()
+    solves = len(ws) / (ms * 1e-3)
+    plain = len(ws) / (plain_ms * 1e-3)
     return {"workload": "256 x N=7 trap, K~U{4..8}, lambda~U(2,200), T~U(77,300), 5 ps, fp32 mixed",
-            "solves_per_s": len(ws) / (ms * 1e-3), "node_rhs_per_s": nodes * 4.0 * nsteps / (ms * 1e-3),
-            "ms": ms, "total_nodes": nodes, "eta_mean": float(np.mean(eta))}
+            "solves_per_s": solves, "node_rhs_per_s": nodes * 4.0 * nsteps / (ms * 1e-3),
+            "ms": ms, "total_nodes": nodes, "eta_mean": float(np.mean(eta)), "launch": launch,
+            "plain_fp64_solves_per_s": plain, "vs_plain_fp64": solves / plain,
+            "plain_fp64_note": "one instance per launch, default shape; one instance of each depth timed",
+            "max_abs_eta_diff_vs_fp64": eta_err}
 
 
 def bench_serving(count):
@@ -396,7 +573,7 @@ def bench_serving(count):
     admission; latency from scheduled arrival to completion."""
     from paper_1012_4382_gb300 import serving
     tr = workloads.serving_trace(count=count)
-    r = serving.run_trace(tr, "fp32", device_bytes=16 << 30, streams=8, time_limit_s=120.0)
+    r = serving.run_trace(tr, "fp32", device_bytes=16 << 30, streams=32, time_limit_s=120.0)
     r["workload"] = ("Poisson 200 req/s, N~U{2..8}, K~U{3..8}, 1-20 ps at 1 fs, fp32 mixed; first %d requests "
                      "of the seeded trace" % count)
     return r

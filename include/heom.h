@@ -160,6 +160,24 @@ int heom_synchronize(heom_ctx* ctx);
  * time; loss_out may be NULL.  Blocking. */
 int heom_efficiency(heom_ctx* ctx, double* eta_out, double* loss_out);
 
+/* Trapping time <t> = int_0^t t' d<RC|rho|RC>/dt' dt' (Eq. trappingtime,
+ * Sec. "Trapping time for different reorganization energies") up to the
+ * current time t (fs from the last heom_set_rho0), evaluated as
+ * t eta(t) - int_0^t eta dt' with the integral carried as one more component
+ * of the RK4 system.  steps_done (may be NULL) receives the number of steps
+ * the last propagate call took (fewer than asked when the stop rule ended it).
+ * heom_set_state restarts the integral (t and int eta dt' set to 0).
+ * Blocking. */
+int heom_trapping_time(heom_ctx* ctx, double* t_mean_fs, int64_t* steps_done);
+
+/* The stop rule of the same section: with stop_trace > 0, the following
+ * propagate calls end after the first step whose site population
+ * sum_m Re <m|rho|m> is below stop_trace (t_max; the paper uses 1e-5).  The
+ * check runs after every step but the last of a call; output rows of later
+ * steps are set to NaN.  0 (the default) turns it off; negative or non-finite
+ * values are HEOM_EINVAL. */
+int heom_set_stop(heom_ctx* ctx, double stop_trace);
+
 /* Current reduced density matrix on the sites, N*N complex.  Blocking. */
 int heom_get_rho(heom_ctx* ctx, double* rho_out);
 
@@ -223,6 +241,10 @@ int heom_batch_synchronize(heom_batch* b);
 
 /* eta_out[count], loss_out[count] (may be NULL); blocking. */
 int heom_batch_efficiency(heom_batch* b, double* eta_out, double* loss_out);
+/* Per instance, as heom_trapping_time / heom_set_stop: t_mean_fs[count],
+ * steps_done[count] (may be NULL); the stop rule applies to every instance. */
+int heom_batch_trapping_time(heom_batch* b, double* t_mean_fs, int64_t* steps_done);
+int heom_batch_set_stop(heom_batch* b, double stop_trace);
 int heom_batch_get_rho(heom_batch* b, int32_t i, double* rho_out);
 
 /* Launch shape of the batch's persistent launches (see heom_set_launch;

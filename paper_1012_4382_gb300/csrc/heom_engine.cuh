@@ -75,8 +75,10 @@ struct Inst {
   void* w0b;
   const void* coef;    // flat coefficient block, see CoefLayout below
   const void* ngam;    // [Mpad] sum_j n_j gamma_j per node (R)
-  double* acc;         // [2] eta and loss integrals (read at the start of a call, written at its end)
-  void* parts;         // [32] partial (eta, loss) sums per unit group: float-float x2 (mixed) or double x2
+  double* acc;         // [8] eta, loss, xi = int eta dt, elapsed time (fs), steps done by the last call
+                       // (read at the start of a call, written at its end)
+  void* parts;         // [32] slots of kPartBytes: partial (eta, loss, xi) sums per unit group,
+                       // float-float x3 (mixed) or double x3
   double* out_pops;    // [nout][N] populations (may be null)
   double* out_el;      // [nout][2] eta, loss (may be null)
   int* done;           // set to 1 (system-wide release) when the instance is finished (may be null)
@@ -86,30 +88,33 @@ struct Inst {
   double hd[4];        // Horner steps h/4, h/3, h/2, h
   float hh[4], hl[4];  // the same as float-float pairs (hi, lo)
   float ec[4 * kMaxSites];  // per site a: h*Gamma_RC,a (hi, lo), h*Gamma_phot,a (hi, lo)
+  float xc[2 * kMaxSites];  // per site a: (h^2/2)*Gamma_RC,a (hi, lo)
+  double stop_trace;        // > 0: stop after the first step whose site population is below it
 };
 
-// Coefficient block (host writes it with the same layout):
-//   R J[N*N]     real part of H off the diagonal (rad/fs), zero diagonal
-//   R Ji[N*N]    imaginary part of H (antisymmetric)
-//   R eps[N]     diagonal of H minus its mean
-//   R ghalf[N]   (Gamma_RC + Gamma_phot) / 2   (1/fs)
-//   R alpha[N]   2 lambda k_B T                (rad^2/fs^2)
-//   R beta[N]    lambda gamma                  (rad^2/fs^2)
-//   R gam[N]     gamma                         (rad/fs)
-//   then, 8-byte aligned: double trap[N], double recomb[N] (1/fs)
+// Bytes of one running-sum slot in Inst::parts.
+constexpr int kPartBytes = 32;
+
+// Coefficient block (host writes it with the same layout; 16-byte aligned):
+//   R J[N][JS]    real part of H off the diagonal (rad/fs), zero diagonal; rows padded
+//                 to JS = 4*ceil(N/4) entries; exactly symmetric
+//   R Ji[N][JS]   imaginary part of H, same padding; exactly antisymmetric
+//   R site[N][4]  per site a: eps_a = H_aa minus the mean diagonal (rad/fs),
+//                 ghalf_a = (Gamma_RC,a + Gamma_phot,a)/2 (1/fs), alpha_a = 2 lambda_a k_B T,
+//                 beta_a = lambda_a gamma_a (rad^2/fs^2)
+//   R gam[N]      gamma_a (rad/fs)
+//   then, 16-byte aligned: double trap[N], double recomb[N] (1/fs)
 template <typename R>
 struct CoefLayout {
+  __host__ __device__ static constexpr int JS(int N) { return (N + 3) / 4 * 4; }
   __host__ __device__ static constexpr int J(int N) { return 0; }
-  __host__ __device__ static constexpr int Ji(int N) { return N * N; }
-  __host__ __device__ static constexpr int eps(int N) { return 2 * N * N; }
-  __host__ __device__ static constexpr int ghalf(int N) { return 2 * N * N + N; }
-  __host__ __device__ static constexpr int alpha(int N) { return 2 * N * N + 2 * N; }
-  __host__ __device__ static constexpr int beta(int N) { return 2 * N * N + 3 * N; }
-  __host__ __device__ static constexpr int gam(int N) { return 2 * N * N + 4 * N; }
-  __host__ __device__ static constexpr int reals(int N) { return 2 * N * N + 5 * N; }
+  __host__ __device__ static constexpr int Ji(int N) { return N * JS(N); }
+  __host__ __device__ static constexpr int site(int N) { return 2 * N * JS(N); }
+  __host__ __device__ static constexpr int gam(int N) { return 2 * N * JS(N) + 4 * N; }
+  __host__ __device__ static constexpr int reals(int N) { return 2 * N * JS(N) + 5 * N; }
   // byte offset of the double arrays
   __host__ __device__ static constexpr int dbl_offset(int N) {
-    return ((reals(N) * (int)sizeof(R) + 7) / 8) * 8;
+    return ((reals(N) * (int)sizeof(R) + 15) / 16) * 16;
   }
   __host__ __device__ static constexpr int bytes(int N) { return dbl_offset(N) + 2 * N * 8; }
 };
@@ -216,6 +221,22 @@ __device__ __forceinline__ bool team_barrier(const EngineArgs& A, unsigned& epoc
 // shared::cluster addresses.  "Reg" views load the node's whole packed matrix
 // into registers once; "Load" views load each element where a unit uses it.
 
+// Loads *a when q holds, else returns 0; predicated, so that gathers of
+// absent neighbours need no branch.
+__device__ __forceinline__ float ld_global_or0(const float* a, bool q) {
+  float v = 0.f;
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.f32 %0, [%1];\n\t}"
+               : "+f"(v)
+               : "l"(a), "r"((unsigned)q));
+  return v;
+}
+__device__ __forceinline__ double ld_global_or0(const double* a, bool q) {
+  double v = 0.0;
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.f64 %0, [%1];\n\t}"
+               : "+d"(v)
+               : "l"(a), "r"((unsigned)q));
+  return v;
+}
 template <typename R>
 struct GlobalArrays {
   const R* __restrict__ win;
@@ -276,11 +297,23 @@ struct GlobalView {
   }
   template <int p>
   __device__ __forceinline__ R G(int h) const { return base[p * Mp + h]; }
+  // element p of node h, or 0 when h == -1 (no link)
+  template <int p>
+  __device__ __forceinline__ R G0(int h) const { return ld_global_or0(base + (p * Mp + h), h != -1); }
   template <int p>
   __device__ __forceinline__ R Y() const { return y[p * Mp]; }
   template <int p>
   __device__ __forceinline__ void St(R v) const { wout[p * Mp] = v; }
 };
+
+__device__ __forceinline__ float ld_dsmem_f32_or0(unsigned addr, bool q) {
+  float v = 0.f;
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.shared::cluster.f32 %0, [%1];\n\t}"
+               : "+f"(v)
+               : "r"(addr), "r"((unsigned)q)
+               : "memory");
+  return v;
+}
 
 __device__ __forceinline__ float ld_dsmem_f32(unsigned addr) {
   float v;
@@ -347,6 +380,10 @@ struct SmemView {
   template <int p>
   __device__ __forceinline__ float G(int h) const {
     return ld_dsmem_f32((unsigned)h + win_off + (unsigned)(p * B * 4));
+  }
+  template <int p>
+  __device__ __forceinline__ float G0(int h) const {
+    return ld_dsmem_f32_or0((unsigned)h + win_off + (unsigned)(p * B * 4), h != -1);
   }
   template <int p>
   __device__ __forceinline__ float Y() const { return y[p * B]; }
@@ -418,33 +455,53 @@ __device__ __forceinline__ double ff_to_double(FF a) { return (double)a.h + (dou
 // diagonal units): float-float in the mixed kernels, double in the FP64 ones.
 template <typename R>
 struct EtaAcc;
+//
+// xi = int eta dt (for the trapping time <t> = t eta - xi, Eq. trappingtime
+// integrated by parts) is one more component of the augmented system:
+// RK4 on (y, eta, xi) gives xi += h eta + (h^2/2) sum_a Gamma_a (w_b)_aa with
+// w_b the stage-2 input (y + h/3 L y + h^2/12 L^2 y).  Each owner adds its
+// share: h e (its own running eta sum, before this step's update) and its
+// diagonals of w_b; h eta at the start of the call is added once at the end.
 template <>
 struct EtaAcc<float> {
-  FF e{0.f, 0.f}, l{0.f, 0.f};
-  // contribution of diagonal a of the root's stage-3 input x: h Gamma_a x
-  __device__ __forceinline__ void add(const Inst& I, int a, FF x) {
-    e = ff_add(e, ff_mul(I.ec[4 * a], I.ec[4 * a + 1], x));
-    l = ff_add(l, ff_mul(I.ec[4 * a + 2], I.ec[4 * a + 3], x));
+  FF e{0.f, 0.f}, l{0.f, 0.f}, x{0.f, 0.f};
+  // contribution of diagonal a of the root's stage-3 input w: h Gamma_a w
+  __device__ __forceinline__ void add(const Inst& I, int a, FF w) {
+    e = ff_add(e, ff_mul(I.ec[4 * a], I.ec[4 * a + 1], w));
+    l = ff_add(l, ff_mul(I.ec[4 * a + 2], I.ec[4 * a + 3], w));
   }
+  // contribution of diagonal a of the root's stage-2 input w: (h^2/2) Gamma_a w
+  __device__ __forceinline__ void add_xi(const Inst& I, int a, FF w) {
+    x = ff_add(x, ff_mul(I.xc[2 * a], I.xc[2 * a + 1], w));
+  }
+  // once per step, before the step's eta update: xi += h e
+  __device__ __forceinline__ void step_xi(const Inst& I) { x = ff_add(x, ff_mul(I.hh[3], I.hl[3], e)); }
   __device__ __forceinline__ void store(const Inst& I, int slot) const {
-    float* p = static_cast<float*>(I.parts) + 4 * slot;
+    float* p = static_cast<float*>(I.parts) + (kPartBytes / 4) * slot;
     p[0] = e.h;
     p[1] = e.l;
     p[2] = l.h;
     p[3] = l.l;
+    p[4] = x.h;
+    p[5] = x.l;
   }
 };
 template <>
 struct EtaAcc<double> {
-  double e = 0.0, l = 0.0;
-  __device__ __forceinline__ void add(const Inst& I, const double* cfd, int N, int a, double x) {
-    e += I.dt * cfd[a] * x;
-    l += I.dt * cfd[N + a] * x;
+  double e = 0.0, l = 0.0, x = 0.0;
+  __device__ __forceinline__ void add(const Inst& I, const double* cfd, int N, int a, double w) {
+    e += I.dt * cfd[a] * w;
+    l += I.dt * cfd[N + a] * w;
   }
+  __device__ __forceinline__ void add_xi(const Inst& I, const double* cfd, int a, double w) {
+    x += 0.5 * I.dt * I.dt * cfd[a] * w;
+  }
+  __device__ __forceinline__ void step_xi(const Inst& I) { x += I.dt * e; }
   __device__ __forceinline__ void store(const Inst& I, int slot) const {
-    double* p = static_cast<double*>(I.parts) + 2 * slot;
+    double* p = static_cast<double*>(I.parts) + (kPartBytes / 8) * slot;
     p[0] = e;
     p[1] = l;
+    p[2] = x;
   }
 };
 
@@ -452,25 +509,32 @@ struct EtaAcc<double> {
 // every owner's running sum (read through L2: the owners wrote them before
 // the last stage barrier).
 template <typename R>
-__device__ __forceinline__ void eta_total(const Inst& I, int nslots, double acc0, double acc1, double& e, double& l) {
+__device__ __forceinline__ void eta_total(const Inst& I, int nslots, double acc0, double acc1, double& e, double& l,
+                                          double* xs = nullptr) {
   if constexpr (sizeof(R) == 4) {
-    FF se{0.f, 0.f}, sl{0.f, 0.f};
+    FF se{0.f, 0.f}, sl{0.f, 0.f}, sx{0.f, 0.f};
     const float* p = static_cast<const float*>(I.parts);
+    constexpr int S = kPartBytes / 4;
     for (int k = 0; k < nslots; ++k) {
-      se = ff_add(se, FF{__ldcg(p + 4 * k), __ldcg(p + 4 * k + 1)});
-      sl = ff_add(sl, FF{__ldcg(p + 4 * k + 2), __ldcg(p + 4 * k + 3)});
+      se = ff_add(se, FF{__ldcg(p + S * k), __ldcg(p + S * k + 1)});
+      sl = ff_add(sl, FF{__ldcg(p + S * k + 2), __ldcg(p + S * k + 3)});
+      if (xs) sx = ff_add(sx, FF{__ldcg(p + S * k + 4), __ldcg(p + S * k + 5)});
     }
     e = acc0 + ff_to_double(se);
     l = acc1 + ff_to_double(sl);
+    if (xs) *xs = ff_to_double(sx);
   } else {
-    double se = 0.0, sl = 0.0;
+    double se = 0.0, sl = 0.0, sx = 0.0;
     const double* p = static_cast<const double*>(I.parts);
+    constexpr int S = kPartBytes / 8;
     for (int k = 0; k < nslots; ++k) {
-      se += __ldcg(p + 2 * k);
-      sl += __ldcg(p + 2 * k + 1);
+      se += __ldcg(p + S * k);
+      sl += __ldcg(p + S * k + 1);
+      sx += __ldcg(p + S * k + 2);
     }
     e = acc0 + se;
     l = acc1 + sl;
+    if (xs) *xs = sx;
   }
 }
 
@@ -492,109 +556,180 @@ struct StageCoef {
   const FF* root_y;  // mixed: the root's float-float y
 };
 
+// Loads M consecutive coefficients (M a multiple of 4, 16-byte aligned) as
+// vectors.
+template <int M, typename R>
+__device__ __forceinline__ void load_row(const R* __restrict__ p, R* out) {
+  if constexpr (sizeof(R) == 4) {
+#pragma unroll
+    for (int i = 0; i < M / 4; ++i) {
+      const float4 v = reinterpret_cast<const float4*>(p)[i];
+      out[4 * i] = v.x;
+      out[4 * i + 1] = v.y;
+      out[4 * i + 2] = v.z;
+      out[4 * i + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < M / 2; ++i) {
+      const double2 v = reinterpret_cast<const double2*>(p)[i];
+      out[2 * i] = v.x;
+      out[2 * i + 1] = v.y;
+    }
+  }
+}
+
 // Right-hand side of unit u (pair (a, b) or diagonal a) of one node.
 // Returns the real part in re and, for pairs, the imaginary part in im.
-template <int N, int u, typename R, bool CPLX, class V>
-__device__ __forceinline__ void unit_rhs(const V& v, const R* __restrict__ cf, R ngam, bool term, R& re, R& im) {
+// J is symmetric and Ji antisymmetric, so all the coefficients of a unit sit
+// in rows a and b and in the site records of a and b.  tc[j] is the
+// terminator factor (n_j + 1) / (ngam + gamma_j) of a leaf node (term), 0
+// elsewhere.  BF: branch-free form -- absent neighbours read as 0 (predicated
+// loads), n_j is 0 where there is no down link and the terminator terms are
+// always evaluated, so the compiler may issue the loads of several units
+// ahead of their arithmetic; worth it where a thread runs many units of a
+// node and arithmetic is cheap (FP32, unit groups G <= 2).  Otherwise each
+// term is skipped where it is absent, which saves FP64 instructions (1/64
+// rate) and the latency of unneeded loads when a thread runs one unit.
+template <int N, int u, typename R, bool CPLX, bool BF, class V>
+__device__ __forceinline__ void unit_rhs(const V& v, const R* __restrict__ cf, R ngam, bool term, const R* tc, R& re,
+                                         R& im) {
   using L = CoefLayout<R>;
   constexpr int NP = N * (N - 1) / 2;
+  constexpr int JS = L::JS(N);
   re = R(0);
   im = R(0);
   if constexpr (u < NP) {
     constexpr int a = pair_a(N, u);
     constexpr int b = pair_b(N, u);
     constexpr int pab = a * N + b, pba = b * N + a;
+    // rows a and b of J and the site records of a and b, as vectors
+    R jr[2 * JS], sa[4], sb[4];
+    load_row<JS>(cf + L::J(N) + a * JS, jr);       // J(a, k)
+    load_row<JS>(cf + L::J(N) + b * JS, jr + JS);  // J(b, k) = J(k, b)
+    auto ja = [&](int k) -> R { return jr[k]; };
+    auto jb = [&](int k) -> R { return jr[JS + k]; };
+    load_row<4>(cf + L::site(N) + 4 * a, sa);
+    load_row<4>(cf + L::site(N) + 4 * b, sb);
     const R x = v.template P<pab>();   // Re sigma_ab
     const R yi = v.template P<pba>();  // Im sigma_ab
     // -i[J, sigma]: Re += [J, A]_ab, Im -= [J, S]_ab
     static_for<0, N>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
       if constexpr (k != a) {
-        const R jak = cf[L::J(N) + a * N + k];
-        if constexpr (k != b) re += jak * Av<N, k, b, V, R>(v);
-        im -= jak * Sv<N, k, b>(v);
+        if constexpr (k != b) re += ja(k) * Av<N, k, b, V, R>(v);
+        im -= ja(k) * Sv<N, k, b>(v);
       }
       if constexpr (k != b) {
-        const R jkb = cf[L::J(N) + k * N + b];
-        if constexpr (k != a) re -= Av<N, a, k, V, R>(v) * jkb;
-        im += Sv<N, a, k>(v) * jkb;
+        if constexpr (k != a) re -= Av<N, a, k, V, R>(v) * jb(k);
+        im += Sv<N, a, k>(v) * jb(k);
       }
     });
     if constexpr (CPLX) {
-      // -i[i Ji, sigma] = [Ji, S] + i [Ji, A]
+      // -i[i Ji, sigma] = [Ji, S] + i [Ji, A], with Ji(k, b) = -Ji(b, k)
+      R ir[2 * JS];
+      load_row<JS>(cf + L::Ji(N) + a * JS, ir);
+      load_row<JS>(cf + L::Ji(N) + b * JS, ir + JS);
+      auto ia = [&](int k) -> R { return ir[k]; };
+      auto ib = [&](int k) -> R { return ir[JS + k]; };
       static_for<0, N>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
         if constexpr (k != a) {
-          const R jak = cf[L::Ji(N) + a * N + k];
-          re += jak * Sv<N, k, b>(v);
-          if constexpr (k != b) im += jak * Av<N, k, b, V, R>(v);
+          re += ia(k) * Sv<N, k, b>(v);
+          if constexpr (k != b) im += ia(k) * Av<N, k, b, V, R>(v);
         }
         if constexpr (k != b) {
-          const R jkb = cf[L::Ji(N) + k * N + b];
-          re -= Sv<N, a, k>(v) * jkb;
-          if constexpr (k != a) im -= Av<N, a, k, V, R>(v) * jkb;
+          re += Sv<N, a, k>(v) * ib(k);
+          if constexpr (k != a) im += Av<N, a, k, V, R>(v) * ib(k);
         }
       });
     }
     // -i (eps_a - eps_b) sigma_ab, anti-Hermitian part and damping
-    const R d = cf[L::eps(N) + a] - cf[L::eps(N) + b];
-    const R c = ngam + cf[L::ghalf(N) + a] + cf[L::ghalf(N) + b];
+    const R d = sa[0] - sb[0];
+    const R c = ngam + sa[1] + sb[1];
     re += d * yi - c * x;
     im -= d * x + c * yi;
-    const R al_a = cf[L::alpha(N) + a], be_a = cf[L::beta(N) + a];
-    const R al_b = cf[L::alpha(N) + b], be_b = cf[L::beta(N) + b];
+    const R al_a = sa[2], be_a = sa[3];
+    const R al_b = sb[2], be_b = sb[3];
     // up-couplings i V_j^x sigma_{n+e_j}: j = a gives +i, j = b gives -i
     const int ua = v.template Up<a>();
     const int ub = v.template Up<b>();
-    if (ua != -1) {
-      re -= v.template G<pba>(ua);
-      im += v.template G<pab>(ua);
-    }
-    if (ub != -1) {
-      re += v.template G<pba>(ub);
-      im -= v.template G<pab>(ub);
-    }
-    if (term) {
-      // sigma_{n+e_j} ~ (n_j+1)/(ngam+gamma_j) theta_j sigma_n, then i V_j^x of it
-      const R ca = (v.template Nj<a>() + R(1)) / (ngam + cf[L::gam(N) + a]);
-      const R cb = (v.template Nj<b>() + R(1)) / (ngam + cf[L::gam(N) + b]);
-      re += ca * (-al_a * x - be_a * yi) + cb * (-al_b * x + be_b * yi);
-      im += ca * (-al_a * yi + be_a * x) + cb * (-al_b * yi - be_b * x);
-    }
     // down-couplings n_j theta_j sigma_{n-e_j}
     const int da = v.template Dn<a>();
     const int db = v.template Dn<b>();
-    if (da != -1) {
+    if constexpr (BF) {
+      const R uar = v.template G0<pab>(ua), uai = v.template G0<pba>(ua);
+      const R ubr = v.template G0<pab>(ub), ubi = v.template G0<pba>(ub);
+      const R dar = v.template G0<pab>(da), dai = v.template G0<pba>(da);
+      const R dbr = v.template G0<pab>(db), dbi = v.template G0<pba>(db);
+      re += ubi - uai;
+      im += uar - ubr;
+      // terminator: sigma_{n+e_j} ~ (n_j+1)/(ngam+gamma_j) theta_j sigma_n, then i V_j^x of it
+      const R ca = tc[a], cb = tc[b];
+      re += ca * (-al_a * x - be_a * yi) + cb * (-al_b * x + be_b * yi);
+      im += ca * (-al_a * yi + be_a * x) + cb * (-al_b * yi - be_b * x);
       const R n_a = v.template Nj<a>();
-      const R yr = v.template G<pab>(da);
-      const R yy = v.template G<pba>(da);
-      re += n_a * (be_a * yr - al_a * yy);
-      im += n_a * (al_a * yr + be_a * yy);
-    }
-    if (db != -1) {
       const R n_b = v.template Nj<b>();
-      const R yr = v.template G<pab>(db);
-      const R yy = v.template G<pba>(db);
-      re += n_b * (be_b * yr + al_b * yy);
-      im += n_b * (be_b * yy - al_b * yr);
+      re += n_a * (be_a * dar - al_a * dai) + n_b * (be_b * dbr + al_b * dbi);
+      im += n_a * (al_a * dar + be_a * dai) + n_b * (be_b * dbi - al_b * dbr);
+    } else {
+      if (ua != -1) {
+        re -= v.template G<pba>(ua);
+        im += v.template G<pab>(ua);
+      }
+      if (ub != -1) {
+        re += v.template G<pba>(ub);
+        im -= v.template G<pab>(ub);
+      }
+      if (term) {
+        const R ca = (v.template Nj<a>() + R(1)) / (ngam + cf[L::gam(N) + a]);
+        const R cb = (v.template Nj<b>() + R(1)) / (ngam + cf[L::gam(N) + b]);
+        re += ca * (-al_a * x - be_a * yi) + cb * (-al_b * x + be_b * yi);
+        im += ca * (-al_a * yi + be_a * x) + cb * (-al_b * yi - be_b * x);
+      }
+      if (da != -1) {
+        const R n_a = v.template Nj<a>();
+        const R yr = v.template G<pab>(da);
+        const R yy = v.template G<pba>(da);
+        re += n_a * (be_a * yr - al_a * yy);
+        im += n_a * (al_a * yr + be_a * yy);
+      }
+      if (db != -1) {
+        const R n_b = v.template Nj<b>();
+        const R yr = v.template G<pab>(db);
+        const R yy = v.template G<pba>(db);
+        re += n_b * (be_b * yr + al_b * yy);
+        im += n_b * (be_b * yy - al_b * yr);
+      }
     }
   } else {
     constexpr int a = u - NP;
     constexpr int paa = a * N + a;
+    R jr[JS], sa[4];
+    load_row<JS>(cf + L::J(N) + a * JS, jr);
+    auto ja = [&](int k) -> R { return jr[k]; };
+    load_row<4>(cf + L::site(N) + 4 * a, sa);
     const R x = v.template P<paa>();
     static_for<0, N>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
-      if constexpr (k != a) re += R(2) * cf[L::J(N) + a * N + k] * Av<N, k, a, V, R>(v);
+      if constexpr (k != a) re += R(2) * ja(k) * Av<N, k, a, V, R>(v);
     });
     if constexpr (CPLX) {
+      R ir[JS];
+      load_row<JS>(cf + L::Ji(N) + a * JS, ir);
+      auto ia = [&](int k) -> R { return ir[k]; };
       static_for<0, N>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
-        if constexpr (k != a) re += R(2) * cf[L::Ji(N) + a * N + k] * Sv<N, k, a>(v);
+        if constexpr (k != a) re += R(2) * ia(k) * Sv<N, k, a>(v);
       });
     }
-    re -= (ngam + R(2) * cf[L::ghalf(N) + a]) * x;
+    re -= (ngam + R(2) * sa[1]) * x;
     const int da = v.template Dn<a>();
-    if (da != -1) re += R(2) * v.template Nj<a>() * cf[L::beta(N) + a] * v.template G<paa>(da);
+    if constexpr (BF) {
+      re += R(2) * v.template Nj<a>() * sa[3] * v.template G0<paa>(da);
+    } else {
+      if (da != -1) re += R(2) * v.template Nj<a>() * sa[3] * v.template G<paa>(da);
+    }
   }
 }
 
@@ -605,64 +740,167 @@ struct OutStep {
   int64_t row;
 };
 
-// All units of one node that belong to the unit mask, one RK4 stage.  For
-// the root node of the mixed path the Horner update w = y + h r runs in
-// float-float on the root's own buffers, and the hi part is stored for the
-// neighbours.  At the last stage the owner of the root's diagonal unit a adds
+// Does unit u belong to this item's group?  GS > 0: the group is u % GS ==
+// GI, known at compile time; GS == 0: the runtime mask umask decides.
+template <int GS, int GI, int u>
+__host__ __device__ constexpr bool in_group(uint64_t umask) {
+  if constexpr (GS > 0) return (u % GS) == GI;
+  else return (umask >> u) & 1ull;
+}
+
+// Shared-memory scratch of one warp for the staged outputs of the global
+// engine: element p of lane l at stg[p * 32 + l]; per CTA the root's
+// float-float stage outputs and its population row.
+template <typename R>
+struct Staging {
+  R* stg;        // this lane's column
+  FF* root_ff;   // [N*N]
+  double* pops;  // [N]
+};
+
+// All units of one node in this item's group, one RK4 stage.  For the root
+// node of the mixed path the Horner update w = y + h r runs in float-float
+// on the root's own buffers, and the hi part is stored for the neighbours.
+// At the last stage the owner of the root's diagonal unit a adds
 // h Gamma_a x_aa to its running eta and loss sums (the extra rows of the
-// augmented RK4 system, x being the stage input).
-template <int N, typename R, bool MIXED, bool CPLX, class V>
+// augmented RK4 system, x being the stage input).  ROOT: the node may be the
+// root (only the item holding node 0 needs that code).  With staging the
+// results first go to shared memory and are copied out after the last unit,
+// so no global store separates the loads of one unit from those of the next
+// (STG; without it the results are stored where they are computed).
+template <int N, typename R, bool MIXED, bool CPLX, int GS, int GI, bool ROOT, bool STG, bool BF, class V>
 __device__ __forceinline__ void node_units(const Inst& I, const R* __restrict__ cf, const double* __restrict__ cfd,
                                            const StageCoef<R>& P, const V& v, R ngam, int s, bool root,
-                                           uint64_t umask, OutStep os, EtaAcc<R>& ea) {
+                                           uint64_t umask, OutStep os, EtaAcc<R>& ea, const Staging<R>& sg) {
+  using L = CoefLayout<R>;
   constexpr int NP = N * (N - 1) / 2;
   constexpr int U = NP + N;
-  const bool term = I.terminator && (v.template Up<0>() == -1);
-  const bool out_row = (s == 3) && root && I.out_pops && os.now;
+  constexpr bool stage_out = STG;
+  // terminator factors: precomputed for the branch-free form, else computed where used
+  R tc[BF ? N : 1];
+#pragma unroll
+  for (int j = 0; j < (BF ? N : 1); ++j) tc[j] = R(0);
+  const bool term = I.terminator && v.template Up<0>() == -1;
+  if constexpr (BF) {
+    if (term) {
+      static_for<0, N>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        tc[j] = (v.template Nj<j>() + R(1)) / (ngam + cf[L::gam(N) + j]);
+      });
+    }
+  }
+  const bool out_row = ROOT && (s == 3) && root && I.out_pops && os.now;
+  auto put = [&](auto pc, R w) {
+    constexpr int p = decltype(pc)::value;
+    if constexpr (stage_out) sg.stg[p * 32] = w;
+    else v.template St<p>(w);
+  };
 
   static_for<0, U>([&](auto uc) {
     constexpr int u = decltype(uc)::value;
-    if (!((umask >> u) & 1ull)) return;
+    if constexpr (GS > 0) {
+      if constexpr (!in_group<GS, GI, u>(0)) return;
+    } else {
+      if (!in_group<0, 0, u>(umask)) return;
+    }
     R re, im;
-    unit_rhs<N, u, R, CPLX>(v, cf, ngam, term, re, im);
+    unit_rhs<N, u, R, CPLX, BF>(v, cf, ngam, term, tc, re, im);
     if constexpr (u < NP) {
       constexpr int a = pair_a(N, u);
       constexpr int b = pair_b(N, u);
       constexpr int pr = a * N + b, pi = b * N + a;
-      if (MIXED && root) {
-        if constexpr (MIXED) {
-          const FF wr = ff_axpy(P.root_y[pr], P.h, P.hl, re);
-          const FF wi = ff_axpy(P.root_y[pi], P.h, P.hl, im);
-          P.root_out[pr] = wr;
-          P.root_out[pi] = wi;
-          v.template St<pr>(wr.h);
-          v.template St<pi>(wi.h);
+      R wr, wi;
+      if constexpr (ROOT && MIXED) {
+        if (root) {
+          const FF fr = ff_axpy(P.root_y[pr], P.h, P.hl, re);
+          const FF fi = ff_axpy(P.root_y[pi], P.h, P.hl, im);
+          if constexpr (stage_out) {
+            sg.root_ff[pr] = fr;
+            sg.root_ff[pi] = fi;
+          } else {
+            P.root_out[pr] = fr;
+            P.root_out[pi] = fi;
+          }
+          wr = fr.h;
+          wi = fi.h;
+        } else {
+          wr = v.template Y<pr>() + P.h * re;
+          wi = v.template Y<pi>() + P.h * im;
         }
       } else {
-        v.template St<pr>(v.template Y<pr>() + P.h * re);
-        v.template St<pi>(v.template Y<pi>() + P.h * im);
+        wr = v.template Y<pr>() + P.h * re;
+        wi = v.template Y<pi>() + P.h * im;
       }
+      put(std::integral_constant<int, pr>{}, wr);
+      put(std::integral_constant<int, pi>{}, wi);
     } else {
       constexpr int a = u - NP;
       constexpr int pd = a * N + a;
-      if (MIXED && root) {
-        if constexpr (MIXED) {
+      R w;
+      [[maybe_unused]] double pop = 0.0;
+      if constexpr (ROOT && MIXED) {
+        if (root) {
           if (s == 3) ea.add(I, a, P.root_in[pd]);
-          const FF w = ff_axpy(P.root_y[pd], P.h, P.hl, re);
-          P.root_out[pd] = w;
-          v.template St<pd>(w.h);
-          if (out_row) I.out_pops[os.row * N + a] = ff_to_double(w);
+          if (s == 2) ea.add_xi(I, a, P.root_in[pd]);
+          const FF f = ff_axpy(P.root_y[pd], P.h, P.hl, re);
+          if constexpr (stage_out) sg.root_ff[pd] = f;
+          else P.root_out[pd] = f;
+          w = f.h;
+          if (out_row) pop = ff_to_double(f);
+        } else {
+          w = v.template Y<pd>() + P.h * re;
         }
       } else {
-        if constexpr (!MIXED) {
+        if constexpr (ROOT && !MIXED) {
           if (root && s == 3) ea.add(I, cfd, N, a, (double)v.template P<pd>());
+          if (root && s == 2) ea.add_xi(I, cfd, a, (double)v.template P<pd>());
         }
-        const R vv = v.template Y<pd>() + P.h * re;
-        v.template St<pd>(vv);
-        if (out_row) I.out_pops[os.row * N + a] = (double)vv;
+        w = v.template Y<pd>() + P.h * re;
+        if constexpr (ROOT) {
+          if (out_row) pop = (double)w;
+        }
+      }
+      put(std::integral_constant<int, pd>{}, w);
+      if constexpr (ROOT) {
+        if (out_row) {
+          if constexpr (stage_out) sg.pops[a] = pop;
+          else I.out_pops[os.row * N + a] = pop;
+        }
       }
     }
   });
+
+  if constexpr (stage_out) {
+    static_for<0, U>([&](auto uc) {
+      constexpr int u = decltype(uc)::value;
+      if constexpr (GS > 0) {
+        if constexpr (!in_group<GS, GI, u>(0)) return;
+      } else {
+        if (!in_group<0, 0, u>(umask)) return;
+      }
+      if constexpr (u < NP) {
+        constexpr int pr = pair_a(N, u) * N + pair_b(N, u), pi = pair_b(N, u) * N + pair_a(N, u);
+        v.template St<pr>(sg.stg[pr * 32]);
+        v.template St<pi>(sg.stg[pi * 32]);
+        if constexpr (ROOT && MIXED) {
+          if (root) {
+            P.root_out[pr] = sg.root_ff[pr];
+            P.root_out[pi] = sg.root_ff[pi];
+          }
+        }
+      } else {
+        constexpr int a = u - NP;
+        constexpr int pd = a * N + a;
+        v.template St<pd>(sg.stg[pd * 32]);
+        if constexpr (ROOT) {
+          if constexpr (MIXED) {
+            if (root) P.root_out[pd] = sg.root_ff[pd];
+          }
+          if (out_row) I.out_pops[os.row * N + a] = sg.pops[a];
+        }
+      }
+    });
+  }
 }
 
 // Row 0 of the outputs (the state at the start of the call).
@@ -734,12 +972,77 @@ struct EtaRows {
   double acc0 = 0.0, acc1 = 0.0;
 };
 
+// The stop rule: true when the site population of the root after the step
+// just finished is below I.stop_trace.  Every CTA of the team evaluates it
+// from the same memory after the stage barrier, so all take the same branch.
+template <typename R, bool MIXED>
+__device__ __forceinline__ bool stop_now(const Inst& I, int N, int* s_flag) {
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    if constexpr (MIXED) {
+      FF sum{0.f, 0.f};
+      const float* y0 = static_cast<const float*>(I.y0);
+      for (int a = 0; a < N; ++a) sum = ff_add(sum, FF{__ldcg(y0 + 2 * (a * N + a)), __ldcg(y0 + 2 * (a * N + a) + 1)});
+      tr = ff_to_double(sum);
+    } else {
+      const R* y = static_cast<const R*>(I.y);
+      for (int a = 0; a < N; ++a) tr += (double)__ldcg(y + (size_t)(a * N + a) * I.Mpad);
+    }
+    *s_flag = tr < I.stop_trace;
+  }
+  __syncthreads();
+  const bool r = *s_flag != 0;
+  __syncthreads();
+  return r;
+}
+
+// End of an instance, lead thread: the last eta row, NaN rows after a stop,
+// and the totals (eta, loss, xi, elapsed time, steps done) for the next call.
+template <typename R>
+__device__ __forceinline__ void finish_instance(const Inst& I, int nslots, const EtaRows& rows, int64_t done,
+                                                int64_t orow, int N) {
+  if (rows.pending >= 0) eta_write_row<R>(I, nslots, rows.acc0, rows.acc1, rows.pending);
+  if (done < I.nsteps) {
+    const int64_t nout = I.nsteps / I.out_every + 1;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    for (int64_t r = orow; r < nout; ++r) {
+      if (I.out_pops)
+        for (int a = 0; a < N; ++a) I.out_pops[r * N + a] = nan;
+      if (I.out_el) {
+        I.out_el[2 * r] = nan;
+        I.out_el[2 * r + 1] = nan;
+      }
+    }
+  }
+  if (done > 0) {
+    double e, l, xs;
+    eta_total<R>(I, nslots, rows.acc0, rows.acc1, e, l, &xs);
+    I.acc[2] += (double)done * I.dt * rows.acc0 + xs;
+    I.acc[3] += (double)done * I.dt;
+    I.acc[0] = e;
+    I.acc[1] = l;
+  }
+  I.acc[4] = (double)done;
+}
+
 // ------------------------------------------------------ global-memory engine
 
+// Dynamic shared memory of the global engine: with FP32 register views (unit
+// groups G <= 2, many units per item) the output staging of every warp,
+// [N*N][32] floats each; none otherwise.
+__host__ __device__ constexpr int engine_dyn_bytes(int N, int block, int rsize, bool reg) {
+  return (reg && rsize == 4) ? (block / 32) * N * N * 32 * rsize : 0;
+}
+
 template <int N, typename R, bool MIXED, bool CPLX, bool REG>
-__global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) heom_engine_kernel(EngineArgs A) {
+__global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, (sizeof(R) == 8 && !REG) ? 2 : 1)
+    heom_engine_kernel(EngineArgs A) {
+  extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ __align__(16) unsigned char s_coef[CoefLayout<R>::bytes(kMaxSmallN) + 64];
+  __shared__ FF s_rootff[kMaxSmallN * kMaxSmallN];
+  __shared__ double s_pops[kMaxSmallN];
   __shared__ Inst s_inst;
+  __shared__ int s_stop;
   __shared__ uint64_t s_umask[32];
   constexpr int U = N * (N - 1) / 2 + N;
   constexpr int NP = N * (N - 1) / 2;
@@ -781,6 +1084,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) heom_engine_kernel
   const bool lead = (warp == 0 && lane == 0);
   const int nslots = G < 32 ? G : 32;
   unsigned epoch = 0;
+  const Staging<R> sg{reinterpret_cast<R*>(dsm) + (threadIdx.x >> 5) * (N * N * 32) + lane, s_rootff, s_pops};
 
   for (int li = A.team_first[team]; li < A.team_first[team + 1]; ++li) {
     load_instance<R>(A, li, s_inst, s_coef);
@@ -801,7 +1105,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) heom_engine_kernel
     if (!team_barrier(A, epoch)) return;
 
     R* arr[3] = {static_cast<R*>(I.y), static_cast<R*>(I.wa), static_cast<R*>(I.wb)};
-    int64_t next_out = I.out_every, orow = 1;
+    int64_t next_out = I.out_every, orow = 1, done = I.nsteps;
     for (int64_t t = 0; t < I.nsteps; ++t) {
       const OutStep os{t + 1 == next_out, orow};
       if (os.now) {
@@ -824,22 +1128,39 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) heom_engine_kernel
           const int n = (nb << 5) + lane;
           if (n >= I.M) continue;
           const GlobalView<N, R, REG> v(ga, n);
-          node_units<N, R, MIXED, CPLX>(I, cf, cfd, P, v, ngam[n], s, n == 0, s_umask[g], os, ea);
+          const R ng = ngam[n];
+          // FP32 register views: staged, branch-free units (see unit_rhs), and the
+          // root's code only in the items that hold it.  Other views run one
+          // instantiation for every item (measured faster: a second copy of the
+          // unit code costs more in instruction fetch than the root branches).
+          constexpr bool BF = REG && sizeof(R) == 4;
+          if constexpr (!BF) {
+            node_units<N, R, MIXED, CPLX, 0, 0, true, false, false>(I, cf, cfd, P, v, ng, s, n == 0, s_umask[g],
+                                                                    os, ea, sg);
+          } else if (nb == 0) {
+            node_units<N, R, MIXED, CPLX, 0, 0, true, true, true>(I, cf, cfd, P, v, ng, s, n == 0, s_umask[g], os,
+                                                                  ea, sg);
+          } else if (G == 1) {
+            node_units<N, R, MIXED, CPLX, 1, 0, false, true, true>(I, cf, cfd, P, v, ng, s, false, 0, os, ea, sg);
+          } else if (g == 0) {  // G == 2
+            node_units<N, R, MIXED, CPLX, 2, 0, false, true, true>(I, cf, cfd, P, v, ng, s, false, 0, os, ea, sg);
+          } else {
+            node_units<N, R, MIXED, CPLX, 2, 1, false, true, true>(I, cf, cfd, P, v, ng, s, false, 0, os, ea, sg);
+          }
         }
+        if (s == 2 && slot >= 0) ea.step_xi(I);
         if (s == 3 && slot >= 0 && (os.now || t + 1 == I.nsteps)) ea.store(I, slot);
         if (!team_barrier(A, epoch)) return;
       }
       if (os.now) rows.pending = os.row;
-    }
-    if (lead) {
-      if (rows.pending >= 0) eta_write_row<R>(I, nslots, rows.acc0, rows.acc1, rows.pending);
-      if (I.nsteps > 0) {
-        double e, l;
-        eta_total<R>(I, nslots, rows.acc0, rows.acc1, e, l);
-        I.acc[0] = e;
-        I.acc[1] = l;
+      if (I.stop_trace > 0.0 && t + 1 < I.nsteps && stop_now<R, MIXED>(I, N, &s_stop)) {
+        if (slot >= 0) ea.store(I, slot);
+        done = t + 1;
+        if (!team_barrier(A, epoch)) return;
+        break;
       }
     }
+    if (lead) finish_instance<R>(I, nslots, rows, done, orow, N);
     if (!team_barrier(A, epoch)) return;
     if (lead) signal_done(I);
   }
@@ -866,6 +1187,7 @@ __global__ void __launch_bounds__(512) heom_smem_kernel(EngineArgs A, int B) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ __align__(16) unsigned char s_coef[CoefLayout<float>::bytes(kMaxSmallN) + 64];
   __shared__ Inst s_inst;
+  __shared__ int s_stop;
   __shared__ uint64_t s_umask[32];
   constexpr int U = N * (N - 1) / 2 + N;
   constexpr int NP = N * (N - 1) / 2;
@@ -954,7 +1276,7 @@ __global__ void __launch_bounds__(512) heom_smem_kernel(EngineArgs A, int B) {
 
     const int nblk = (nloc + 31) >> 5;
     const int items = nblk * G;
-    int64_t next_out = I.out_every, orow = 1;
+    int64_t next_out = I.out_every, orow = 1, done = I.nsteps;
     for (int64_t t = 0; t < I.nsteps; ++t) {
       const OutStep os{t + 1 == next_out, orow};
       if (os.now) {
@@ -978,22 +1300,22 @@ __global__ void __launch_bounds__(512) heom_smem_kernel(EngineArgs A, int B) {
           const int l = (nb << 5) + lane;
           if (l >= nloc) continue;
           const SmemView<N, REG> v(sa, l);
-          node_units<N, float, true, CPLX>(I, cf, cfd, P, v, sng[l], s, rank == 0 && l == 0, s_umask[g], os, ea);
+          node_units<N, float, true, CPLX, 0, 0, true, false, false>(I, cf, cfd, P, v, sng[l], s, rank == 0 && l == 0,
+                                                              s_umask[g], os, ea, Staging<float>{nullptr, nullptr, nullptr});
         }
+        if (s == 2 && slot >= 0) ea.step_xi(I);
         if (s == 3 && slot >= 0 && (os.now || t + 1 == I.nsteps)) ea.store(I, slot);
         cluster_sync_all();
       }
       if (os.now) rows.pending = os.row;
-    }
-    if (lead) {
-      if (rows.pending >= 0) eta_write_row<float>(I, nslots, rows.acc0, rows.acc1, rows.pending);
-      if (I.nsteps > 0) {
-        double e, l;
-        eta_total<float>(I, nslots, rows.acc0, rows.acc1, e, l);
-        I.acc[0] = e;
-        I.acc[1] = l;
+      if (I.stop_trace > 0.0 && t + 1 < I.nsteps && stop_now<float, true>(I, N, &s_stop)) {
+        if (slot >= 0) ea.store(I, slot);
+        done = t + 1;
+        cluster_sync_all();
+        break;
       }
     }
+    if (lead) finish_instance<float>(I, nslots, rows, done, orow, N);
     // write the slice of y back
     float* gyw = static_cast<float*>(I.y);
     for (int idx = threadIdx.x; idx < NN * B; idx += blockDim.x) {
@@ -1009,20 +1331,21 @@ __global__ void __launch_bounds__(512) heom_smem_kernel(EngineArgs A, int B) {
 //
 // Hierarchies with 9..24 sites (N is a run-time argument).  A CTA stages a
 // tile of 32 consecutive nodes' packed matrices in shared memory (element-
-// major, one lane per node, so every access is bank-conflict free); warp w
-// then computes the units u = w, w + nwarps, ... of all 32 nodes, reading the
-// node's own elements from shared memory and its neighbours' from device
-// memory.  Teams and barriers are those of the small-N engine.
-
-struct LargeUnit {
-  unsigned char a, b;
-};
+// major, one lane per node, so every access is bank-conflict free).  The
+// node's outputs are cut into 4 x 4 blocks (a in A, b in B, A <= B, the
+// upper triangle); warp w computes blocks w, w + nwarps, ... of all 32 nodes.
+// Within a block the commutator is a small matrix product: for each k the
+// thread reads column k of its own sigma restricted to A and B (16 values)
+// and row k of J (two 4-vectors) and does 64 multiply-adds, so shared-memory
+// traffic per output is about a sixth of an element-by-element loop.
+// Neighbours are read from device memory, a row segment per linked node.
+// Teams and barriers are those of the small-N engine.
 
 template <typename R, bool MIXED, bool CPLX>
-__global__ void __launch_bounds__(256) heom_large_kernel(EngineArgs A) {
+__global__ void __launch_bounds__(256, 1) heom_large_kernel(EngineArgs A) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ Inst s_inst;
-  __shared__ LargeUnit s_units[kMaxSites * (kMaxSites + 1) / 2];
+  __shared__ int s_stop;
 
   int team, rank, team_size;
   if (A.mode == 0) {
@@ -1037,7 +1360,7 @@ __global__ void __launch_bounds__(256) heom_large_kernel(EngineArgs A) {
   const int nwarps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int slot = (rank == 0 && lane == 0) ? warp : -1;  // tile 0 is on rank 0; warp w owns units w, w + nwarps, ...
+  const int slot = (rank == 0 && lane == 0) ? warp : -1;  // tile 0 is on rank 0; warp w owns blocks w, w + nwarps, ...
   const bool lead = (rank == 0 && threadIdx.x == 0);
   unsigned epoch = 0;
 
@@ -1048,27 +1371,15 @@ __global__ void __launch_bounds__(256) heom_large_kernel(EngineArgs A) {
     const Inst& I = s_inst;
     const int N = I.N;
     const int NN = N * N;
-    const int NP = N * (N - 1) / 2;
-    const int U = NP + N;
     using L = CoefLayout<R>;
+    const int JS = L::JS(N);  // = 4 * number of blocks per side
+    const int NB = JS / 4;
+    const int nblk = NB * (NB + 1) / 2;
     // shared memory: tile [NN][32] | coefficients
     R* tile = reinterpret_cast<R*>(dsm);
     unsigned char* cbytes = dsm + (size_t)NN * 32 * sizeof(R);
     const int cb = L::bytes(N);
     for (int i = threadIdx.x; i < cb; i += blockDim.x) cbytes[i] = static_cast<const unsigned char*>(I.coef)[i];
-    for (int u = threadIdx.x; u < U; u += blockDim.x) {
-      int a, b;
-      if (u < NP) {
-        int r = u;
-        a = 0;
-        while (r >= N - 1 - a) { r -= N - 1 - a; ++a; }
-        b = a + 1 + r;
-      } else {
-        a = b = u - NP;
-      }
-      s_units[u].a = (unsigned char)a;
-      s_units[u].b = (unsigned char)b;
-    }
     __syncthreads();
     const R* cf = reinterpret_cast<const R*>(cbytes);
     const double* cfd = reinterpret_cast<const double*>(cbytes + L::dbl_offset(N));
@@ -1093,7 +1404,7 @@ __global__ void __launch_bounds__(256) heom_large_kernel(EngineArgs A) {
       for (int k = 0; k < nwarps; ++k) ea.store(I, k);  // zero every running-sum slot of this instance
     if (!team_barrier(A, epoch)) return;
     R* arr[3] = {static_cast<R*>(I.y), static_cast<R*>(I.wa), static_cast<R*>(I.wb)};
-    int64_t next_out = I.out_every, orow = 1;
+    int64_t next_out = I.out_every, orow = 1, done = I.nsteps;
     for (int64_t t = 0; t < I.nsteps; ++t) {
       const OutStep os{t + 1 == next_out, orow};
       if (os.now) {
@@ -1116,137 +1427,221 @@ __global__ void __launch_bounds__(256) heom_large_kernel(EngineArgs A) {
         for (int tl = rank; tl < ntiles; tl += team_size) {
           const int n0 = tl << 5;
           __syncthreads();
-          for (int i = threadIdx.x; i < NN * 32; i += blockDim.x) {
-            const int p = i >> 5, l = i & 31;
-            tile[i] = (n0 + l < I.M) ? win[p * Mp + n0 + l] : R(0);
+          {
+            // 8 loads in flight per thread before their stores
+            const bool lv = n0 + lane < I.M;
+            const int total = NN * 32;
+            for (int i0 = threadIdx.x; i0 < total; i0 += 8 * blockDim.x) {
+              R v[8];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const int i = i0 + q * blockDim.x;
+                v[q] = ld_global_or0(win + ((i >> 5) * Mp + n0 + lane), lv && i < total);
+              }
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const int i = i0 + q * blockDim.x;
+                if (i < total) tile[i] = v[q];
+              }
+            }
           }
           __syncthreads();
           const int n = n0 + lane;
-          const bool live = n < I.M;
+          if (n >= I.M) continue;
           const bool root = (n == 0);
-          const R ng = live ? ngam[n] : R(0);
-          const bool term = live && I.terminator && I.up[n] < 0;
-          auto Pk = [&](int k, int l) -> R { return tile[(k * N + l) * 32 + lane]; };
-          auto S = [&](int k, int l) -> R { return k <= l ? Pk(k, l) : Pk(l, k); };
-          auto Aim = [&](int k, int l) -> R { return k < l ? Pk(l, k) : (k > l ? -Pk(k, l) : R(0)); };
-          for (int u = warp; u < U && live; u += nwarps) {
-            const int a = s_units[u].a, b = s_units[u].b;
-            R re = R(0), im = R(0);
-            const int da_raw = I.dn[a * Mp + n];
-            const int da = da_raw < 0 ? -1 : (da_raw & 0xFFFFFF);
-            const R na = da_raw < 0 ? R(0) : R(da_raw >> 24);
-            if (a != b) {
-              const R x = Pk(a, b), yi = Pk(b, a);
-              for (int k = 0; k < N; ++k) {
-                const R jak = cf[L::J(N) + a * N + k];
-                const R jkb = cf[L::J(N) + k * N + b];
-                re += jak * Aim(k, b) - Aim(a, k) * jkb;
-                im += S(a, k) * jkb - jak * S(k, b);
-                if (CPLX) {
-                  const R iak = cf[L::Ji(N) + a * N + k];
-                  const R ikb = cf[L::Ji(N) + k * N + b];
-                  re += iak * S(k, b) - S(a, k) * ikb;
-                  im += iak * Aim(k, b) - Aim(a, k) * ikb;
+          const R ng = ngam[n];
+          const bool term = I.terminator && I.up[n] < 0;
+          // packed element (i, j) of this lane's node; 0 outside the N x N matrix
+          auto Pk = [&](int i, int j) -> R { return (i < N && j < N) ? tile[(i * N + j) * 32 + lane] : R(0); };
+          for (int bk = warp; bk < nblk; bk += nwarps) {
+            // block index -> (A0, B0), A0 <= B0
+            int ab = 0, rem = bk;
+            while (rem >= NB - ab) { rem -= NB - ab; ++ab; }
+            const int A0 = 4 * ab, B0 = 4 * (ab + rem);
+            R re[4][4], im[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) re[i][j] = im[i][j] = R(0);
+            // -i[H, sigma] with the real part J (symmetric) and imaginary part Ji (antisymmetric) of H:
+            //   Re += sum_k J(a,k) A(k,b) - A(a,k) J(k,b);  Im -= sum_k J(a,k) S(k,b) - S(a,k) J(k,b)
+            //   Re += sum_k Ji(a,k) S(k,b) - S(a,k) Ji(k,b); Im += sum_k Ji(a,k) A(k,b) - A(a,k) Ji(k,b)
+            // with S = Re sigma, A = Im sigma; J(a,k) = J(k,a) is read from row k.
+#pragma unroll 1
+            for (int k = 0; k < N; ++k) {
+              R ja[4], jb[4];
+              load_row<4>(cf + L::J(N) + k * JS + A0, ja);
+              load_row<4>(cf + L::J(N) + k * JS + B0, jb);
+              R sak[4], aak[4], skb[4], akb[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const int a = A0 + i;
+                sak[i] = a <= k ? Pk(a, k) : Pk(k, a);
+                aak[i] = a < k ? Pk(k, a) : (a > k ? -Pk(a, k) : R(0));
+                const int b = B0 + i;
+                skb[i] = k <= b ? Pk(k, b) : Pk(b, k);
+                akb[i] = k < b ? Pk(b, k) : (k > b ? -Pk(k, b) : R(0));
+              }
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  re[i][j] += ja[i] * akb[j] - aak[i] * jb[j];
+                  im[i][j] -= ja[i] * skb[j] - sak[i] * jb[j];
                 }
+              if constexpr (CPLX) {
+                R ia[4], ib[4];  // row k of Ji: Ji(k, a) = -Ji(a, k)
+                load_row<4>(cf + L::Ji(N) + k * JS + A0, ia);
+                load_row<4>(cf + L::Ji(N) + k * JS + B0, ib);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                  for (int j = 0; j < 4; ++j) {
+                    re[i][j] -= ia[i] * skb[j] + sak[i] * ib[j];
+                    im[i][j] -= ia[i] * akb[j] + aak[i] * ib[j];
+                  }
               }
-              const R d = cf[L::eps(N) + a] - cf[L::eps(N) + b];
-              const R c = ng + cf[L::ghalf(N) + a] + cf[L::ghalf(N) + b];
-              re += d * yi - c * x;
-              im -= d * x + c * yi;
-              const R al_a = cf[L::alpha(N) + a], be_a = cf[L::beta(N) + a];
-              const R al_b = cf[L::alpha(N) + b], be_b = cf[L::beta(N) + b];
-              const int upa = I.up[a * Mp + n];
-              const int upb = I.up[b * Mp + n];
-              if (upa >= 0) {
-                re -= win[(b * N + a) * Mp + upa];
-                im += win[(a * N + b) * Mp + upa];
-              }
-              if (upb >= 0) {
-                re += win[(b * N + a) * Mp + upb];
-                im -= win[(a * N + b) * Mp + upb];
-              }
-              const int db_raw = I.dn[b * Mp + n];
-              const R nb = db_raw < 0 ? R(0) : R(db_raw >> 24);
-              if (term) {
-                const R ca = (na + R(1)) / (ng + cf[L::gam(N) + a]);
-                const R cbf = (nb + R(1)) / (ng + cf[L::gam(N) + b]);
-                re += ca * (-al_a * x - be_a * yi) + cbf * (-al_b * x + be_b * yi);
-                im += ca * (-al_a * yi + be_a * x) + cbf * (-al_b * yi - be_b * x);
-              }
-              if (da >= 0) {
-                const R yr = win[(a * N + b) * Mp + da];
-                const R yy = win[(b * N + a) * Mp + da];
-                re += na * (be_a * yr - al_a * yy);
-                im += na * (al_a * yr + be_a * yy);
-              }
-              if (db_raw >= 0) {
-                const int db = db_raw & 0xFFFFFF;
-                const R yr = win[(a * N + b) * Mp + db];
-                const R yy = win[(b * N + a) * Mp + db];
-                re += nb * (be_b * yr + al_b * yy);
-                im += nb * (be_b * yy - al_b * yr);
-              }
-            } else {
-              const R x = Pk(a, a);
-              for (int k = 0; k < N; ++k) {
-                if (k == a) continue;
-                re += R(2) * cf[L::J(N) + a * N + k] * Aim(k, a);
-                if (CPLX) re += R(2) * cf[L::Ji(N) + a * N + k] * S(k, a);
-              }
-              re -= (ng + R(2) * cf[L::ghalf(N) + a]) * x;
-              if (da >= 0) re += R(2) * na * cf[L::beta(N) + a] * win[(a * N + a) * Mp + da];
             }
-            // Horner update w = y + h r (root in float-float for mixed precision)
-            const int pr = a * N + b, pi = b * N + a;
-            if (MIXED && root) {
-              if constexpr (MIXED) {
-                if (a == b && s == 3) ea.add(I, a, P.root_in[pr]);
-                const FF wr = ff_axpy(P.root_y[pr], P.h, P.hl, re);
-                P.root_out[pr] = wr;
-                wout[pr * Mp] = wr.h;
+            // links of the block's rows and columns
+            int ua[4], ub[4], da[4], db[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int a = A0 + q, b = B0 + q;
+              ua[q] = a < N ? I.up[a * Mp + n] : -1;
+              da[q] = a < N ? I.dn[a * Mp + n] : -1;
+              ub[q] = b < N ? I.up[b * Mp + n] : -1;
+              db[q] = b < N ? I.dn[b * Mp + n] : -1;
+            }
+            // Local, neighbour and terminator terms of every output of the
+            // block, with the stage's y values, before any store: the loads of
+            // all 16 outputs are independent and can be in flight together.
+            R yr[4][4], yim[4][4];
+            // terminator factors (n_j + 1) / (ngam + gamma_j) of the block's rows and columns (leaf nodes)
+            R tca[4], tcb[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) tca[q] = tcb[q] = R(0);
+            if (term) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const int a = min(A0 + q, N - 1), b = min(B0 + q, N - 1);
+                tca[q] = ((da[q] < 0 ? R(0) : R(da[q] >> 24)) + R(1)) / (ng + cf[L::gam(N) + a]);
+                tcb[q] = ((db[q] < 0 ? R(0) : R(db[q] >> 24)) + R(1)) / (ng + cf[L::gam(N) + b]);
+              }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int a = A0 + i;
+              const int ac = a < N ? a : N - 1;  // clamped for addressing; outputs with a >= N are dropped
+              const R* sa = cf + L::site(N) + 4 * ac;
+              const R eps_a = sa[0], gh_a = sa[1], al_a = sa[2], be_a = sa[3];
+              const R na = da[i] < 0 ? R(0) : R(da[i] >> 24);
+              const int dai = da[i] < 0 ? -1 : (da[i] & 0xFFFFFF);
+              const R ca = tca[i];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const int b = B0 + j;
+                const int bc = b < N ? b : N - 1;
+                const bool keep = a < N && b < N && b >= a;
+                const int pr = ac * N + bc, pi = bc * N + ac;
+                yr[i][j] = ld_global_or0(yv + (pr * Mp + n), keep);
+                yim[i][j] = ld_global_or0(yv + (pi * Mp + n), keep && a != b);
+                const R* sb = cf + L::site(N) + 4 * bc;
+                const R eps_b = sb[0], gh_b = sb[1], al_b = sb[2], be_b = sb[3];
+                const R x = Pk(a, b), yi = Pk(b, a);
+                const int dbj = db[j] < 0 ? -1 : (db[j] & 0xFFFFFF);
+                const R nb = db[j] < 0 ? R(0) : R(db[j] >> 24);
+                // up-couplings i V_j^x sigma_{n+e_j}: j = a gives +i, j = b gives -i
+                const R uar = ld_global_or0(win + (pr * Mp + ua[i]), keep && a != b && ua[i] >= 0);
+                const R uai = ld_global_or0(win + (pi * Mp + ua[i]), keep && a != b && ua[i] >= 0);
+                const R ubr = ld_global_or0(win + (pr * Mp + ub[j]), keep && a != b && ub[j] >= 0);
+                const R ubi = ld_global_or0(win + (pi * Mp + ub[j]), keep && a != b && ub[j] >= 0);
+                // down-couplings n_j theta_j sigma_{n-e_j}
+                const R dar = ld_global_or0(win + (pr * Mp + dai), keep && dai >= 0);
+                const R dai_ = ld_global_or0(win + (pi * Mp + dai), keep && a != b && dai >= 0);
+                const R dbr = ld_global_or0(win + (pr * Mp + dbj), keep && a != b && dbj >= 0);
+                const R dbi = ld_global_or0(win + (pi * Mp + dbj), keep && a != b && dbj >= 0);
+                R r = re[i][j], m = im[i][j];
                 if (a != b) {
-                  const FF wi = ff_axpy(P.root_y[pi], P.h, P.hl, im);
-                  P.root_out[pi] = wi;
-                  wout[pi * Mp] = wi.h;
-                } else if (s == 3 && I.out_pops && os.now) {
-                  I.out_pops[os.row * N + a] = ff_to_double(wr);
+                  const R d = eps_a - eps_b;
+                  const R c = ng + gh_a + gh_b;
+                  r += d * yi - c * x;
+                  m -= d * x + c * yi;
+                  r += ubi - uai;
+                  m += uar - ubr;
+                  const R cbf = tcb[j];
+                  r += ca * (-al_a * x - be_a * yi) + cbf * (-al_b * x + be_b * yi);
+                  m += ca * (-al_a * yi + be_a * x) + cbf * (-al_b * yi - be_b * x);
+                  r += na * (be_a * dar - al_a * dai_) + nb * (be_b * dbr + al_b * dbi);
+                  m += na * (al_a * dar + be_a * dai_) + nb * (be_b * dbi - al_b * dbr);
+                } else {
+                  r -= (ng + R(2) * gh_a) * x;
+                  r += R(2) * na * be_a * dar;
                 }
+                re[i][j] = r;
+                im[i][j] = m;
               }
-            } else {
-              if constexpr (!MIXED) {
-                if (root && a == b && s == 3) ea.add(I, cfd, N, a, (double)Pk(a, a));
-              }
-              const R vr = yv[pr * Mp + n] + h * re;
-              wout[pr * Mp + n] = vr;
-              if (a != b) {
-                wout[pi * Mp + n] = yv[pi * Mp + n] + h * im;
-              } else if (root && s == 3 && I.out_pops && os.now) {
-                I.out_pops[os.row * N + a] = (double)vr;
+            }
+            // Horner update w = y + h r and the stores (root in float-float for mixed precision)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int a = A0 + i;
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const int b = B0 + j;
+                if (a >= N || b >= N || b < a) continue;
+                const int pr = a * N + b, pi = b * N + a;
+                const R r = re[i][j], m = im[i][j];
+                if (MIXED && root) {
+                  if constexpr (MIXED) {
+                    if (a == b && s == 3) ea.add(I, a, P.root_in[pr]);
+                    if (a == b && s == 2) ea.add_xi(I, a, P.root_in[pr]);
+                    const FF wr = ff_axpy(P.root_y[pr], P.h, P.hl, r);
+                    P.root_out[pr] = wr;
+                    wout[pr * Mp] = wr.h;
+                    if (a != b) {
+                      const FF wi = ff_axpy(P.root_y[pi], P.h, P.hl, m);
+                      P.root_out[pi] = wi;
+                      wout[pi * Mp] = wi.h;
+                    } else if (s == 3 && I.out_pops && os.now) {
+                      I.out_pops[os.row * N + a] = ff_to_double(wr);
+                    }
+                  }
+                } else {
+                  if constexpr (!MIXED) {
+                    if (root && a == b && s == 3) ea.add(I, cfd, N, a, (double)Pk(a, a));
+                    if (root && a == b && s == 2) ea.add_xi(I, cfd, a, (double)Pk(a, a));
+                  }
+                  const R vr = yr[i][j] + h * r;
+                  wout[pr * Mp + n] = vr;
+                  if (a != b) {
+                    wout[pi * Mp + n] = yim[i][j] + h * m;
+                  } else if (root && s == 3 && I.out_pops && os.now) {
+                    I.out_pops[os.row * N + a] = (double)vr;
+                  }
+                }
               }
             }
           }
         }
+        if (s == 2 && slot >= 0) ea.step_xi(I);
         if (s == 3 && slot >= 0 && (os.now || t + 1 == I.nsteps)) ea.store(I, slot);
         if (!team_barrier(A, epoch)) return;
       }
       if (os.now) rows.pending = os.row;
-    }
-    if (lead) {
-      if (rows.pending >= 0) eta_write_row<R>(I, nwarps, rows.acc0, rows.acc1, rows.pending);
-      if (I.nsteps > 0) {
-        double e, l;
-        eta_total<R>(I, nwarps, rows.acc0, rows.acc1, e, l);
-        I.acc[0] = e;
-        I.acc[1] = l;
+      if (I.stop_trace > 0.0 && t + 1 < I.nsteps && stop_now<R, MIXED>(I, N, &s_stop)) {
+        if (slot >= 0) ea.store(I, slot);
+        done = t + 1;
+        if (!team_barrier(A, epoch)) return;
+        break;
       }
     }
+    if (lead) finish_instance<R>(I, nwarps, rows, done, orow, N);
     if (!team_barrier(A, epoch)) return;
     if (lead) signal_done(I);
   }
 }
 
 __host__ __device__ constexpr int large_smem_bytes(int N, int rsize) {
-  return N * N * 32 * rsize + ((2 * N * N + 5 * N) * rsize + 7) / 8 * 8 + 2 * N * 8;
+  return N * N * 32 * rsize + (rsize == 8 ? CoefLayout<double>::bytes(N) : CoefLayout<float>::bytes(N));
 }
-
 }  // namespace heom

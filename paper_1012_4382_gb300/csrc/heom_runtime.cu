@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <chrono>
 #include <set>
+#include <tuple>
 #include <cmath>
 #include <deque>
 #include <cstdarg>
@@ -65,6 +66,9 @@ constexpr double kSpeedOfLightCmPerFs = 2.99792458e-5;
 constexpr double kCmToRadPerFs = 2.0 * kPi * kSpeedOfLightCmPerFs;
 constexpr double kBoltzmannCmPerK = 0.6950348004;  // k_B / (h c)
 constexpr double kPerPsToPerFs = 1e-3;
+// per-instance totals carried between calls: eta, loss, xi = int eta dt,
+// elapsed time (fs), steps done by the last call, spare
+constexpr int kAccDoubles = 8;
 
 // ------------------------------------------------------------------ memory
 
@@ -163,10 +167,8 @@ __global__ void set_root_kernel(R* y, int Mpad, float2* y0, const double* rho, i
     y[(size_t)p * Mpad] = (R)v;
     if (y0) y0[p] = to_ff(v);
   }
-  if (p == 0) {
-    acc[0] = 0.0;
-    acc[1] = 0.0;
-  }
+  if (p == 0)
+    for (int k = 0; k < kAccDoubles; ++k) acc[k] = 0.0;
 }
 
 // packed element-major state -> full complex matrices [M][N][N]
@@ -256,16 +258,20 @@ int ilog2(int v) {
   return l;
 }
 
-// Validates one parameter set; fills the instance's host coefficients.
+// Coefficient block of CoefLayout<R> for a validated parameter set, written
+// into out (CoefLayout<R>::bytes(N) bytes; no heap).  J is taken from the
+// upper triangle of H and mirrored, so it is exactly symmetric and Ji
+// exactly antisymmetric, as the kernels assume.
 template <typename R>
-void fill_coefficients(const heom_params& p, std::vector<unsigned char>& out, int* complex_h) {
+void write_coefficients(const heom_params& p, unsigned char* out, int* complex_h) {
   using L = CoefLayout<R>;
   const int N = p.N;
-  out.assign(L::bytes(N), 0);
-  R* c = reinterpret_cast<R*>(out.data());
-  double* cd = reinterpret_cast<double*>(out.data() + L::dbl_offset(N));
+  const int JS = L::JS(N);
+  memset(out, 0, L::bytes(N));
+  R* c = reinterpret_cast<R*>(out);
+  double* cd = reinterpret_cast<double*>(out + L::dbl_offset(N));
+  double diag[heom::kMaxSites];
   double mean = 0.0;
-  std::vector<double> diag(N);
   for (int a = 0; a < N; ++a) {
     diag[a] = p.H[2 * (a * N + a)] + (p.add_reorg_to_H ? p.lambda[a] : 0.0);
     mean += diag[a];
@@ -273,11 +279,14 @@ void fill_coefficients(const heom_params& p, std::vector<unsigned char>& out, in
   mean /= N;
   int cplx = 0;
   for (int a = 0; a < N; ++a)
-    for (int b = 0; b < N; ++b) {
-      if (a == b) continue;
-      c[L::J(N) + a * N + b] = (R)(p.H[2 * (a * N + b)] * kCmToRadPerFs);
+    for (int b = a + 1; b < N; ++b) {
+      const R re = (R)(p.H[2 * (a * N + b)] * kCmToRadPerFs);
       const double im = p.H[2 * (a * N + b) + 1];
-      c[L::Ji(N) + a * N + b] = (R)(im * kCmToRadPerFs);
+      const R ri = (R)(im * kCmToRadPerFs);
+      c[L::J(N) + a * JS + b] = re;
+      c[L::J(N) + b * JS + a] = re;
+      c[L::Ji(N) + a * JS + b] = ri;
+      c[L::Ji(N) + b * JS + a] = -ri;
       if (im != 0.0) cplx = 1;
     }
   const double kT = kBoltzmannCmPerK * p.T_kelvin * kCmToRadPerFs;
@@ -286,15 +295,23 @@ void fill_coefficients(const heom_params& p, std::vector<unsigned char>& out, in
     const double gam = p.gamma[a] * kCmToRadPerFs;
     const double tr = p.trap_rate ? p.trap_rate[a] * kPerPsToPerFs : 0.0;
     const double rc = p.recomb_rate ? p.recomb_rate[a] * kPerPsToPerFs : 0.0;
-    c[L::eps(N) + a] = (R)((diag[a] - mean) * kCmToRadPerFs);
-    c[L::ghalf(N) + a] = (R)(0.5 * (tr + rc));
-    c[L::alpha(N) + a] = (R)(2.0 * lam * kT);
-    c[L::beta(N) + a] = (R)(lam * gam);
+    R* st = c + L::site(N) + 4 * a;
+    st[0] = (R)((diag[a] - mean) * kCmToRadPerFs);
+    st[1] = (R)(0.5 * (tr + rc));
+    st[2] = (R)(2.0 * lam * kT);
+    st[3] = (R)(lam * gam);
     c[L::gam(N) + a] = (R)gam;
     cd[a] = tr;
     cd[N + a] = rc;
   }
   *complex_h = cplx;
+}
+
+// The same into a host vector (the instance's copy of its coefficients).
+template <typename R>
+void fill_coefficients(const heom_params& p, std::vector<unsigned char>& out, int* complex_h) {
+  out.assign(CoefLayout<R>::bytes(p.N), 0);
+  write_coefficients<R>(p, out.data(), complex_h);
 }
 
 int validate(const heom_params* p, int idx) {
@@ -354,6 +371,9 @@ void fill_steps(Inst& d, double dt, const double* rates /* trap[N], recomb[N] in
     d.ec[4 * a + 1] = (float)(et - (double)d.ec[4 * a]);
     d.ec[4 * a + 2] = (float)el;
     d.ec[4 * a + 3] = (float)(el - (double)d.ec[4 * a + 2]);
+    const double ex = 0.5 * dt * dt * rates[a];
+    d.xc[2 * a] = (float)ex;
+    d.xc[2 * a + 1] = (float)(ex - (double)d.xc[2 * a]);
   }
 }
 
@@ -382,6 +402,7 @@ struct Engine {
   std::vector<std::unique_ptr<Instance>> inst;
   std::shared_ptr<TableCache> tables = std::make_shared<TableCache>();
   std::map<int, LaunchCfg> cfg;  // per N
+  double stop_trace = 0.0;        // the stop rule (0: off)
   bool pageable_args = false;     // stage launch descriptors from pageable memory (servers)
   std::vector<unsigned char> h_args_pageable;
   // per-instance output destinations and cadences (servers); empty = contiguous buffers
@@ -568,14 +589,14 @@ struct Engine {
     TRY(in->y.alloc(arr, hooks));
     TRY(in->wa.alloc(arr, hooks));
     TRY(in->wb.alloc(arr, hooks));
-    // three root buffers of N*N float-float pairs, then the 32 (eta, loss) partial-sum slots
-    TRY(in->root64.alloc(3 * 8 * p.N * p.N + 32 * 16, hooks));
+    // three root buffers of N*N float-float pairs, then the 32 (eta, loss, xi) partial-sum slots
+    TRY(in->root64.alloc(3 * 8 * p.N * p.N + 32 * heom::kPartBytes, hooks));
     TRY(in->coef.alloc(in->coef_host.size(), hooks));
-    TRY(in->acc.alloc(4 * sizeof(double), hooks));
+    TRY(in->acc.alloc(kAccDoubles * sizeof(double), hooks));
     TRY(in->stage.alloc(2 * sizeof(double) * p.N * p.N, hooks));
     CUDA_TRY(cudaMemcpyAsync(in->coef.p, in->coef_host.data(), in->coef_host.size(), cudaMemcpyHostToDevice, stream));
     CUDA_TRY(cudaMemsetAsync(in->y.p, 0, arr, stream));
-    CUDA_TRY(cudaMemsetAsync(in->acc.p, 0, 4 * sizeof(double), stream));
+    CUDA_TRY(cudaMemsetAsync(in->acc.p, 0, kAccDoubles * sizeof(double), stream));
     CUDA_TRY(cudaStreamSynchronize(stream));  // coef_host must outlive the copy
     inst.push_back(std::move(in));
     return HEOM_OK;
@@ -660,6 +681,7 @@ struct Engine {
         d.out_every = ovr_every[i];
       }
       d.dt = dt[i];
+      d.stop_trace = stop_trace;
       const int64_t nout = nout_of(nsteps[i], out_every);
       pop_off += nout * in.N;
       row_off += nout;
@@ -669,7 +691,7 @@ struct Engine {
       int N;
       int cplx;
       int B = 0;       // nodes per CTA (mode 2)
-      int dyn = 0;     // dynamic shared memory per CTA (mode 2)
+      int dyn = 0;     // dynamic shared memory per CTA
       LaunchCfg c;
       int nteams;
       std::vector<int32_t> first, list;
@@ -696,6 +718,8 @@ struct Engine {
                       "launch mode 2: %lld nodes of N=%d need %d bytes of shared memory per CTA with %d CTAs "
                       "(at most %d); use more team CTAs or mode 0",
                       (long long)Mmax, g.N, g.dyn, g.c.team_ctas, max_dyn_smem());
+      } else {
+        g.dyn = heom::engine_dyn_bytes(g.N, g.c.block, (int)rsize(), g.c.G <= 2);
       }
       if (g.c.mode == 1) {
         g.nteams = 1;
@@ -912,6 +936,18 @@ struct Engine {
     return HEOM_OK;
   }
 
+  int trapping_time(double* tmean, int64_t* steps) {
+    TRY(ensure_device());
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    for (size_t i = 0; i < inst.size(); ++i) {
+      double v[5];
+      CUDA_TRY(cudaMemcpy(v, inst[i]->acc.p, sizeof(v), cudaMemcpyDeviceToHost));
+      if (tmean) tmean[i] = v[3] * v[0] - v[2];
+      if (steps) steps[i] = (int64_t)v[4];
+    }
+    return HEOM_OK;
+  }
+
   int efficiency(double* eta, double* loss) {
     TRY(ensure_device());
     CUDA_TRY(cudaStreamSynchronize(stream));
@@ -964,7 +1000,7 @@ struct Engine {
       pack_state_kernel<float><<<launch_blocks(work, 256), 256, 0, stream>>>(tmp.as<double>(), in.y.as<float>(),
                                                                             in.Mpad, in.M, in.N, root_ptr(in, 0));
     CUDA_TRY(cudaGetLastError());
-    double acc[2] = {extra ? extra[0] : 0.0, extra ? extra[1] : 0.0};
+    double acc[kAccDoubles] = {extra ? extra[0] : 0.0, extra ? extra[1] : 0.0};
     CUDA_TRY(cudaMemcpyAsync(in.acc.p, acc, sizeof(acc), cudaMemcpyHostToDevice, stream));
     CUDA_TRY(cudaStreamSynchronize(stream));
     return HEOM_OK;
@@ -1062,6 +1098,18 @@ int heom_synchronize(heom_ctx* ctx) {
 int heom_efficiency(heom_ctx* ctx, double* eta_out, double* loss_out) {
   if (!ctx || !eta_out) return fail(HEOM_EINVAL, "ctx or eta_out is NULL");
   return ctx->e.efficiency(eta_out, loss_out);
+}
+
+int heom_trapping_time(heom_ctx* ctx, double* t_mean_fs, int64_t* steps_done) {
+  if (!ctx || !t_mean_fs) return fail(HEOM_EINVAL, "ctx or t_mean_fs is NULL");
+  return ctx->e.trapping_time(t_mean_fs, steps_done);
+}
+
+int heom_set_stop(heom_ctx* ctx, double stop_trace) {
+  if (!ctx) return fail(HEOM_EINVAL, "ctx is NULL");
+  if (!(stop_trace >= 0.0) || !std::isfinite(stop_trace)) return fail(HEOM_EINVAL, "stop_trace must be finite and >= 0");
+  ctx->e.stop_trace = stop_trace;
+  return HEOM_OK;
 }
 
 int heom_get_rho(heom_ctx* ctx, double* rho_out) {
@@ -1183,7 +1231,8 @@ int heom_autotune(heom_ctx* ctx, int64_t trial_steps, double* best_us_per_step) 
   for (const LaunchCfg& c : cands) {
     e.cfg[in.N] = c;
     const int dyn = large ? heom::large_smem_bytes(in.N, (int)e.rsize())
-                          : (c.mode == 2 ? heom::smem_dyn_bytes(in.N, Engine::smem_slice(in.M, c.team_ctas)) : 0);
+                          : (c.mode == 2 ? heom::smem_dyn_bytes(in.N, Engine::smem_slice(in.M, c.team_ctas))
+                                         : heom::engine_dyn_bytes(in.N, c.block, (int)e.rsize(), c.G <= 2));
     if (c.mode != 1 && e.max_active_teams(in.N, in.complex_h, c, dyn) < 1) {
       t_err.clear();
       continue;
@@ -1265,6 +1314,18 @@ int heom_batch_efficiency(heom_batch* b, double* eta_out, double* loss_out) {
   return b->e.efficiency(eta_out, loss_out);
 }
 
+int heom_batch_trapping_time(heom_batch* b, double* t_mean_fs, int64_t* steps_done) {
+  if (!b || !t_mean_fs) return fail(HEOM_EINVAL, "batch or t_mean_fs is NULL");
+  return b->e.trapping_time(t_mean_fs, steps_done);
+}
+
+int heom_batch_set_stop(heom_batch* b, double stop_trace) {
+  if (!b) return fail(HEOM_EINVAL, "batch is NULL");
+  if (!(stop_trace >= 0.0) || !std::isfinite(stop_trace)) return fail(HEOM_EINVAL, "stop_trace must be finite and >= 0");
+  b->e.stop_trace = stop_trace;
+  return HEOM_OK;
+}
+
 int heom_batch_get_rho(heom_batch* b, int32_t i, double* rho_out) {
   if (!b || !rho_out) return fail(HEOM_EINVAL, "batch or rho_out is NULL");
   if (i < 0 || i >= (int32_t)b->e.inst.size()) return fail(HEOM_EINVAL, "instance %d out of range", i);
@@ -1334,46 +1395,6 @@ int static_scratch_address(void** out) {
   return HEOM_OK;
 }
 
-// Coefficient block of CoefLayout<R> written into a caller buffer (no heap).
-template <typename R>
-void write_coefficients_static(const heom_params& p, unsigned char* out, int* complex_h) {
-  using L = CoefLayout<R>;
-  const int N = p.N;
-  memset(out, 0, L::bytes(N));
-  R* c = reinterpret_cast<R*>(out);
-  double* cd = reinterpret_cast<double*>(out + L::dbl_offset(N));
-  double diag[heom::kMaxSmallN];
-  double mean = 0.0;
-  for (int a = 0; a < N; ++a) {
-    diag[a] = p.H[2 * (a * N + a)] + (p.add_reorg_to_H ? p.lambda[a] : 0.0);
-    mean += diag[a];
-  }
-  mean /= N;
-  int cplx = 0;
-  for (int a = 0; a < N; ++a)
-    for (int b = 0; b < N; ++b) {
-      if (a == b) continue;
-      c[L::J(N) + a * N + b] = (R)(p.H[2 * (a * N + b)] * kCmToRadPerFs);
-      const double im = p.H[2 * (a * N + b) + 1];
-      c[L::Ji(N) + a * N + b] = (R)(im * kCmToRadPerFs);
-      if (im != 0.0) cplx = 1;
-    }
-  const double kT = kBoltzmannCmPerK * p.T_kelvin * kCmToRadPerFs;
-  for (int a = 0; a < N; ++a) {
-    const double lam = p.lambda[a] * kCmToRadPerFs;
-    const double gam = p.gamma[a] * kCmToRadPerFs;
-    const double tr = p.trap_rate ? p.trap_rate[a] * kPerPsToPerFs : 0.0;
-    const double rc = p.recomb_rate ? p.recomb_rate[a] * kPerPsToPerFs : 0.0;
-    c[L::eps(N) + a] = (R)((diag[a] - mean) * kCmToRadPerFs);
-    c[L::ghalf(N) + a] = (R)(0.5 * (tr + rc));
-    c[L::alpha(N) + a] = (R)(2.0 * lam * kT);
-    c[L::beta(N) + a] = (R)(lam * gam);
-    c[L::gam(N) + a] = (R)gam;
-    cd[a] = tr;
-    cd[N + a] = rc;
-  }
-  *complex_h = cplx;
-}
 
 }  // namespace
 
@@ -1399,10 +1420,10 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
   const size_t o_status = align256(o_team + 4 * sizeof(int32_t));
   const size_t o_gsync = o_status + 4 * sizeof(int);
   const size_t o_acc = align256(o_gsync + 4 * sizeof(unsigned));
-  const size_t o_coef = align256(o_acc + 4 * sizeof(double));
+  const size_t o_coef = align256(o_acc + kAccDoubles * sizeof(double));
   const size_t coef_bytes = fp64 ? CoefLayout<double>::bytes(N) : CoefLayout<float>::bytes(N);
   const size_t o_root = align256(o_coef + coef_bytes);
-  const size_t o_up = align256(o_root + 3 * 8 * N * N + 32 * 16);
+  const size_t o_up = align256(o_root + 3 * 8 * N * N + 32 * heom::kPartBytes);
   const size_t tab_bytes = sizeof(int32_t) * (size_t)N * Mpad;
   const size_t o_dn = align256(o_up + tab_bytes);
   const size_t o_ngam = align256(o_dn + tab_bytes);
@@ -1445,9 +1466,9 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
   alignas(8) unsigned char h_coef[CoefLayout<double>::bytes(heom::kMaxSmallN)];
   int complex_h = 0;
   if (fp64)
-    write_coefficients_static<double>(p, h_coef, &complex_h);
+    write_coefficients<double>(p, h_coef, &complex_h);
   else
-    write_coefficients_static<float>(p, h_coef, &complex_h);
+    write_coefficients<float>(p, h_coef, &complex_h);
 
   Inst d;
   memset(&d, 0, sizeof(d));
@@ -1489,6 +1510,8 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
   ctas = std::min(16, p2);
   const void* k = heom::engine_kernel(fp64, complex_h != 0, G <= 2, N);
   if (!k) return fail(HEOM_EUNSUPPORTED, "no engine kernel for N=%d", N);
+  const int dyn = heom::engine_dyn_bytes(N, block, fp64 ? 8 : 4, G <= 2);
+  if (dyn > 0) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute at[1];
   for (;;) {
@@ -1496,6 +1519,7 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
     lc = cudaLaunchConfig_t{};
     lc.gridDim = dim3(ctas);
     lc.blockDim = dim3(block);
+    lc.dynamicSmemBytes = dyn;
     lc.stream = stream;
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = ctas;
@@ -1706,18 +1730,28 @@ struct heom_server {
     if (host_mem) cudaFreeHost(host_mem);
   }
 
-  // One thread block per request; the hierarchy lives in the block's shared
-  // memory when every request of the group fits.
-  static LaunchCfg launch_for(const Engine& e, int N, int64_t Mmax) {
+  // Team of a request: about 256 nodes per CTA (1..16 CTAs), the hierarchy in
+  // the team's shared memory when it fits.
+  static int team_for(int64_t M) {
+    int c = 1;
+    while (c < 16 && (int64_t)c * 256 < M) c <<= 1;
+    return c;
+  }
+  static LaunchCfg launch_for(int prec, int N, int64_t M, int max_dyn) {
     LaunchCfg c;
     c.mode = 0;
-    c.team_ctas = 1;
-    c.block = e.max_block();
+    c.team_ctas = team_for(M);
+    c.block = prec == HEOM_FP64 ? 256 : 512;
     c.G = 2;
-    if (e.prec == HEOM_FP32_MIXED && N <= heom::kMaxSmallN &&
-        heom::smem_dyn_bytes(N, Engine::smem_slice(Mmax, 1)) <= e.max_dyn_smem())
+    if (prec == HEOM_FP32_MIXED && N <= heom::kMaxSmallN &&
+        heom::smem_dyn_bytes(N, Engine::smem_slice(M, c.team_ctas)) <= max_dyn)
       c.mode = 2;
     return c;
+  }
+  int max_dyn_smem() const {
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    return optin - 4096;
   }
 
   int start_launch(int li, const std::vector<int64_t>& ids) {
@@ -1728,9 +1762,9 @@ struct heom_server {
     for (int64_t id : ids) ps.push_back(reqs[id]->p);
     int rc = eng->init(ps.data(), (int)ps.size(), L.s, &hooks, tables);
     if (rc != HEOM_OK) return rc;
-    std::map<int, int64_t> mmax;
-    for (auto& in : eng->inst) mmax[in->N] = std::max<int64_t>(mmax[in->N], in->M);
-    for (auto& kv : mmax) eng->cfg[kv.first] = launch_for(*eng, kv.first, kv.second);
+    int64_t Mmax = 0;
+    for (auto& in : eng->inst) Mmax = std::max<int64_t>(Mmax, in->M);
+    for (auto& in : eng->inst) eng->cfg[in->N] = launch_for(eng->prec, in->N, Mmax, max_dyn_smem());
     std::vector<double> dts;
     std::vector<int64_t> steps;
     for (size_t k = 0; k < ids.size(); ++k) {
@@ -1785,9 +1819,16 @@ struct heom_server {
       if (e != cudaSuccess) cudaGetLastError();
       for (int64_t id : L.reqs) {
         Request& q = *reqs[id];
-        if (q.state == kReqRunning) {  // finished without a flag: the launch failed
-          q.state = kReqFailed;
-          q.err = e != cudaSuccess ? cudaGetErrorString(e) : "launch ended before the request finished";
+        if (q.state == kReqRunning) {
+          if (e == cudaSuccess && *reinterpret_cast<volatile int*>(q.h_done()) != 0) {
+            // finished between the flag scan above and this event query
+            q.pops.assign(q.h_pops(), q.h_pops() + q.nout * q.p.N);
+            q.el.assign(q.h_el(), q.h_el() + 2 * q.nout);
+            q.state = kReqDone;
+          } else {  // the launch ended without the request's flag: it failed
+            q.state = kReqFailed;
+            q.err = e != cudaSuccess ? cudaGetErrorString(e) : "launch ended before the request finished";
+          }
           q.t_done = now_s();
           ++done;
         }
@@ -1801,49 +1842,54 @@ struct heom_server {
       L.reqs.clear();
       L.busy = false;
     }
-    // admit queued requests into one launch on a free stream
-    int li = -1;
+    // admit queued requests, in arrival order, while they fit in the budget;
+    // each launch holds requests of one precision, site count and team shape
+    // and takes one free stream
+    std::vector<int> free_streams;
     for (size_t k = 0; k < launches.size(); ++k)
-      if (!launches[k].busy) {
-        li = (int)k;
-        break;
+      if (!launches[k].busy) free_streams.push_back((int)k);
+    std::map<std::tuple<int, int, int, int>, std::vector<int64_t>> groups;
+    std::vector<std::tuple<int, int, int, int>> order;
+    size_t budget = arena.in_use;
+    std::set<std::pair<int, int>> new_tables;
+    const int max_dyn = max_dyn_smem();
+    while (!queue.empty()) {
+      Request& q = *reqs[queue.front()];
+      const auto tkey = std::make_pair(q.p.N, q.p.K);
+      const bool cached = tables->count(tkey) != 0 || new_tables.count(tkey) != 0;
+      const size_t need = request_bytes(q.p, cached) + 8192;
+      if (budget + need > arena.bytes) break;
+      const int64_t M = heom::num_nodes(q.p.N, q.p.K);
+      const LaunchCfg c = launch_for(q.p.precision, q.p.N, M, max_dyn);
+      const auto gkey = std::make_tuple(q.p.precision, q.p.N, c.team_ctas, c.mode);
+      if (!groups.count(gkey)) {
+        if (groups.size() == free_streams.size()) break;  // no stream for a new group
+        order.push_back(gkey);
       }
-    if (li >= 0 && !queue.empty()) {
-      std::vector<int64_t> ids;
-      size_t budget = arena.in_use;
-      std::set<std::pair<int, int>> new_tables;
-      while (!queue.empty()) {
-        Request& q = *reqs[queue.front()];
-        const auto key = std::make_pair(q.p.N, q.p.K);
-        const bool cached = tables->count(key) != 0 || new_tables.count(key) != 0;
-        const size_t need = request_bytes(q.p, cached) + 8192;
-        if (budget + need > arena.bytes) break;
-        if (!ids.empty() && reqs[ids[0]]->p.precision != q.p.precision) break;
-        q.host = static_cast<unsigned char*>(harena.alloc(q.host_bytes()));
-        if (!q.host) break;
-        budget += need;
-        new_tables.insert(key);
-        ids.push_back(q.id);
-        queue.pop_front();
-      }
-      if (!ids.empty()) {
-        const int rc = start_launch(li, ids);
-        if (rc != HEOM_OK) {
-          // put them back at the head of the queue (in order) and report
-          Launch& L = launches[li];
-          L.eng.reset();
-          for (auto it = ids.rbegin(); it != ids.rend(); ++it) {
-            Request& q = *reqs[*it];
-            harena.release(q.host);
-            q.host = nullptr;
-            if (rc == HEOM_ENOMEM) {
-              queue.push_front(*it);
-            } else {
-              q.state = kReqFailed;
-              q.err = t_err;
-            }
+      q.host = static_cast<unsigned char*>(harena.alloc(q.host_bytes()));
+      if (!q.host) break;
+      budget += need;
+      new_tables.insert(tkey);
+      groups[gkey].push_back(q.id);
+      queue.pop_front();
+    }
+    for (size_t g = 0; g < order.size(); ++g) {
+      const int li = free_streams[g];
+      std::vector<int64_t>& ids = groups[order[g]];
+      const int rc = start_launch(li, ids);
+      if (rc != HEOM_OK) {
+        Launch& L = launches[li];
+        L.eng.reset();
+        for (auto it = ids.rbegin(); it != ids.rend(); ++it) {
+          Request& q = *reqs[*it];
+          harena.release(q.host);
+          q.host = nullptr;
+          if (rc == HEOM_ENOMEM) {
+            queue.push_front(*it);
+          } else {
+            q.state = kReqFailed;
+            q.err = t_err;
           }
-          if (rc != HEOM_ENOMEM) return rc;
         }
       }
     }

@@ -80,6 +80,8 @@ def lib() -> ctypes.CDLL:
             "heom_propagate_device": [vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int64, vp, vp],
             "heom_synchronize": [vp],
             "heom_efficiency": [vp, _dp, _dp],
+            "heom_trapping_time": [vp, _dp, _i64p],
+            "heom_set_stop": [vp, ctypes.c_double],
             "heom_get_rho": [vp, _dp],
             "heom_get_state": [vp, _dp, _dp],
             "heom_set_state": [vp, _dp, _dp],
@@ -94,6 +96,8 @@ def lib() -> ctypes.CDLL:
             "heom_batch_propagate_device": [vp, _dp, _i64p, ctypes.c_int64, vp, vp],
             "heom_batch_synchronize": [vp],
             "heom_batch_efficiency": [vp, _dp, _dp],
+            "heom_batch_trapping_time": [vp, _dp, _i64p],
+            "heom_batch_set_stop": [vp, ctypes.c_double],
             "heom_batch_get_rho": [vp, ctypes.c_int32, _dp],
             "heom_batch_set_launch": [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
         }
@@ -289,6 +293,16 @@ class Context:
         _check(lib().heom_efficiency(self._h, ctypes.byref(e), ctypes.byref(l)))
         return e.value, l.value
 
+    def trapping_time(self):
+        """(<t> in fs up to now, steps taken by the last propagate call)."""
+        t, n = ctypes.c_double(), ctypes.c_int64()
+        _check(lib().heom_trapping_time(self._h, ctypes.byref(t), ctypes.byref(n)))
+        return t.value, n.value
+
+    def set_stop(self, stop_trace):
+        """Stop rule: end a propagate call once the site population drops below stop_trace (0: off)."""
+        _check(lib().heom_set_stop(self._h, float(stop_trace)))
+
     def rho(self):
         out = np.zeros(2 * self.N * self.N)
         _check(lib().heom_get_rho(self._h, _ptr(out)))
@@ -389,6 +403,15 @@ class Batch:
         l = np.zeros(self.count)
         _check(lib().heom_batch_efficiency(self._h, _ptr(e), _ptr(l)))
         return e, l
+
+    def trapping_time(self):
+        t = np.zeros(self.count)
+        n = np.zeros(self.count, dtype=np.int64)
+        _check(lib().heom_batch_trapping_time(self._h, _ptr(t), n.ctypes.data_as(_i64p)))
+        return t, n
+
+    def set_stop(self, stop_trace):
+        _check(lib().heom_batch_set_stop(self._h, float(stop_trace)))
 
     def rho(self, i):
         out = np.zeros(2 * self.Ns[i] ** 2)

@@ -7,7 +7,13 @@ slot management and the propagation itself run in libheom.
 from __future__ import annotations
 
 import ctypes
+import os
 import time
+
+# Streams of concurrent launches must not share hardware work queues (the
+# default is 8 queues per process); this takes effect when the CUDA context
+# is created after this import.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import numpy as np
 
@@ -50,7 +56,7 @@ class Server:
     """Continuous-batching server: a device-memory budget, a pinned host
     buffer for results and `streams` CUDA streams (concurrent launches)."""
 
-    def __init__(self, device_bytes: int = 4 << 30, host_bytes: int = 64 << 20, streams: int = 8):
+    def __init__(self, device_bytes: int = 4 << 30, host_bytes: int = 64 << 20, streams: int = 32):
         self._h = ctypes.c_void_p()
         heom._check(_lib().heom_server_create(int(device_bytes), int(host_bytes), int(streams),
                                               ctypes.byref(self._h)))
@@ -116,7 +122,7 @@ class Server:
         return {"queued": q.value, "running": r.value, "bytes_in_use": b.value}
 
 
-def run_trace(trace, precision="fp32", device_bytes=8 << 30, streams=8, keep_results=False, time_limit_s=None):
+def run_trace(trace, precision="fp32", device_bytes=8 << 30, streams=32, keep_results=False, time_limit_s=None):
     """Replays `trace` (dicts with arrival_s, params, rho0, dt, nsteps,
     out_every) against a fresh server in real time.  Latency of a request =
     time from its scheduled arrival to the progress call that saw it finish."""
