@@ -95,6 +95,7 @@ typedef struct {
   const double* recomb;    /* N radiative decay rates Gamma_phot (ps^-1) or NULL */
   int32_t terminator;      /* 0: plain truncation, 1: Markovian terminator */
   int32_t add_reorg;       /* 1: eps_m -> eps_m + lambda_m (Eq. H_ex) */
+  int32_t low_temp;        /* 1: lowest-order quantum (low-temperature) correction */
 } oracle_params;
 
 /* ---------------------------------------------------------------------- */
@@ -214,6 +215,7 @@ typedef struct {
   double kT;         /* rad/fs */
   double* g_rc;      /* N, fs^-1 */
   double* g_phot;    /* N, fs^-1 */
+  double* ltc;       /* N, fs^-1: low-temperature correction rate per bath (0: off) */
   int terminator;
   hierarchy hier;
 } model;
@@ -224,6 +226,7 @@ static void model_free(model* m) {
   free(m->gam);
   free(m->g_rc);
   free(m->g_phot);
+  free(m->ltc);
   hier_free(&m->hier);
   memset(m, 0, sizeof(*m));
 }
@@ -239,7 +242,8 @@ static int model_build(model* m, const oracle_params* p) {
   m->gam = (double*)calloc((size_t)N, sizeof(double));
   m->g_rc = (double*)calloc((size_t)N, sizeof(double));
   m->g_phot = (double*)calloc((size_t)N, sizeof(double));
-  if (!m->H || !m->lam || !m->gam || !m->g_rc || !m->g_phot) {
+  m->ltc = (double*)calloc((size_t)N, sizeof(double));
+  if (!m->H || !m->lam || !m->gam || !m->g_rc || !m->g_phot || !m->ltc) {
     model_free(m);
     return -1;
   }
@@ -257,6 +261,19 @@ static int model_build(model* m, const oracle_params* p) {
   }
   m->kT = cm_to_rad_per_fs(OR_KB_CM_PER_K * p->T);
   m->terminator = p->terminator;
+  /* Lowest-order quantum correction (the paper cites Ishizaki-Fleming for it):
+   * the Drude-Lorentz correlation function has, besides the exp(-gamma t)
+   * term kept in the hierarchy, Matsubara terms
+   *   c_k exp(-nu_k t),  nu_k = 2 pi k kT,  c_k = 4 lambda gamma kT nu_k / (nu_k^2 - gamma^2),  k >= 1.
+   * Taking exp(-nu_k t) ~ delta(t) / nu_k turns them into the local term
+   *   - sum_j ltc_j V_j^x V_j^x sigma_n,  ltc_j = sum_k c_k / nu_k,
+   * and with sum_{k>=1} 1/(k^2 - x^2) = 1/(2 x^2) - pi cot(pi x) / (2 x)
+   * the sum is ltc_j = 2 lambda_j kT / gamma_j - lambda_j cot(gamma_j / (2 kT)). */
+  if (p->low_temp)
+    for (int a = 0; a < N; ++a) {
+      const double x = m->gam[a] / (2.0 * m->kT);
+      m->ltc[a] = 2.0 * m->lam[a] * m->kT / m->gam[a] - m->lam[a] * cos(x) / sin(x);
+    }
   if (hier_build(&m->hier, N, p->K) != 0) {
     model_free(m);
     return -1;
@@ -336,6 +353,13 @@ static void rhs_node(const model* m, long i, const cplx* state, cplx* out, cplx*
   for (int s = 0; s < N; ++s) {
     add_lindblad(D, N, s, m->g_phot[s], x, o);
     add_lindblad(D, N + 1, s, m->g_rc[s], x, o);
+  }
+  /* - sum_j ltc_j V_j^x (V_j^x sigma_n): the low-temperature correction */
+  for (int j = 0; j < N; ++j) {
+    if (m->ltc[j] == 0.0) continue;
+    for (size_t e = 0; e < DD; ++e) scratch[e] = 0;
+    add_Vcomm(D, j, 1.0, x, scratch);
+    add_Vcomm(D, j, -m->ltc[j], scratch, o);
   }
   /* - sum_m n_m gamma_m sigma_n */
   double ngam = 0.0;
