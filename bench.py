@@ -60,6 +60,8 @@ def parse():
                     help="mode,team_ctas,block,node_threads for the mixed path instead of autotuning (profiling runs)")
     ap.add_argument("--solve-steps", type=int, default=0,
                     help="RK4 steps per solve instead of the workload's 10 000 (profiling runs; not a bench value)")
+    ap.add_argument("--large-steps", type=int, default=0,
+                    help="RK4 steps of the 24-site workload instead of its 2000 (profiling runs; not a bench value)")
     return ap.parse_args()
 
 
@@ -179,18 +181,21 @@ def peaks():
 
 def traffic_from_profile(name):
     """DRAM bytes per launch recorded in profiles/<name> by an ncu capture,
-    or None when the engine source changed since (its sha256 differs)."""
+    or None when the kernel's source file changed since (its sha256, recorded
+    beside the figure, differs)."""
     import hashlib
     try:
         rec = {}
         with open(os.path.join(ROOT, "profiles", name)) as f:
             for ln in f:
-                if ":" in ln and ln.split(":", 1)[0].strip() in ("traffic_bytes_per_launch", "engine_sha256"):
+                if ":" in ln:
                     k, v = ln.split(":", 1)
-                    rec[k.strip()] = v.strip().strip("`")
-        with open(os.path.join(ROOT, "paper_1012_4382_gb300", "csrc", "heom_engine.cuh"), "rb") as f:
+                    k = k.strip().strip("-* `")
+                    if k in ("traffic_bytes_per_launch", "source_file", "source_sha256"):
+                        rec[k] = v.strip().strip("`")
+        with open(os.path.join(ROOT, rec["source_file"]), "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
-        if rec.get("engine_sha256") != sha:
+        if rec.get("source_sha256") != sha:
             return None
         return float(rec["traffic_bytes_per_launch"])
     except Exception:
@@ -347,7 +352,7 @@ def main():
             m, c, b, g = (int(x) for x in args.launch.split(","))
             ctx.set_launch(mode=m, team_ctas=c, block_threads=b, node_threads=g)
         elif not args.no_autotune:
-            ctx.autotune(trial_steps=50)
+            ctx.autotune(trial_steps=200)
         results[prec] = {"ctx": ctx, "launch": ctx.get_launch()}
 
     # ---- timed region: mixed-precision path (headline)
@@ -438,7 +443,7 @@ def main():
     if rank == 0 and not args.no_batched:
         line["batched"] = bench_batched(heom, torch, stream)
     if rank == 0 and not args.no_large:
-        line["large"] = bench_large(heom, torch, stream, peak, peak_kind)
+        line["large"] = bench_large(heom, torch, stream, peak, peak_kind, args.large_steps)
     if rank == 0 and not args.no_serving:
         line["serving"] = bench_serving(args.serving_requests)
     if rank == 0:
@@ -460,11 +465,11 @@ def kernel_name(launch, N, prec):
     return "heom_engine_kernel<%d, %s>%s" % (N, prec, " (cooperative grid)" if mode == 1 else "")
 
 
-def bench_large(heom, torch, stream, peak, peak_kind):
+def bench_large(heom, torch, stream, peak, peak_kind, steps=0):
     """24-site trimer, depth 4 (20 475 nodes of 24 x 24): the state is larger
     than L2, so every stage streams it from HBM.  Times the full 2 ps (2000
     steps) in FP64 and mixed precision; roofline of the FP64 launch."""
-    w = workloads.large_trimer()
+    w = workloads.large_trimer(nsteps=steps) if steps > 0 else workloads.large_trimer()
     p = w["params"]
     N = p["N"]
     nodes = heom.num_nodes(N, p["K"])

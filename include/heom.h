@@ -70,6 +70,13 @@ extern "C" {
 #define HEOM_TERM_NONE 0    /* sigma_{n+e_j} = 0 beyond the last level */
 #define HEOM_TERM_MARKOV 1  /* sigma_{n+e_j} ~ (n_j+1) theta_j sigma_n / (sum_k n_k gamma_k + gamma_j) */
 
+/* heom_params.flags */
+#define HEOM_FLAG_LOW_TEMP 1 /* lowest-order quantum correction to the high-temperature baths (the
+                                paper includes it, citing Ishizaki and Fleming, without giving it):
+                                -sum_j c_j V_j^x V_j^x sigma_n on every node, c_j the Markovian
+                                weight of the Matsubara terms, 2 lambda_j k_B T / gamma_j -
+                                lambda_j cot(gamma_j / (2 k_B T)) (hbar = 1) */
+
 /* largest supported number of sites and of hierarchy nodes per instance */
 #define HEOM_MAX_SITES 24
 #define HEOM_MAX_NODES 16777215
@@ -86,7 +93,7 @@ typedef struct heom_params {
   int32_t precision;         /* HEOM_FP64 or HEOM_FP32_MIXED */
   int32_t terminator;        /* HEOM_TERM_NONE or HEOM_TERM_MARKOV */
   int32_t add_reorg_to_H;    /* 0: H used as given; 1: lambda_m added to H_mm (Eq. H_ex) */
-  int32_t reserved;          /* must be 0 */
+  int32_t flags;             /* 0 or HEOM_FLAG_LOW_TEMP */
 } heom_params;
 
 typedef struct heom_ctx heom_ctx;     /* one propagated hierarchy */

@@ -1,5 +1,5 @@
 // Instantiations of the large-N (9..24 sites) engine kernel.
-#include "heom_engine.cuh"
+#include "heom_large.cuh"
 #include "heom_internal.h"
 
 namespace heom {

@@ -1,0 +1,357 @@
+// Large-N engine of the HEOM RK4 propagation (9..24 sites): see the comment
+// below.  Shares the descriptors, coefficient layout, barriers, eta sums and
+// stop rule of heom_engine.cuh.
+#pragma once
+
+#include "heom_engine.cuh"
+
+namespace heom {
+
+// ------------------------------------------------------------ large-N engine
+//
+// Hierarchies with 9..24 sites (N is a run-time argument).  A CTA stages a
+// tile of 32 consecutive nodes' packed matrices in shared memory (element-
+// major, one lane per node, so every access is bank-conflict free).  The
+// node's outputs are cut into 4 x 4 blocks (a in A, b in B, A <= B, the
+// upper triangle); warp w computes blocks w, w + nwarps, ... of all 32 nodes.
+// Within a block the commutator is a small matrix product: for each k the
+// thread reads column k of its own sigma restricted to A and B (16 values)
+// and row k of J (two 4-vectors) and does 64 multiply-adds, so shared-memory
+// traffic per output is about a sixth of an element-by-element loop.
+// Neighbours are read from device memory, a row segment per linked node.
+// Teams and barriers are those of the small-N engine.
+
+template <typename R, bool MIXED, bool CPLX>
+__global__ void __launch_bounds__(256, 1) heom_large_kernel(EngineArgs A) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ Inst s_inst;
+  __shared__ int s_stop;
+
+  int team, rank, team_size;
+  if (A.mode == 0) {
+    team = blockIdx.x / A.team_ctas;
+    rank = blockIdx.x - team * A.team_ctas;
+    team_size = A.team_ctas;
+  } else {
+    team = 0;
+    rank = blockIdx.x;
+    team_size = gridDim.x;
+  }
+  const int nwarps = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int slot = (rank == 0 && lane == 0) ? warp : -1;  // tile 0 is on rank 0; warp w owns blocks w, w + nwarps, ...
+  const bool lead = (rank == 0 && threadIdx.x == 0);
+  unsigned epoch = 0;
+
+  for (int li = A.team_first[team]; li < A.team_first[team + 1]; ++li) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_inst = A.insts[A.team_list[li]];
+    __syncthreads();
+    const Inst& I = s_inst;
+    const int N = I.N;
+    const int NN = N * N;
+    using L = CoefLayout<R>;
+    const int JS = L::JS(N);  // = 4 * number of blocks per side
+    const int NB = JS / 4;
+    const int nblk = NB * (NB + 1) / 2;
+    // shared memory: the tile | coefficients.  FULL (FP32): S = Re sigma and
+    // A = Im sigma as full JS x JS matrices [JS*JS][32] each, zero outside
+    // N x N; otherwise the packed matrix [NN][32] (FP64: the unpacked form
+    // would not fit).
+    constexpr bool FULL = sizeof(R) == 4;
+    R* tile = reinterpret_cast<R*>(dsm);
+    R* tileA = tile + JS * JS * 32;
+    unsigned char* cbytes = dsm + (size_t)(FULL ? 2 * JS * JS : NN) * 32 * sizeof(R);
+    const int cb = L::bytes(N);
+    for (int i = threadIdx.x; i < cb; i += blockDim.x) cbytes[i] = static_cast<const unsigned char*>(I.coef)[i];
+    if (FULL)
+      for (int i = threadIdx.x; i < 2 * JS * JS * 32; i += blockDim.x) tile[i] = R(0);  // padding stays 0
+    __syncthreads();
+    const R* cf = reinterpret_cast<const R*>(cbytes);
+    const double* cfd = reinterpret_cast<const double*>(cbytes + L::dbl_offset(N));
+    const R* ngam = static_cast<const R*>(I.ngam);
+    const int Mp = I.Mpad;
+    const int ntiles = (I.M + 31) >> 5;
+    EtaAcc<R> ea;
+    EtaRows rows;
+    rows.acc0 = I.acc[0];
+    rows.acc1 = I.acc[1];
+    if (lead) {
+      if (I.out_pops)
+        for (int a = 0; a < N; ++a)
+          I.out_pops[a] = MIXED ? ff_to_double(static_cast<const FF*>(I.y0)[a * N + a])
+                                : (double)static_cast<const R*>(I.y)[(a * N + a) * Mp];
+      if (I.out_el) {
+        I.out_el[0] = I.acc[0];
+        I.out_el[1] = I.acc[1];
+      }
+    }
+    if (lead)
+      for (int k = 0; k < nwarps; ++k) ea.store(I, k);  // zero every running-sum slot of this instance
+    if (!team_barrier(A, epoch)) return;
+    R* arr[3] = {static_cast<R*>(I.y), static_cast<R*>(I.wa), static_cast<R*>(I.wb)};
+    int64_t next_out = I.out_every, orow = 1, done = I.nsteps;
+    for (int64_t t = 0; t < I.nsteps; ++t) {
+      const OutStep os{t + 1 == next_out, orow};
+      if (os.now) {
+        next_out += I.out_every;
+        ++orow;
+      }
+#pragma unroll 1
+      for (int s = 0; s < 4; ++s) {
+        if (s == 0 && rows.pending >= 0) {
+          if (lead) eta_write_row<R>(I, nwarps, rows.acc0, rows.acc1, rows.pending);
+          rows.pending = -1;
+        }
+        int in_sel, out_sel;
+        stage_buffers(s, in_sel, out_sel);
+        const StageCoef<R> P = stage_coef<R>(I, s, in_sel, out_sel);
+        const R h = P.h;
+        const R* __restrict__ win = arr[in_sel];
+        R* __restrict__ wout = arr[out_sel];
+        const R* __restrict__ yv = arr[0];
+        for (int tl = rank; tl < ntiles; tl += team_size) {
+          const int n0 = tl << 5;
+          __syncthreads();
+          {
+            // 8 loads in flight per thread before their stores
+            const bool lv = n0 + lane < I.M;
+            const int total = NN * 32;
+            for (int i0 = threadIdx.x; i0 < total; i0 += 8 * blockDim.x) {
+              R v[8];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const int i = i0 + q * blockDim.x;
+                v[q] = ld_global_or0(win + ((i >> 5) * Mp + n0 + lane), lv && i < total);
+              }
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const int i = i0 + q * blockDim.x;
+                if (i < total) {
+                  if constexpr (FULL) {
+                    // packed (r, c): Re sigma_rc for r <= c, Im sigma_cr for r > c
+                    const int pp = i >> 5, r = pp / N, c = pp - r * N, l = i & 31;
+                    if (r < c) {
+                      tile[(r * JS + c) * 32 + l] = v[q];
+                      tile[(c * JS + r) * 32 + l] = v[q];
+                    } else if (r > c) {
+                      tileA[(c * JS + r) * 32 + l] = v[q];
+                      tileA[(r * JS + c) * 32 + l] = -v[q];
+                    } else {
+                      tile[(r * JS + r) * 32 + l] = v[q];
+                    }
+                  } else {
+                    tile[i] = v[q];
+                  }
+                }
+              }
+            }
+          }
+          __syncthreads();
+          const int n = n0 + lane;
+          if (n >= I.M) continue;
+          const bool root = (n == 0);
+          const R ng = ngam[n];
+          const bool term = I.terminator && I.up[n] < 0;
+          // packed element (i, j) of this lane's node; 0 outside the N x N matrix
+          auto Pk = [&](int i, int j) -> R { return (i < N && j < N) ? tile[(i * N + j) * 32 + lane] : R(0); };
+          // Re sigma_ij and Im sigma_ij (FULL tile: no bounds checks, padding is 0)
+          auto Sf = [&](int i, int j) -> R { return tile[(i * JS + j) * 32 + lane]; };
+          auto Af = [&](int i, int j) -> R { return tileA[(i * JS + j) * 32 + lane]; };
+          for (int bk = warp; bk < nblk; bk += nwarps) {
+            // block index -> (A0, B0), A0 <= B0
+            int ab = 0, rem = bk;
+            while (rem >= NB - ab) { rem -= NB - ab; ++ab; }
+            const int A0 = 4 * ab, B0 = 4 * (ab + rem);
+            R re[4][4], im[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) re[i][j] = im[i][j] = R(0);
+            // -i[H, sigma] with the real part J (symmetric) and imaginary part Ji (antisymmetric) of H:
+            //   Re += sum_k J(a,k) A(k,b) - A(a,k) J(k,b);  Im -= sum_k J(a,k) S(k,b) - S(a,k) J(k,b)
+            //   Re += sum_k Ji(a,k) S(k,b) - S(a,k) Ji(k,b); Im += sum_k Ji(a,k) A(k,b) - A(a,k) Ji(k,b)
+            // with S = Re sigma, A = Im sigma; J(a,k) = J(k,a) is read from row k.
+#pragma unroll 1
+            for (int k = 0; k < N; ++k) {
+              R ja[4], jb[4];
+              load_row<4>(cf + L::J(N) + k * JS + A0, ja);
+              load_row<4>(cf + L::J(N) + k * JS + B0, jb);
+              R sak[4], aak[4], skb[4], akb[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const int a = A0 + i, b = B0 + i;
+                if constexpr (FULL) {
+                  sak[i] = Sf(a, k);
+                  aak[i] = Af(a, k);
+                  skb[i] = Sf(b, k);   // S(k, b) = S(b, k)
+                  akb[i] = -Af(b, k);  // A(k, b) = -A(b, k)
+                } else {
+                  sak[i] = a <= k ? Pk(a, k) : Pk(k, a);
+                  aak[i] = a < k ? Pk(k, a) : (a > k ? -Pk(a, k) : R(0));
+                  skb[i] = k <= b ? Pk(k, b) : Pk(b, k);
+                  akb[i] = k < b ? Pk(b, k) : (k > b ? -Pk(k, b) : R(0));
+                }
+              }
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  re[i][j] += ja[i] * akb[j] - aak[i] * jb[j];
+                  im[i][j] -= ja[i] * skb[j] - sak[i] * jb[j];
+                }
+              if constexpr (CPLX) {
+                R ia[4], ib[4];  // row k of Ji: Ji(k, a) = -Ji(a, k)
+                load_row<4>(cf + L::Ji(N) + k * JS + A0, ia);
+                load_row<4>(cf + L::Ji(N) + k * JS + B0, ib);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                  for (int j = 0; j < 4; ++j) {
+                    re[i][j] -= ia[i] * skb[j] + sak[i] * ib[j];
+                    im[i][j] -= ia[i] * akb[j] + aak[i] * ib[j];
+                  }
+              }
+            }
+            // links of the block's rows and columns
+            int ua[4], ub[4], da[4], db[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int a = A0 + q, b = B0 + q;
+              ua[q] = a < N ? I.up[a * Mp + n] : -1;
+              da[q] = a < N ? I.dn[a * Mp + n] : -1;
+              ub[q] = b < N ? I.up[b * Mp + n] : -1;
+              db[q] = b < N ? I.dn[b * Mp + n] : -1;
+            }
+            // Per row of the block: the local, neighbour and terminator terms of
+            // its four outputs and their y values are loaded before any of its
+            // stores, so those loads are in flight together.
+            // terminator factors (n_j + 1) / (ngam + gamma_j) of the block's rows and columns (leaf nodes)
+            R tca[4], tcb[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) tca[q] = tcb[q] = R(0);
+            if (term) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const int a = min(A0 + q, N - 1), b = min(B0 + q, N - 1);
+                tca[q] = ((da[q] < 0 ? R(0) : R(da[q] >> 24)) + R(1)) / (ng + cf[L::gam(N) + a]);
+                tcb[q] = ((db[q] < 0 ? R(0) : R(db[q] >> 24)) + R(1)) / (ng + cf[L::gam(N) + b]);
+              }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              R yr[4], yim[4];
+              const int a = A0 + i;
+              const int ac = a < N ? a : N - 1;  // clamped for addressing; outputs with a >= N are dropped
+              const R* sa = cf + L::site(N) + 4 * ac;
+              const R eps_a = sa[0], gh_a = sa[1], al_a = sa[2], be_a = sa[3];
+              const R na = da[i] < 0 ? R(0) : R(da[i] >> 24);
+              const int dai = da[i] < 0 ? -1 : (da[i] & 0xFFFFFF);
+              const R ca = tca[i];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const int b = B0 + j;
+                const int bc = b < N ? b : N - 1;
+                const bool keep = a < N && b < N && b >= a;
+                const int pr = ac * N + bc, pi = bc * N + ac;
+                yr[j] = ld_global_or0(yv + (pr * Mp + n), keep);
+                yim[j] = ld_global_or0(yv + (pi * Mp + n), keep && a != b);
+                const R* sb = cf + L::site(N) + 4 * bc;
+                const R eps_b = sb[0], gh_b = sb[1], al_b = sb[2], be_b = sb[3];
+                const R x = FULL ? Sf(a, b) : Pk(a, b), yi = FULL ? Af(a, b) : Pk(b, a);
+                const int dbj = db[j] < 0 ? -1 : (db[j] & 0xFFFFFF);
+                const R nb = db[j] < 0 ? R(0) : R(db[j] >> 24);
+                // up-couplings i V_j^x sigma_{n+e_j}: j = a gives +i, j = b gives -i
+                const R uar = ld_global_or0(win + (pr * Mp + ua[i]), keep && a != b && ua[i] >= 0);
+                const R uai = ld_global_or0(win + (pi * Mp + ua[i]), keep && a != b && ua[i] >= 0);
+                const R ubr = ld_global_or0(win + (pr * Mp + ub[j]), keep && a != b && ub[j] >= 0);
+                const R ubi = ld_global_or0(win + (pi * Mp + ub[j]), keep && a != b && ub[j] >= 0);
+                // down-couplings n_j theta_j sigma_{n-e_j}
+                const R dar = ld_global_or0(win + (pr * Mp + dai), keep && dai >= 0);
+                const R dai_ = ld_global_or0(win + (pi * Mp + dai), keep && a != b && dai >= 0);
+                const R dbr = ld_global_or0(win + (pr * Mp + dbj), keep && a != b && dbj >= 0);
+                const R dbi = ld_global_or0(win + (pi * Mp + dbj), keep && a != b && dbj >= 0);
+                R r = re[i][j], m = im[i][j];
+                if (a != b) {
+                  const R d = eps_a - eps_b;
+                  const R c = ng + gh_a + gh_b;
+                  r += d * yi - c * x;
+                  m -= d * x + c * yi;
+                  r += ubi - uai;
+                  m += uar - ubr;
+                  const R cbf = tcb[j];
+                  r += ca * (-al_a * x - be_a * yi) + cbf * (-al_b * x + be_b * yi);
+                  m += ca * (-al_a * yi + be_a * x) + cbf * (-al_b * yi - be_b * x);
+                  r += na * (be_a * dar - al_a * dai_) + nb * (be_b * dbr + al_b * dbi);
+                  m += na * (al_a * dar + be_a * dai_) + nb * (be_b * dbi - al_b * dbr);
+                } else {
+                  r -= (ng + R(2) * cf[L::gd(N) + ac]) * x;
+                  r += R(2) * na * be_a * dar;
+                }
+                re[i][j] = r;
+                im[i][j] = m;
+              }
+              // Horner update w = y + h r and the stores (root in float-float for mixed precision)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const int b = B0 + j;
+                if (a >= N || b >= N || b < a) continue;
+                const int pr = a * N + b, pi = b * N + a;
+                const R r = re[i][j], m = im[i][j];
+                if (MIXED && root) {
+                  if constexpr (MIXED) {
+                    if (a == b && s == 3) ea.add(I, a, P.root_in[pr]);
+                    if (a == b && s == 2) ea.add_xi(I, a, P.root_in[pr]);
+                    const FF wr = ff_axpy(P.root_y[pr], P.h, P.hl, r);
+                    P.root_out[pr] = wr;
+                    wout[pr * Mp] = wr.h;
+                    if (a != b) {
+                      const FF wi = ff_axpy(P.root_y[pi], P.h, P.hl, m);
+                      P.root_out[pi] = wi;
+                      wout[pi * Mp] = wi.h;
+                    } else if (s == 3 && I.out_pops && os.now) {
+                      I.out_pops[os.row * N + a] = ff_to_double(wr);
+                    }
+                  }
+                } else {
+                  if constexpr (!MIXED) {
+                    if (root && a == b && s == 3) ea.add(I, cfd, N, a, (double)(FULL ? Sf(a, a) : Pk(a, a)));
+                    if (root && a == b && s == 2) ea.add_xi(I, cfd, a, (double)(FULL ? Sf(a, a) : Pk(a, a)));
+                  }
+                  const R vr = yr[j] + h * r;
+                  wout[pr * Mp + n] = vr;
+                  if (a != b) {
+                    wout[pi * Mp + n] = yim[j] + h * m;
+                  } else if (root && s == 3 && I.out_pops && os.now) {
+                    I.out_pops[os.row * N + a] = (double)vr;
+                  }
+                }
+              }
+            }
+          }
+        }
+        if (s == 2 && slot >= 0) ea.step_xi(I);
+        if (s == 3 && slot >= 0 && (os.now || t + 1 == I.nsteps)) ea.store(I, slot);
+        if (!team_barrier(A, epoch)) return;
+      }
+      if (os.now) rows.pending = os.row;
+      if (I.stop_trace > 0.0 && t + 1 < I.nsteps && stop_now<R, MIXED>(I, N, &s_stop)) {
+        if (slot >= 0) ea.store(I, slot);
+        done = t + 1;
+        if (!team_barrier(A, epoch)) return;
+        break;
+      }
+    }
+    if (lead) finish_instance<R>(I, nwarps, rows, done, orow, N);
+    if (!team_barrier(A, epoch)) return;
+    if (lead) signal_done(I);
+  }
+}
+
+__host__ __device__ constexpr int large_smem_bytes(int N, int rsize) {
+  // FP32: unpacked S and A tiles of (4 ceil(N/4))^2 x 32; FP64: the packed tile N^2 x 32
+  return rsize == 8 ? N * N * 32 * 8 + CoefLayout<double>::bytes(N)
+                    : 2 * CoefLayout<float>::JS(N) * CoefLayout<float>::JS(N) * 32 * 4 + CoefLayout<float>::bytes(N);
+}
+}  // namespace heom

@@ -23,7 +23,7 @@
 #include <vector>
 
 #include "heom.h"
-#include "heom_engine.cuh"
+#include "heom_large.cuh"
 #include "heom_internal.h"
 
 using heom::CoefLayout;
@@ -258,6 +258,23 @@ int ilog2(int v) {
   return l;
 }
 
+// Lowest-order quantum (low-temperature) correction of bath a, 1/fs, when
+// HEOM_FLAG_LOW_TEMP is set (else 0).  The Matsubara terms k >= 1 of the
+// Drude-Lorentz correlation function, c_k exp(-nu_k t) with nu_k = 2 pi k kT
+// and c_k = 4 lambda gamma kT nu_k / (nu_k^2 - gamma^2), taken as
+// delta(t) c_k / nu_k, give the local term -c_a V_a^x V_a^x sigma_n with
+// c_a = sum_k c_k / nu_k = 2 lambda kT / gamma - lambda cot(gamma / (2 kT)).
+// V_a^x V_a^x damps the elements (a, b) and (b, a), b != a, and leaves the
+// diagonal alone, so c_a enters the off-diagonal damping only.
+double low_temp_rate(const heom_params& p, int a) {
+  if (!(p.flags & HEOM_FLAG_LOW_TEMP)) return 0.0;
+  const double kT = kBoltzmannCmPerK * p.T_kelvin * kCmToRadPerFs;
+  const double lam = p.lambda[a] * kCmToRadPerFs;
+  const double gam = p.gamma[a] * kCmToRadPerFs;
+  const double x = gam / (2.0 * kT);
+  return 2.0 * lam * kT / gam - lam * std::cos(x) / std::sin(x);
+}
+
 // Coefficient block of CoefLayout<R> for a validated parameter set, written
 // into out (CoefLayout<R>::bytes(N) bytes; no heap).  J is taken from the
 // upper triangle of H and mirrored, so it is exactly symmetric and Ji
@@ -297,7 +314,8 @@ void write_coefficients(const heom_params& p, unsigned char* out, int* complex_h
     const double rc = p.recomb_rate ? p.recomb_rate[a] * kPerPsToPerFs : 0.0;
     R* st = c + L::site(N) + 4 * a;
     st[0] = (R)((diag[a] - mean) * kCmToRadPerFs);
-    st[1] = (R)(0.5 * (tr + rc));
+    st[1] = (R)(0.5 * (tr + rc) + low_temp_rate(p, a));
+    c[L::gd(N) + a] = (R)(0.5 * (tr + rc));
     st[2] = (R)(2.0 * lam * kT);
     st[3] = (R)(lam * gam);
     c[L::gam(N) + a] = (R)gam;
@@ -329,7 +347,7 @@ int validate(const heom_params* p, int idx) {
     return fail(HEOM_EINVAL, "params[%d]: unknown terminator %d", idx, p->terminator);
   if (p->add_reorg_to_H != 0 && p->add_reorg_to_H != 1)
     return fail(HEOM_EINVAL, "params[%d]: add_reorg_to_H must be 0 or 1", idx);
-  if (p->reserved != 0) return fail(HEOM_EINVAL, "params[%d]: reserved must be 0", idx);
+  if (p->flags & ~HEOM_FLAG_LOW_TEMP) return fail(HEOM_EINVAL, "params[%d]: unknown flags 0x%x", idx, p->flags);
   const int N = p->N;
   double scale = 0.0;
   for (int i = 0; i < 2 * N * N; ++i) {
@@ -353,6 +371,10 @@ int validate(const heom_params* p, int idx) {
     if (p->recomb_rate && (!(p->recomb_rate[a] >= 0.0) || !std::isfinite(p->recomb_rate[a])))
       return fail(HEOM_EINVAL, "params[%d]: recomb_rate[%d] must be finite and >= 0", idx, a);
   }
+  if (p->flags & HEOM_FLAG_LOW_TEMP)
+    for (int a = 0; a < N; ++a)
+      if (!std::isfinite(low_temp_rate(*p, a)))
+        return fail(HEOM_EINVAL, "params[%d]: the low-temperature correction of site %d is not finite", idx, a);
   return HEOM_OK;
 }
 
@@ -488,10 +510,12 @@ struct Engine {
       return c;
     }
     if (count == 1) {
-      if (prec == HEOM_FP64 && Mmax >= 256) {
+      // one hierarchy: the whole GPU with one unit per warp for large enough
+      // hierarchies (measured best on the FMO-like N = 7, depth 6 workload)
+      if ((prec == HEOM_FP64 && Mmax >= 256) || (prec == HEOM_FP32_MIXED && Mmax >= 1024)) {
         c.mode = 1;
-        c.block = 256;
-        c.G = N >= 4 ? 8 : 2;
+        c.block = max_block();
+        c.G = N >= 4 ? 32 : 2;
         c.team_ctas = 1;
       } else {
         c.mode = 0;
@@ -1199,8 +1223,8 @@ int heom_autotune(heom_ctx* ctx, int64_t trial_steps, double* best_us_per_step) 
         if ((int64_t)ctas * block / 32 > 4 * units && ctas > 1) continue;  // mostly idle warps
         cands.push_back(c);
       }
-    for (int block : {128, 256}) {
-      if (large && block != 256) continue;
+    for (int block : {128, 256, 512}) {
+      if (block > e.max_block() || (large && block != 256)) continue;
       LaunchCfg c;
       c.mode = 1;
       c.block = block;

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "libheom.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, 1, 2, 3, 4, 5
 FP64, FP32_MIXED = 0, 1
+FLAG_LOW_TEMP = 1  # heom_params.flags: low-temperature correction
 TERM_NONE, TERM_MARKOV = 0, 1
 MAX_SITES = 24
 
@@ -54,7 +55,7 @@ class _Params(ctypes.Structure):
         ("precision", ctypes.c_int32),
         ("terminator", ctypes.c_int32),
         ("add_reorg", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
     ]
 
 
@@ -176,7 +177,7 @@ class _Keep:
                 raise ValueError("rate arrays need N entries")
         self.c = _Params(N, int(p["K"]), _ptr(self.H), _ptr(self.lam), _ptr(self.gam), float(p["T"]),
                          _ptr(self.trap), _ptr(self.recomb), int(precision), int(p.get("terminator", 0)),
-                         int(p.get("add_reorg", 0)), 0)
+                         int(p.get("add_reorg", 0)), FLAG_LOW_TEMP if p.get("low_temp", 0) else 0)
 
 
 def _precision(precision):

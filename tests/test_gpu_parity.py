@@ -327,3 +327,28 @@ def test_autotune_keeps_state_and_result():
         assert us > 0
         r = c.propagate(1.0, 40, 10)
     assert np.abs(r["pops"] - o["pops"]).max() < TOL64
+
+
+@pytest.mark.parametrize("N,K", [(3, 3), (7, 2), (10, 2)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_low_temperature_correction_matches_oracle(N, K, precision):
+    """HEOM_FLAG_LOW_TEMP at 77 K (small-N engine, complex H at N = 7, large-N engine)."""
+    w = workloads.random_instance(N, K, seed=500 + N, complex_h=(N == 7))
+    w["params"]["low_temp"] = 1
+    w["params"]["T"] = 77.0
+    g = run_gpu(w, precision)
+    o = run_oracle(w)
+    off = run_oracle(dict(w, params=dict(w["params"], low_temp=0)))
+    tp, te = (TOL64, TOL64) if precision == "fp64" else (TOL32_POP, TOL32_ETA)
+    assert np.abs(g["pops"] - o["pops"]).max() < tp
+    assert np.abs(g["eta"] - o["eta"]).max() < te
+    assert np.abs(o["pops"] - off["pops"]).max() > 20 * tp  # the correction is visible
+
+
+def test_unknown_flags_rejected():
+    w = workloads.random_instance(3, 2, seed=5)
+    p = dict(w["params"])
+    keep = heom._Keep(p, heom.FP64)
+    keep.c.flags = 6
+    h = heom.ctypes.c_void_p()
+    assert heom.lib().heom_create(heom.ctypes.byref(keep.c), None, heom.ctypes.byref(h)) == heom.EINVAL
