@@ -40,6 +40,9 @@ METRIC = "HEOM node-RHS evals/s, batched solves/s and p99 latency vs plain FP64 
 UNIT = "node-RHS evals/s"
 WORKLOAD = "FMO-like N=7 with trap: K=6 (1716 nodes), dt=1 fs for 10 ps, seed 1234"
 L2_FLUSH_BYTES = 256 << 20
+# the paper's table of GPU timings (Tesla C2050, FP32): N = 7, N_max = 6, 1716 matrices,
+# 1000 RK4 steps in 3 s -> 1716 x 4 x 1000 / 3 node-RHS evaluations per second
+PAPER_NODE_RHS_PER_S = 1716 * 4 * 1000 / 3.0
 
 
 def parse():
@@ -60,6 +63,8 @@ def parse():
                     help="mode,team_ctas,block,node_threads for the mixed path instead of autotuning (profiling runs)")
     ap.add_argument("--solve-steps", type=int, default=0,
                     help="RK4 steps per solve instead of the workload's 10 000 (profiling runs; not a bench value)")
+    ap.add_argument("--batched-steps", type=int, default=0,
+                    help="RK4 steps of the batched scan instead of its 5000 (profiling runs; not a bench value)")
     ap.add_argument("--large-steps", type=int, default=0,
                     help="RK4 steps of the 24-site workload instead of its 2000 (profiling runs; not a bench value)")
     return ap.parse_args()
@@ -408,7 +413,10 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (float-float rho_0, populations and eta)", "data": "synthetic",
+        "vs_baseline": value / PAPER_NODE_RHS_PER_S,
+        "vs_baseline_note": "against the paper's N=7, N_max=6 (1716 matrices) GPU timing on a Tesla C2050 in FP32 "
+                            "(1000 steps in 3 s = %.3g node-RHS/s); other hardware, context only" % PAPER_NODE_RHS_PER_S,
+        "dtype": "f32 (float-float rho_0, populations and eta)", "data": "synthetic",
         "config": {"workload": WORKLOAD, "global_batch": world, "seq_len": None,
                    "parallelism": "replicas x%d" % world,
                    "l2": "flushed (256 MB write) before every solve; the 1.0 MB state is L2-resident within a solve",
@@ -441,7 +449,7 @@ def main():
         "eta_10ps": float(eta_gpu[-1]),
     }
     if rank == 0 and not args.no_batched:
-        line["batched"] = bench_batched(heom, torch, stream)
+        line["batched"] = bench_batched(heom, torch, stream, args.batched_steps)
     if rank == 0 and not args.no_large:
         line["large"] = bench_large(heom, torch, stream, peak, peak_kind, args.large_steps)
     if rank == 0 and not args.no_serving:
@@ -513,10 +521,10 @@ def bench_large(heom, torch, stream, peak, peak_kind, steps=0):
     return out
 
 
-def bench_batched(heom, torch, stream):
+def bench_batched(heom, torch, stream, steps=0):
     """Batched scan: 256 seeded N = 7 trap instances, depth 4..8, lambda and T
     scanned, 5 ps each, mixed precision, one persistent launch."""
-    ws = workloads.batched_scan()
+    ws = workloads.batched_scan(nsteps=steps) if steps > 0 else workloads.batched_scan()
     b = heom.Batch([w["params"] for w in ws], "fp32", stream=stream)
     nodes = sum(heom.num_nodes(w["params"]["N"], w["params"]["K"]) for w in ws)
     nsteps = ws[0]["nsteps"]
