@@ -261,6 +261,24 @@ int heom_batch_set_launch(heom_batch* b, int32_t mode, int32_t team_ctas, int32_
 
 void heom_batch_destroy(heom_batch* b);
 
+/* CUDA graph of one batch propagate call (no counterpart in the paper: a
+ * serving-side way to replay a fixed persistent launch without host work).
+ * heom_batch_graph_create captures what heom_batch_propagate_device(b, dt_fs,
+ * nsteps, out_every, d_pops, d_eta_loss) would launch -- step counts, time
+ * steps, output pointers and launch shapes are fixed in the graph -- without
+ * running it.  Each heom_graph_launch then runs that propagation once more on
+ * the batch's stream (asynchronously; heom_batch_synchronize waits), continuing
+ * from the current state and overwriting the same output rows; heom_batch_set_rho0
+ * between launches restarts the instances.  Launch modes 0 and 2 only (mode 1
+ * gives HEOM_EUNSUPPORTED).  The batch must outlive its graphs; later
+ * heom_batch_set_launch / heom_batch_set_stop calls do not change a graph.
+ * heom_graph_destroy is NULL-safe. */
+typedef struct heom_graph heom_graph;
+int heom_batch_graph_create(heom_batch* b, const double* dt_fs, const int64_t* nsteps, int64_t out_every,
+                            double* d_pops, double* d_eta_loss, heom_graph** out);
+int heom_graph_launch(heom_graph* g);
+void heom_graph_destroy(heom_graph* g);
+
 /* -------------------------------------------------------------- serving */
 
 /* Continuous batching of propagation requests (N <= 8).  The server owns a

@@ -115,35 +115,45 @@ __global__ void __launch_bounds__(256, 1) heom_large_kernel(EngineArgs A) {
           const int n0 = tl << 5;
           __syncthreads();
           {
-            // 8 loads in flight per thread before their stores
+            // Warp w copies packed elements w, w + nwarps, ... of the 32 nodes
+            // (lane = node), 8 loads in flight before their stores; (r, c) of
+            // the packed element is stepped along without a division.
             const bool lv = n0 + lane < I.M;
-            const int total = NN * 32;
-            for (int i0 = threadIdx.x; i0 < total; i0 += 8 * blockDim.x) {
+            int r0 = 0, c0 = warp;
+            while (c0 >= N) { c0 -= N; ++r0; }
+            for (int p0 = warp; p0 < NN; p0 += 8 * nwarps) {
               R v[8];
+              int rr[8], cc[8];
+              int r = r0, c = c0;
 #pragma unroll
               for (int q = 0; q < 8; ++q) {
-                const int i = i0 + q * blockDim.x;
-                v[q] = ld_global_or0(win + ((i >> 5) * Mp + n0 + lane), lv && i < total);
+                const int pp = p0 + q * nwarps;
+                rr[q] = r;
+                cc[q] = c;
+                v[q] = ld_global_or0(win + (pp * Mp + n0 + lane), lv && pp < NN);
+                c += nwarps;
+                while (c >= N) { c -= N; ++r; }
               }
+              r0 = r;
+              c0 = c;
 #pragma unroll
               for (int q = 0; q < 8; ++q) {
-                const int i = i0 + q * blockDim.x;
-                if (i < total) {
-                  if constexpr (FULL) {
-                    // packed (r, c): Re sigma_rc for r <= c, Im sigma_cr for r > c
-                    const int pp = i >> 5, r = pp / N, c = pp - r * N, l = i & 31;
-                    if (r < c) {
-                      tile[(r * JS + c) * 32 + l] = v[q];
-                      tile[(c * JS + r) * 32 + l] = v[q];
-                    } else if (r > c) {
-                      tileA[(c * JS + r) * 32 + l] = v[q];
-                      tileA[(r * JS + c) * 32 + l] = -v[q];
-                    } else {
-                      tile[(r * JS + r) * 32 + l] = v[q];
-                    }
+                const int pp = p0 + q * nwarps;
+                if (pp >= NN) break;
+                if constexpr (FULL) {
+                  // packed (r, c): Re sigma_rc for r <= c, Im sigma_cr for r > c
+                  const int rq = rr[q], cq = cc[q];
+                  if (rq < cq) {
+                    tile[(rq * JS + cq) * 32 + lane] = v[q];
+                    tile[(cq * JS + rq) * 32 + lane] = v[q];
+                  } else if (rq > cq) {
+                    tileA[(cq * JS + rq) * 32 + lane] = v[q];
+                    tileA[(rq * JS + cq) * 32 + lane] = -v[q];
                   } else {
-                    tile[i] = v[q];
+                    tile[(rq * JS + rq) * 32 + lane] = v[q];
                   }
+                } else {
+                  tile[pp * 32 + lane] = v[q];
                 }
               }
             }
@@ -173,7 +183,7 @@ __global__ void __launch_bounds__(256, 1) heom_large_kernel(EngineArgs A) {
             //   Re += sum_k J(a,k) A(k,b) - A(a,k) J(k,b);  Im -= sum_k J(a,k) S(k,b) - S(a,k) J(k,b)
             //   Re += sum_k Ji(a,k) S(k,b) - S(a,k) Ji(k,b); Im += sum_k Ji(a,k) A(k,b) - A(a,k) Ji(k,b)
             // with S = Re sigma, A = Im sigma; J(a,k) = J(k,a) is read from row k.
-#pragma unroll 1
+#pragma unroll 2
             for (int k = 0; k < N; ++k) {
               R ja[4], jb[4];
               load_row<4>(cf + L::J(N) + k * JS + A0, ja);

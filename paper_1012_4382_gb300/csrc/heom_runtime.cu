@@ -435,6 +435,11 @@ struct Engine {
   PinnedBuf h_args;
   cudaEvent_t args_done = nullptr;
   bool args_pending = false;
+  // set while a CUDA graph of one propagate call is being built: the launch
+  // descriptors go to *graph_args (copied before the capture starts) and the
+  // launches are captured into *graph_out instead of being run
+  DevBuf* graph_args = nullptr;
+  cudaGraph_t* graph_out = nullptr;
 
   ~Engine() {
     if (args_done) {
@@ -783,6 +788,45 @@ struct Engine {
       bytes += sizeof(int32_t) * groups[k].list.size();
       bytes = (bytes + 15) / 16 * 16;
     }
+    if (graph_args) {
+      for (auto& g : groups)
+        if (g.c.mode == 1) return fail(HEOM_EUNSUPPORTED, "CUDA graphs take launch modes 0 and 2");
+      std::vector<unsigned char> hg(bytes, 0);
+      memcpy(hg.data(), hi.data(), sizeof(Inst) * count);
+      for (size_t k = 0; k < groups.size(); ++k) {
+        memcpy(hg.data() + off_first[k], groups[k].first.data(), sizeof(int32_t) * groups[k].first.size());
+        memcpy(hg.data() + off_list[k], groups[k].list.data(), sizeof(int32_t) * groups[k].list.size());
+      }
+      TRY(graph_args->alloc(bytes, hooks));
+      CUDA_TRY(cudaStreamSynchronize(stream));
+      CUDA_TRY(cudaMemcpy(graph_args->p, hg.data(), bytes, cudaMemcpyHostToDevice));
+      unsigned char* gdb = graph_args->as<unsigned char>();
+      CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+      int rc = HEOM_OK;
+      for (size_t k = 0; k < groups.size() && rc == HEOM_OK; ++k) {
+        Group& g = groups[k];
+        EngineArgs A;
+        A.insts = reinterpret_cast<const Inst*>(gdb);
+        A.team_first = reinterpret_cast<const int32_t*>(gdb + off_first[k]);
+        A.team_list = reinterpret_cast<const int32_t*>(gdb + off_list[k]);
+        A.G = g.c.G;
+        A.logG = ilog2(g.c.G);
+        A.mode = g.c.mode;
+        A.team_ctas = g.c.team_ctas;
+        A.gsync = d_gsync.as<unsigned>();
+        A.status = d_status.as<int>();
+        rc = launch(g.N, g.cplx, g.c, g.nteams, A, g.B, g.dyn);
+      }
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(stream, &graph);
+      if (rc != HEOM_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc != HEOM_OK ? rc : fail(HEOM_ECUDA, "stream capture: %s", cudaGetErrorString(ce));
+      }
+      *graph_out = graph;
+      return HEOM_OK;
+    }
     if (args_pending) {
       CUDA_TRY(cudaEventSynchronize(args_done));
       args_pending = false;
@@ -1036,6 +1080,18 @@ struct heom_ctx {
 };
 struct heom_batch {
   Engine e;
+};
+
+// One captured propagate call of a batch (heom_batch_graph_create).
+struct heom_graph {
+  Engine* e = nullptr;
+  DevBuf args;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~heom_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
 };
 
 // ------------------------------------------------------------------- C ABI
@@ -1349,6 +1405,33 @@ int heom_batch_set_stop(heom_batch* b, double stop_trace) {
   b->e.stop_trace = stop_trace;
   return HEOM_OK;
 }
+
+int heom_batch_graph_create(heom_batch* b, const double* dt_fs, const int64_t* nsteps, int64_t out_every,
+                            double* d_pops, double* d_eta_loss, heom_graph** out) {
+  if (!b || !dt_fs || !nsteps || !out) return fail(HEOM_EINVAL, "batch, dt_fs, nsteps or out is NULL");
+  *out = nullptr;
+  TRY(b->e.ensure_device());
+  std::unique_ptr<heom_graph> g(new heom_graph());
+  g->e = &b->e;
+  b->e.graph_args = &g->args;
+  b->e.graph_out = &g->graph;
+  const int rc = b->e.propagate(dt_fs, nsteps, out_every, d_pops, d_eta_loss);
+  b->e.graph_args = nullptr;
+  b->e.graph_out = nullptr;
+  if (rc != HEOM_OK) return rc;
+  CUDA_TRY(cudaGraphInstantiate(&g->exec, g->graph, 0));
+  *out = g.release();
+  return HEOM_OK;
+}
+
+int heom_graph_launch(heom_graph* g) {
+  if (!g || !g->exec) return fail(HEOM_EINVAL, "graph is NULL");
+  TRY(g->e->ensure_device());
+  CUDA_TRY(cudaGraphLaunch(g->exec, g->e->stream));
+  return HEOM_OK;
+}
+
+void heom_graph_destroy(heom_graph* g) { delete g; }
 
 int heom_batch_get_rho(heom_batch* b, int32_t i, double* rho_out) {
   if (!b || !rho_out) return fail(HEOM_EINVAL, "batch or rho_out is NULL");

@@ -95,6 +95,8 @@ def lib() -> ctypes.CDLL:
             "heom_batch_set_rho0": [vp, _dp],
             "heom_batch_propagate": [vp, _dp, _i64p, ctypes.c_int64, _dp, _dp],
             "heom_batch_propagate_device": [vp, _dp, _i64p, ctypes.c_int64, vp, vp],
+            "heom_batch_graph_create": [vp, _dp, _i64p, ctypes.c_int64, vp, vp, ctypes.POINTER(vp)],
+            "heom_graph_launch": [vp],
             "heom_batch_synchronize": [vp],
             "heom_batch_efficiency": [vp, _dp, _dp],
             "heom_batch_trapping_time": [vp, _dp, _i64p],
@@ -110,6 +112,8 @@ def lib() -> ctypes.CDLL:
         L.heom_destroy.restype = None
         L.heom_batch_destroy.argtypes = [vp]
         L.heom_batch_destroy.restype = None
+        L.heom_graph_destroy.argtypes = [vp]
+        L.heom_graph_destroy.restype = None
         L.heom_last_error.argtypes = []
         L.heom_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -396,6 +400,15 @@ class Batch:
                                                  ctypes.c_void_p(_dev_ptr(d_pops)),
                                                  ctypes.c_void_p(_dev_ptr(d_eta_loss))))
 
+    def graph(self, dt, nsteps, out_every, d_pops=None, d_eta_loss=None):
+        """Captures one propagate_device call as a CUDA graph (see Graph)."""
+        dt, ns = self._steps(dt, nsteps)
+        h = ctypes.c_void_p()
+        _check(lib().heom_batch_graph_create(self._h, _ptr(dt), ns.ctypes.data_as(_i64p), int(out_every),
+                                             ctypes.c_void_p(_dev_ptr(d_pops)), ctypes.c_void_p(_dev_ptr(d_eta_loss)),
+                                             ctypes.byref(h)))
+        return Graph(h, self)
+
     def synchronize(self):
         _check(lib().heom_batch_synchronize(self._h))
 
@@ -422,3 +435,32 @@ class Batch:
     def set_launch(self, mode=-1, team_ctas=0, block_threads=0, node_threads=0):
         _check(lib().heom_batch_set_launch(self._h, int(mode), int(team_ctas), int(block_threads),
                                            int(node_threads)))
+
+
+class Graph:
+    """A captured batch propagation (heom_batch_graph_create): each launch()
+    runs the same persistent launch again on the batch's stream."""
+
+    def __init__(self, h, batch):
+        self._h = h
+        self._batch = batch  # the batch must outlive the graph
+
+    def launch(self):
+        _check(lib().heom_graph_launch(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().heom_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
