@@ -1068,6 +1068,107 @@ __device__ __forceinline__ void node_units_rt(const Inst& I, const R* __restrict
   }
 }
 
+// ------------------------------------- one unit per warp, links in registers
+//
+// When every warp owns at most one item and every unit group holds one unit
+// (G >= N(N+1)/2: the single-instance grid launch), the node, the unit and
+// its links are the same in every stage of the call.  They are read once
+// into registers, so a stage issues only the loads of stage values, all of
+// them independent: one trip to L2 instead of two (links, then neighbours).
+template <typename R>
+struct CachedUnit {
+  bool valid = false, term = false, root = false;
+  int n = 0, a = 0, b = 0;
+  int ua = -1, ub = -1, da = -1, db = -1;
+  R na = R(0), nb = R(0), ng = R(0);
+};
+
+template <int N, typename R>
+struct CachedView {
+  const R* __restrict__ win;
+  const R* __restrict__ base;
+  R* __restrict__ wout;
+  const R* __restrict__ y;
+  int Mp;
+  const CachedUnit<R>& c;
+  __device__ __forceinline__ CachedView(const GlobalArrays<R>& g, const CachedUnit<R>& cu)
+      : win(g.win + cu.n), base(g.win), wout(g.wout + cu.n), y(g.y + cu.n), Mp(g.Mp), c(cu) {}
+  __device__ __forceinline__ R Pr(int p) const { return win[p * Mp]; }
+  // links are asked for the unit's own sites only
+  __device__ __forceinline__ int Upr(int j) const { return j == c.a ? c.ua : c.ub; }
+  __device__ __forceinline__ int Dnr(int j) const { return j == c.a ? c.da : c.db; }
+  __device__ __forceinline__ R Njr(int j) const { return j == c.a ? c.na : c.nb; }
+  __device__ __forceinline__ R Gr(int p, int h) const { return base[p * Mp + h]; }
+  __device__ __forceinline__ R Yr(int p) const { return y[p * Mp]; }
+  __device__ __forceinline__ void Str(int p, R v) const { wout[p * Mp] = v; }
+};
+
+template <int N, typename R>
+__device__ __forceinline__ CachedUnit<R> cache_unit(const Inst& I, int warp, int G, int lane) {
+  constexpr int NP = N * (N - 1) / 2;
+  constexpr int U = NP + N;
+  CachedUnit<R> c;
+  const int nblk = (I.M + 31) >> 5;
+  if (warp >= nblk * G) return c;
+  const int nb = warp / G, g = warp - nb * G;
+  const int n = (nb << 5) + lane;
+  if (n >= I.M || g >= U) return c;
+  c.valid = true;
+  c.n = n;
+  if (g < NP) unit_pair_of(N, g, c.a, c.b);
+  else c.a = c.b = g - NP;
+  const int Mp = I.Mpad;
+  c.ua = I.up[c.a * Mp + n];
+  c.ub = I.up[c.b * Mp + n];
+  const int ra = I.dn[c.a * Mp + n], rb = I.dn[c.b * Mp + n];
+  c.da = ra < 0 ? -1 : (ra & 0xFFFFFF);
+  c.db = rb < 0 ? -1 : (rb & 0xFFFFFF);
+  c.na = ra < 0 ? R(0) : R(ra >> 24);
+  c.nb = rb < 0 ? R(0) : R(rb >> 24);
+  c.ng = static_cast<const R*>(I.ngam)[n];
+  c.term = I.terminator && I.up[n] < 0;
+  c.root = n == 0;
+  return c;
+}
+
+// The one unit of a cached item, one RK4 stage (the per-unit part of node_units_rt).
+template <int N, typename R, bool MIXED, bool CPLX>
+__device__ __forceinline__ void cached_unit_stage(const Inst& I, const R* __restrict__ cf,
+                                                  const double* __restrict__ cfd, const StageCoef<R>& P,
+                                                  const CachedView<N, R>& v, const CachedUnit<R>& c, int s,
+                                                  OutStep os, EtaAcc<R>& ea) {
+  const int a = c.a, b = c.b;
+  const bool out_row = (s == 3) && c.root && I.out_pops && os.now;
+  R re, im;
+  unit_rhs_rt<N, R, CPLX>(v, cf, c.ng, c.term, a, b, re, im);
+  const int pr = a * N + b, pi = b * N + a;
+  if (MIXED && c.root) {
+    if constexpr (MIXED) {
+      if (a == b && s == 3) ea.add(I, a, P.root_in[pr]);
+      if (a == b && s == 2) ea.add_xi(I, a, P.root_in[pr]);
+      const FF wr = ff_axpy(P.root_y[pr], P.h, P.hl, re);
+      P.root_out[pr] = wr;
+      v.Str(pr, wr.h);
+      if (a != b) {
+        const FF wi = ff_axpy(P.root_y[pi], P.h, P.hl, im);
+        P.root_out[pi] = wi;
+        v.Str(pi, wi.h);
+      } else if (out_row) {
+        I.out_pops[os.row * N + a] = ff_to_double(wr);
+      }
+    }
+  } else {
+    if constexpr (!MIXED) {
+      if (c.root && a == b && s == 3) ea.add(I, cfd, N, a, (double)v.Pr(pr));
+      if (c.root && a == b && s == 2) ea.add_xi(I, cfd, a, (double)v.Pr(pr));
+    }
+    const R w = v.Yr(pr) + P.h * re;
+    v.Str(pr, w);
+    if (a != b) v.Str(pi, v.Yr(pi) + P.h * im);
+    else if (out_row) I.out_pops[os.row * N + a] = (double)w;
+  }
+}
+
 // Row 0 of the outputs (the state at the start of the call).
 template <int N, typename R, bool MIXED>
 __device__ __forceinline__ void write_row0(const Inst& I) {
@@ -1270,6 +1371,11 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, (sizeof(R) == 8 &&
     if (!team_barrier(A, epoch)) return;
 
     R* arr[3] = {static_cast<R*>(I.y), static_cast<R*>(I.wa), static_cast<R*>(I.wb)};
+    // FP32 load views with one unit per warp: the unit and its links stay in registers
+    constexpr bool CACHE_OK = !REG && sizeof(R) == 4;
+    const bool cached = CACHE_OK && G >= N * (N + 1) / 2 && items <= W;
+    CachedUnit<R> cu;
+    if (CACHE_OK && cached) cu = cache_unit<N, R>(I, warp, G, lane);
     int64_t next_out = I.out_every, orow = 1, done = I.nsteps;
     for (int64_t t = 0; t < I.nsteps; ++t) {
       const OutStep os{t + 1 == next_out, orow};
@@ -1287,7 +1393,12 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, (sizeof(R) == 8 &&
         stage_buffers(s, in_sel, out_sel);
         const StageCoef<R> P = stage_coef<R>(I, s, in_sel, out_sel);
         GlobalArrays<R> ga{arr[in_sel], arr[out_sel], arr[0], I.up, I.dn, I.Mpad};
-        for (int it = warp; it < items; it += W) {
+        if constexpr (CACHE_OK) {
+          if (cached) {
+            if (cu.valid) cached_unit_stage<N, R, MIXED, CPLX>(I, cf, cfd, P, CachedView<N, R>(ga, cu), cu, s, os, ea);
+          }
+        }
+        for (int it = warp; it < items && !(CACHE_OK && cached); it += W) {
           const int nb = it / G;
           const int g = it - nb * G;
           const int n = (nb << 5) + lane;

@@ -801,7 +801,18 @@ struct Engine {
       CUDA_TRY(cudaStreamSynchronize(stream));
       CUDA_TRY(cudaMemcpy(graph_args->p, hg.data(), bytes, cudaMemcpyHostToDevice));
       unsigned char* gdb = graph_args->as<unsigned char>();
-      CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+      // capture on a private stream (the context's stream may be the legacy
+      // default stream, which cannot be captured); launches go there meanwhile
+      cudaStream_t cs = nullptr;
+      CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      const cudaStream_t saved = stream;
+      stream = cs;
+      const cudaError_t be = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (be != cudaSuccess) {
+        stream = saved;
+        cudaStreamDestroy(cs);
+        return fail(HEOM_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(be));
+      }
       int rc = HEOM_OK;
       for (size_t k = 0; k < groups.size() && rc == HEOM_OK; ++k) {
         Group& g = groups[k];
@@ -818,7 +829,9 @@ struct Engine {
         rc = launch(g.N, g.cplx, g.c, g.nteams, A, g.B, g.dyn);
       }
       cudaGraph_t graph = nullptr;
-      const cudaError_t ce = cudaStreamEndCapture(stream, &graph);
+      const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+      stream = saved;
+      cudaStreamDestroy(cs);
       if (rc != HEOM_OK || ce != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
         cudaGetLastError();
