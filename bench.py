@@ -391,6 +391,7 @@ def main():
             e2e_times.append(time.perf_counter() - t)
     e2e_s = allreduce_max(sum(e2e_times), world)
     e2e_value = total_units / e2e_s
+    t_mean_fs, _ = ctx.trapping_time()  # <t> up to 10 ps of the last solve
     h2d = 16 * N * N
     d2h = 8 * (nout * N + 2 * nout)
 
@@ -447,6 +448,7 @@ def main():
                      "note": "the 1 MB working set is L2-resident: the launch is bound by the latency of its "
                              "40 000 dependent stages, not by a bandwidth"},
         "eta_10ps": float(eta_gpu[-1]),
+        "trapping_time_10ps_fs": t_mean_fs,
     }
     if rank == 0 and not args.no_batched:
         line["batched"] = bench_batched(heom, torch, stream, args.batched_steps)

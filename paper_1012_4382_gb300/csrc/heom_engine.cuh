@@ -1139,18 +1139,29 @@ __device__ __forceinline__ void cached_unit_stage(const Inst& I, const R* __rest
                                                   OutStep os, EtaAcc<R>& ea) {
   const int a = c.a, b = c.b;
   const bool out_row = (s == 3) && c.root && I.out_pops && os.now;
+  const int pr = a * N + b, pi = b * N + a;
+  // every load of the stage before the arithmetic: y values, and for the root
+  // its float-float y and stage input
+  const R ypr = v.Yr(pr), ypi = a != b ? v.Yr(pi) : R(0);
+  FF ry_r{0.f, 0.f}, ry_i{0.f, 0.f}, rin{0.f, 0.f};
+  if constexpr (MIXED) {
+    if (c.root) {
+      ry_r = P.root_y[pr];
+      if (a != b) ry_i = P.root_y[pi];
+      else rin = P.root_in[pr];
+    }
+  }
   R re, im;
   unit_rhs_rt<N, R, CPLX>(v, cf, c.ng, c.term, a, b, re, im);
-  const int pr = a * N + b, pi = b * N + a;
   if (MIXED && c.root) {
     if constexpr (MIXED) {
-      if (a == b && s == 3) ea.add(I, a, P.root_in[pr]);
-      if (a == b && s == 2) ea.add_xi(I, a, P.root_in[pr]);
-      const FF wr = ff_axpy(P.root_y[pr], P.h, P.hl, re);
+      if (a == b && s == 3) ea.add(I, a, rin);
+      if (a == b && s == 2) ea.add_xi(I, a, rin);
+      const FF wr = ff_axpy(ry_r, P.h, P.hl, re);
       P.root_out[pr] = wr;
       v.Str(pr, wr.h);
       if (a != b) {
-        const FF wi = ff_axpy(P.root_y[pi], P.h, P.hl, im);
+        const FF wi = ff_axpy(ry_i, P.h, P.hl, im);
         P.root_out[pi] = wi;
         v.Str(pi, wi.h);
       } else if (out_row) {
@@ -1162,9 +1173,9 @@ __device__ __forceinline__ void cached_unit_stage(const Inst& I, const R* __rest
       if (c.root && a == b && s == 3) ea.add(I, cfd, N, a, (double)v.Pr(pr));
       if (c.root && a == b && s == 2) ea.add_xi(I, cfd, a, (double)v.Pr(pr));
     }
-    const R w = v.Yr(pr) + P.h * re;
+    const R w = ypr + P.h * re;
     v.Str(pr, w);
-    if (a != b) v.Str(pi, v.Yr(pi) + P.h * im);
+    if (a != b) v.Str(pi, ypi + P.h * im);
     else if (out_row) I.out_pops[os.row * N + a] = (double)w;
   }
 }
