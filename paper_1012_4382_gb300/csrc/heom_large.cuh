@@ -10,22 +10,29 @@ namespace heom {
 // ------------------------------------------------------------ large-N engine
 //
 // Hierarchies with 9..24 sites (N is a run-time argument).  A CTA stages a
-// tile of 32 consecutive nodes' packed matrices in shared memory (element-
-// major, one lane per node, so every access is bank-conflict free).  The
-// node's outputs are cut into 4 x 4 blocks (a in A, b in B, A <= B, the
-// upper triangle); warp w computes blocks w, w + nwarps, ... of all 32 nodes.
-// Within a block the commutator is a small matrix product: for each k the
-// thread reads column k of its own sigma restricted to A and B (16 values)
-// and row k of J (two 4-vectors) and does 64 multiply-adds, so shared-memory
-// traffic per output is about a sixth of an element-by-element loop.
-// Neighbours are read from device memory, a row segment per linked node.
-// Teams and barriers are those of the small-N engine.
+// tile of 16 consecutive nodes' matrices in shared memory, element-major with
+// the 16 nodes innermost; two lanes share a node (lane = 2 x node + half), so
+// a warp covers the 16 nodes and every shared-memory access is free of bank
+// conflicts (the two lanes of a node read the same word).  The node's outputs
+// are cut into 4 x 4 blocks (a in A, b in B, A <= B, the upper triangle);
+// warp w computes blocks w, w + nwarps, ... of all 16 nodes, each lane two
+// rows of a block.  Within a block the commutator is a small matrix product:
+// for each k the thread reads sigma_ak for its two rows and sigma_kb for the
+// four columns, row k of J, and does 32 multiply-adds.  Neighbours are read
+// from device memory.  Teams and barriers are those of the small-N engine.
+//
+// FP32 keeps Re sigma and Im sigma in the tile as full, zero-padded
+// 4 ceil(N/4)-square matrices (no selects in the product loop); FP64 keeps
+// the packed matrix.  The 16-node tile (74 KB at N = 24) lets two FP32 CTAs share
+// an SM, so one CTA's loads overlap the other's arithmetic.
+constexpr int kLargeTile = 16;
 
 template <typename R, bool MIXED, bool CPLX>
-__global__ void __launch_bounds__(256, 1) heom_large_kernel(EngineArgs A) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) heom_large_kernel(EngineArgs A) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ Inst s_inst;
   __shared__ int s_stop;
+  constexpr int TN = kLargeTile;
 
   int team, rank, team_size;
   if (A.mode == 0) {
@@ -40,7 +47,10 @@ __global__ void __launch_bounds__(256, 1) heom_large_kernel(EngineArgs A) {
   const int nwarps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int slot = (rank == 0 && lane == 0) ? warp : -1;  // tile 0 is on rank 0; warp w owns blocks w, w + nwarps, ...
+  const int node = lane >> 1, half = lane & 1;
+  // tile 0 is on rank 0; its node 0 is the root, on lanes 0 and 1 of every warp
+  const int nslots = 2 * nwarps;
+  const int slot = (rank == 0 && lane < 2) ? 2 * warp + lane : -1;
   const bool lead = (rank == 0 && threadIdx.x == 0);
   unsigned epoch = 0;
 
@@ -55,24 +65,20 @@ __global__ void __launch_bounds__(256, 1) heom_large_kernel(EngineArgs A) {
     const int JS = L::JS(N);  // = 4 * number of blocks per side
     const int NB = JS / 4;
     const int nblk = NB * (NB + 1) / 2;
-    // shared memory: the tile | coefficients.  FULL (FP32): S = Re sigma and
-    // A = Im sigma as full JS x JS matrices [JS*JS][32] each, zero outside
-    // N x N; otherwise the packed matrix [NN][32] (FP64: the unpacked form
-    // would not fit).
     constexpr bool FULL = sizeof(R) == 4;
     R* tile = reinterpret_cast<R*>(dsm);
-    R* tileA = tile + JS * JS * 32;
-    unsigned char* cbytes = dsm + (size_t)(FULL ? 2 * JS * JS : NN) * 32 * sizeof(R);
+    R* tileA = tile + JS * JS * TN;
+    unsigned char* cbytes = dsm + (size_t)(FULL ? 2 * JS * JS : NN) * TN * sizeof(R);
     const int cb = L::bytes(N);
     for (int i = threadIdx.x; i < cb; i += blockDim.x) cbytes[i] = static_cast<const unsigned char*>(I.coef)[i];
     if (FULL)
-      for (int i = threadIdx.x; i < 2 * JS * JS * 32; i += blockDim.x) tile[i] = R(0);  // padding stays 0
+      for (int i = threadIdx.x; i < 2 * JS * JS * TN; i += blockDim.x) tile[i] = R(0);  // padding stays 0
     __syncthreads();
     const R* cf = reinterpret_cast<const R*>(cbytes);
     const double* cfd = reinterpret_cast<const double*>(cbytes + L::dbl_offset(N));
     const R* ngam = static_cast<const R*>(I.ngam);
     const int Mp = I.Mpad;
-    const int ntiles = (I.M + 31) >> 5;
+    const int ntiles = (I.M + TN - 1) / TN;
     EtaAcc<R> ea;
     EtaRows rows;
     rows.acc0 = I.acc[0];
@@ -86,9 +92,8 @@ __global__ void __launch_bounds__(256, 1) heom_large_kernel(EngineArgs A) {
         I.out_el[0] = I.acc[0];
         I.out_el[1] = I.acc[1];
       }
+      for (int k = 0; k < nslots; ++k) ea.store(I, k);  // zero every running-sum slot of this instance
     }
-    if (lead)
-      for (int k = 0; k < nwarps; ++k) ea.store(I, k);  // zero every running-sum slot of this instance
     if (!team_barrier(A, epoch)) return;
     R* arr[3] = {static_cast<R*>(I.y), static_cast<R*>(I.wa), static_cast<R*>(I.wb)};
     int64_t next_out = I.out_every, orow = 1, done = I.nsteps;
@@ -101,7 +106,7 @@ __global__ void __launch_bounds__(256, 1) heom_large_kernel(EngineArgs A) {
 #pragma unroll 1
       for (int s = 0; s < 4; ++s) {
         if (s == 0 && rows.pending >= 0) {
-          if (lead) eta_write_row<R>(I, nwarps, rows.acc0, rows.acc1, rows.pending);
+          if (lead) eta_write_row<R>(I, nslots, rows.acc0, rows.acc1, rows.pending);
           rows.pending = -1;
         }
         int in_sel, out_sel;
@@ -112,71 +117,77 @@ __global__ void __launch_bounds__(256, 1) heom_large_kernel(EngineArgs A) {
         R* __restrict__ wout = arr[out_sel];
         const R* __restrict__ yv = arr[0];
         for (int tl = rank; tl < ntiles; tl += team_size) {
-          const int n0 = tl << 5;
+          const int n0 = tl * TN;
           __syncthreads();
           {
-            // Warp w copies packed elements w, w + nwarps, ... of the 32 nodes
-            // (lane = node), 8 loads in flight before their stores; (r, c) of
-            // the packed element is stepped along without a division.
-            const bool lv = n0 + lane < I.M;
-            int r0 = 0, c0 = warp;
+            // thread t copies (element, node) pairs e = t, t + blockDim, ...,
+            // element e / 16 of node e % 16; 8 loads in flight before their
+            // stores; (r, c) of the packed element is stepped along.
+            const int jn = threadIdx.x & (TN - 1);
+            const bool lv = n0 + jn < I.M;
+            const int pstep = blockDim.x / TN;
+            int r0 = 0, c0 = threadIdx.x / TN;
             while (c0 >= N) { c0 -= N; ++r0; }
-            for (int p0 = warp; p0 < NN; p0 += 8 * nwarps) {
+            for (int p0 = threadIdx.x / TN; p0 < NN; p0 += 8 * pstep) {
               R v[8];
               int rr[8], cc[8];
               int r = r0, c = c0;
 #pragma unroll
               for (int q = 0; q < 8; ++q) {
-                const int pp = p0 + q * nwarps;
+                const int pp = p0 + q * pstep;
                 rr[q] = r;
                 cc[q] = c;
-                v[q] = ld_global_or0(win + (pp * Mp + n0 + lane), lv && pp < NN);
-                c += nwarps;
+                v[q] = ld_global_or0(win + (pp * Mp + n0 + jn), lv && pp < NN);
+                c += pstep;
                 while (c >= N) { c -= N; ++r; }
               }
               r0 = r;
               c0 = c;
 #pragma unroll
               for (int q = 0; q < 8; ++q) {
-                const int pp = p0 + q * nwarps;
+                const int pp = p0 + q * pstep;
                 if (pp >= NN) break;
                 if constexpr (FULL) {
                   // packed (r, c): Re sigma_rc for r <= c, Im sigma_cr for r > c
                   const int rq = rr[q], cq = cc[q];
                   if (rq < cq) {
-                    tile[(rq * JS + cq) * 32 + lane] = v[q];
-                    tile[(cq * JS + rq) * 32 + lane] = v[q];
+                    tile[(rq * JS + cq) * TN + jn] = v[q];
+                    tile[(cq * JS + rq) * TN + jn] = v[q];
                   } else if (rq > cq) {
-                    tileA[(cq * JS + rq) * 32 + lane] = v[q];
-                    tileA[(rq * JS + cq) * 32 + lane] = -v[q];
+                    tileA[(cq * JS + rq) * TN + jn] = v[q];
+                    tileA[(rq * JS + cq) * TN + jn] = -v[q];
                   } else {
-                    tile[(rq * JS + rq) * 32 + lane] = v[q];
+                    tile[(rq * JS + rq) * TN + jn] = v[q];
                   }
                 } else {
-                  tile[pp * 32 + lane] = v[q];
+                  tile[pp * TN + jn] = v[q];
                 }
               }
             }
           }
           __syncthreads();
-          const int n = n0 + lane;
+          const int n = n0 + node;
           if (n >= I.M) continue;
           const bool root = (n == 0);
           const R ng = ngam[n];
           const bool term = I.terminator && I.up[n] < 0;
           // packed element (i, j) of this lane's node; 0 outside the N x N matrix
-          auto Pk = [&](int i, int j) -> R { return (i < N && j < N) ? tile[(i * N + j) * 32 + lane] : R(0); };
+          auto Pk = [&](int i, int j) -> R { return (i < N && j < N) ? tile[(i * N + j) * TN + node] : R(0); };
           // Re sigma_ij and Im sigma_ij (FULL tile: no bounds checks, padding is 0)
-          auto Sf = [&](int i, int j) -> R { return tile[(i * JS + j) * 32 + lane]; };
-          auto Af = [&](int i, int j) -> R { return tileA[(i * JS + j) * 32 + lane]; };
+          auto Sf = [&](int i, int j) -> R { return tile[(i * JS + j) * TN + node]; };
+          auto Af = [&](int i, int j) -> R { return tileA[(i * JS + j) * TN + node]; };
+          auto Re_ = [&](int i, int j) -> R { return FULL ? Sf(i, j) : Pk(i <= j ? i : j, i <= j ? j : i); };
+          auto Im_ = [&](int i, int j) -> R {
+            return FULL ? Af(i, j) : (i < j ? Pk(j, i) : (i > j ? -Pk(i, j) : R(0)));
+          };
           for (int bk = warp; bk < nblk; bk += nwarps) {
-            // block index -> (A0, B0), A0 <= B0
+            // block index -> (A0, B0), A0 <= B0; this lane's rows A0 + 2 half + {0, 1}
             int ab = 0, rem = bk;
             while (rem >= NB - ab) { rem -= NB - ab; ++ab; }
-            const int A0 = 4 * ab, B0 = 4 * (ab + rem);
-            R re[4][4], im[4][4];
+            const int A0 = 4 * ab + 2 * half, B0 = 4 * (ab + rem);
+            R re[2][4], im[2][4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 2; ++i)
 #pragma unroll
               for (int j = 0; j < 4; ++j) re[i][j] = im[i][j] = R(0);
             // -i[H, sigma] with the real part J (symmetric) and imaginary part Ji (antisymmetric) of H:
@@ -185,38 +196,35 @@ __global__ void __launch_bounds__(256, 1) heom_large_kernel(EngineArgs A) {
             // with S = Re sigma, A = Im sigma; J(a,k) = J(k,a) is read from row k.
 #pragma unroll 2
             for (int k = 0; k < N; ++k) {
-              R ja[4], jb[4];
-              load_row<4>(cf + L::J(N) + k * JS + A0, ja);
+              R ja[2], jb[4];
+              ja[0] = cf[L::J(N) + k * JS + A0];
+              ja[1] = cf[L::J(N) + k * JS + A0 + 1];
               load_row<4>(cf + L::J(N) + k * JS + B0, jb);
-              R sak[4], aak[4], skb[4], akb[4];
+              R sak[2], aak[2], skb[4], akb[4];
 #pragma unroll
-              for (int i = 0; i < 4; ++i) {
-                const int a = A0 + i, b = B0 + i;
-                if constexpr (FULL) {
-                  sak[i] = Sf(a, k);
-                  aak[i] = Af(a, k);
-                  skb[i] = Sf(b, k);   // S(k, b) = S(b, k)
-                  akb[i] = -Af(b, k);  // A(k, b) = -A(b, k)
-                } else {
-                  sak[i] = a <= k ? Pk(a, k) : Pk(k, a);
-                  aak[i] = a < k ? Pk(k, a) : (a > k ? -Pk(a, k) : R(0));
-                  skb[i] = k <= b ? Pk(k, b) : Pk(b, k);
-                  akb[i] = k < b ? Pk(b, k) : (k > b ? -Pk(k, b) : R(0));
-                }
+              for (int i = 0; i < 2; ++i) {
+                sak[i] = Re_(A0 + i, k);
+                aak[i] = Im_(A0 + i, k);
               }
 #pragma unroll
-              for (int i = 0; i < 4; ++i)
+              for (int j = 0; j < 4; ++j) {
+                skb[j] = Re_(B0 + j, k);    // S(k, b) = S(b, k)
+                akb[j] = -Im_(B0 + j, k);   // A(k, b) = -A(b, k)
+              }
+#pragma unroll
+              for (int i = 0; i < 2; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                   re[i][j] += ja[i] * akb[j] - aak[i] * jb[j];
                   im[i][j] -= ja[i] * skb[j] - sak[i] * jb[j];
                 }
               if constexpr (CPLX) {
-                R ia[4], ib[4];  // row k of Ji: Ji(k, a) = -Ji(a, k)
-                load_row<4>(cf + L::Ji(N) + k * JS + A0, ia);
+                R ia[2], ib[4];  // row k of Ji: Ji(k, a) = -Ji(a, k)
+                ia[0] = cf[L::Ji(N) + k * JS + A0];
+                ia[1] = cf[L::Ji(N) + k * JS + A0 + 1];
                 load_row<4>(cf + L::Ji(N) + k * JS + B0, ib);
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 2; ++i)
 #pragma unroll
                   for (int j = 0; j < 4; ++j) {
                     re[i][j] -= ia[i] * skb[j] + sak[i] * ib[j];
@@ -225,32 +233,43 @@ __global__ void __launch_bounds__(256, 1) heom_large_kernel(EngineArgs A) {
               }
             }
             // links of the block's rows and columns
-            int ua[4], ub[4], da[4], db[4];
+            int ua[2], ub[4], da[2], db[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int a = A0 + q, b = B0 + q;
+            for (int q = 0; q < 2; ++q) {
+              const int a = A0 + q;
               ua[q] = a < N ? I.up[a * Mp + n] : -1;
               da[q] = a < N ? I.dn[a * Mp + n] : -1;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int b = B0 + q;
               ub[q] = b < N ? I.up[b * Mp + n] : -1;
               db[q] = b < N ? I.dn[b * Mp + n] : -1;
             }
-            // Per row of the block: the local, neighbour and terminator terms of
-            // its four outputs and their y values are loaded before any of its
-            // stores, so those loads are in flight together.
             // terminator factors (n_j + 1) / (ngam + gamma_j) of the block's rows and columns (leaf nodes)
-            R tca[4], tcb[4];
+            R tca[2], tcb[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) tca[q] = tcb[q] = R(0);
+            for (int q = 0; q < 2; ++q) tca[q] = R(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) tcb[q] = R(0);
             if (term) {
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const int a = min(A0 + q, N - 1), b = min(B0 + q, N - 1);
+              for (int q = 0; q < 2; ++q) {
+                const int a = min(A0 + q, N - 1);
                 tca[q] = ((da[q] < 0 ? R(0) : R(da[q] >> 24)) + R(1)) / (ng + cf[L::gam(N) + a]);
+              }
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const int b = min(B0 + q, N - 1);
                 tcb[q] = ((db[q] < 0 ? R(0) : R(db[q] >> 24)) + R(1)) / (ng + cf[L::gam(N) + b]);
               }
             }
+            // Per row and pair of columns: the local, neighbour and terminator
+            // terms of two outputs and their y values are loaded before their
+            // stores.
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int ij = 0; ij < 4; ++ij) {
+              const int i = ij >> 1, j0 = 2 * (ij & 1);
               R yr[4], yim[4];
               const int a = A0 + i;
               const int ac = a < N ? a : N - 1;  // clamped for addressing; outputs with a >= N are dropped
@@ -260,7 +279,7 @@ __global__ void __launch_bounds__(256, 1) heom_large_kernel(EngineArgs A) {
               const int dai = da[i] < 0 ? -1 : (da[i] & 0xFFFFFF);
               const R ca = tca[i];
 #pragma unroll
-              for (int j = 0; j < 4; ++j) {
+              for (int j = j0; j < j0 + 2; ++j) {
                 const int b = B0 + j;
                 const int bc = b < N ? b : N - 1;
                 const bool keep = a < N && b < N && b >= a;
@@ -269,7 +288,7 @@ __global__ void __launch_bounds__(256, 1) heom_large_kernel(EngineArgs A) {
                 yim[j] = ld_global_or0(yv + (pi * Mp + n), keep && a != b);
                 const R* sb = cf + L::site(N) + 4 * bc;
                 const R eps_b = sb[0], gh_b = sb[1], al_b = sb[2], be_b = sb[3];
-                const R x = FULL ? Sf(a, b) : Pk(a, b), yi = FULL ? Af(a, b) : Pk(b, a);
+                const R x = Re_(a, b), yi = Im_(a, b);
                 const int dbj = db[j] < 0 ? -1 : (db[j] & 0xFFFFFF);
                 const R nb = db[j] < 0 ? R(0) : R(db[j] >> 24);
                 // up-couplings i V_j^x sigma_{n+e_j}: j = a gives +i, j = b gives -i
@@ -304,7 +323,7 @@ __global__ void __launch_bounds__(256, 1) heom_large_kernel(EngineArgs A) {
               }
               // Horner update w = y + h r and the stores (root in float-float for mixed precision)
 #pragma unroll
-              for (int j = 0; j < 4; ++j) {
+              for (int j = j0; j < j0 + 2; ++j) {
                 const int b = B0 + j;
                 if (a >= N || b >= N || b < a) continue;
                 const int pr = a * N + b, pi = b * N + a;
@@ -326,8 +345,8 @@ __global__ void __launch_bounds__(256, 1) heom_large_kernel(EngineArgs A) {
                   }
                 } else {
                   if constexpr (!MIXED) {
-                    if (root && a == b && s == 3) ea.add(I, cfd, N, a, (double)(FULL ? Sf(a, a) : Pk(a, a)));
-                    if (root && a == b && s == 2) ea.add_xi(I, cfd, a, (double)(FULL ? Sf(a, a) : Pk(a, a)));
+                    if (root && a == b && s == 3) ea.add(I, cfd, N, a, (double)Re_(a, a));
+                    if (root && a == b && s == 2) ea.add_xi(I, cfd, a, (double)Re_(a, a));
                   }
                   const R vr = yr[j] + h * r;
                   wout[pr * Mp + n] = vr;
@@ -353,15 +372,17 @@ __global__ void __launch_bounds__(256, 1) heom_large_kernel(EngineArgs A) {
         break;
       }
     }
-    if (lead) finish_instance<R>(I, nwarps, rows, done, orow, N);
+    if (lead) finish_instance<R>(I, nslots, rows, done, orow, N);
     if (!team_barrier(A, epoch)) return;
     if (lead) signal_done(I);
   }
 }
 
 __host__ __device__ constexpr int large_smem_bytes(int N, int rsize) {
-  // FP32: unpacked S and A tiles of (4 ceil(N/4))^2 x 32; FP64: the packed tile N^2 x 32
-  return rsize == 8 ? N * N * 32 * 8 + CoefLayout<double>::bytes(N)
-                    : 2 * CoefLayout<float>::JS(N) * CoefLayout<float>::JS(N) * 32 * 4 + CoefLayout<float>::bytes(N);
+  // FP32: unpacked Re and Im tiles of (4 ceil(N/4))^2 x 16 nodes; FP64: the packed tile N^2 x 16
+  return rsize == 8 ? N * N * kLargeTile * 8 + CoefLayout<double>::bytes(N)
+                    : 2 * CoefLayout<float>::JS(N) * CoefLayout<float>::JS(N) * kLargeTile * 4 +
+                          CoefLayout<float>::bytes(N);
 }
+
 }  // namespace heom
