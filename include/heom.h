@@ -20,7 +20,11 @@
  *     with 4th-order Runge-Kutta (App. B);
  *   * the efficiency eta = <RC|rho(t)|RC> (Eq. eta), obtained as the time
  *     integral of sum_m Gamma_RC,m <m|rho|m> integrated by the same RK4, and
- *     the radiative loss <0|rho|0> likewise.
+ *     the radiative loss <0|rho|0> likewise;
+ *   * the trapping time <t> (Eq. trappingtime) and the t_max stop rule of the
+ *     section on trapping times (heom_trapping_time, heom_set_stop);
+ *   * optionally, the lowest-order quantum correction to the high-temperature
+ *     baths (HEOM_FLAG_LOW_TEMP).
  * Readings taken where the paper is ambiguous: damping term
  * -sum_m n_m gamma_m sigma_n (the printed sign in lab8 would be unstable);
  * theta_m = i (2 lambda_m k_B T V_m^x - i lambda_m gamma_m V_m^o) (the printed
