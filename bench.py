@@ -271,7 +271,7 @@ def run_reference(args):
         barrier(world)
         return
     w = workloads.fmo_trap()
-    steps = args.cpu_sample_steps or 20
+    steps = args.cpu_sample_steps or 1000  # about 2 s of host work per timed step
     for _ in range(max(args.warmup, 0)):
         oracle_sample(w, 2)
     vals = []
@@ -457,7 +457,7 @@ def main():
     if rank == 0 and not args.no_serving:
         line["serving"] = bench_serving(args.serving_requests)
     if rank == 0:
-        n_sample = args.cpu_sample_steps or 25
+        n_sample = args.cpu_sample_steps or 5000  # about 10 s of host work
         if not args.no_cpu:
             line["cpu_baseline"] = oracle_sample(w, n_sample)
         print(json.dumps(line), flush=True)
