@@ -50,6 +50,7 @@ class _Params(ctypes.Structure):
         ("terminator", ctypes.c_int32),
         ("add_reorg", ctypes.c_int32),
         ("low_temp", ctypes.c_int32),
+        ("scaled", ctypes.c_int32),
     ]
 
 
@@ -110,7 +111,7 @@ class _Keep:
         self.recomb = _f64(p.get("recomb"), N)
         self.c = _Params(N, int(p["K"]), _dptr(self.H), _dptr(self.lam), _dptr(self.gam), float(p["T"]),
                          _dptr(self.trap), _dptr(self.recomb), int(p.get("terminator", 0)),
-                         int(p.get("add_reorg", 0)), int(p.get("low_temp", 0)))
+                         int(p.get("add_reorg", 0)), int(p.get("low_temp", 0)), int(p.get("scaled", 0)))
 
 
 def set_threads(n: int) -> None:
@@ -157,7 +158,8 @@ def propagate(params: dict, rho0, dt_fs: float, nsteps: int, out_every: int = 1,
 
     ``params`` keys: N, K, H (N x N complex, cm^-1), lam, gam (cm^-1, scalar or
     per site), T (K), trap, recomb (ps^-1 per site, optional), terminator
-    (0/1), add_reorg (0/1), low_temp (0/1: low-temperature correction).
+    (0/1), add_reorg (0/1), low_temp (0/1: low-temperature correction),
+    scaled (0/1: rescaled auxiliaries; the state then holds sigma~_n).
     Returns a dict with pops [nout, N], trace [nout], eta [nout], loss [nout],
     tmean [nout] (trapping time <t> up to each row, fs), steps_done,
     rho [N, N] complex, and with ``want_state`` the full final state

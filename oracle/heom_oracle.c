@@ -41,6 +41,17 @@
  *   * the stop rule of Sec. "Trapping time": propagation ends at t_max, the
  *     first step at which the population left on the sites has dropped below
  *     a threshold (1e-5 in the paper).
+ *   * optionally the scaled hierarchy the paper points to in its introduction
+ *     (the "scaled version of the HEOM"; the formula is not printed there):
+ *     the auxiliaries are rescaled, sigma~_n = sigma_n / S(n) with
+ *     S(n) = prod_j sqrt(n_j! s_j^{n_j}) and s_j = |2 lambda_j kT - i lambda_j gamma_j|
+ *     the modulus of the bath's correlation amplitude (1 where lambda_j = 0;
+ *     the rescaling of Shi et
+ *     al., J. Chem. Phys. 130, 084105 (2009)).  Substituting sigma_n = S(n)
+ *     sigma~_n into the hierarchy gives the same equations with the up link
+ *     weighted by S(n+e_j)/S(n) = sqrt((n_j+1) s_j) and the down link's n_j
+ *     replaced by n_j S(n-e_j)/S(n) = sqrt(n_j / s_j).  S(0) = 1, so rho is the
+ *     same; the terminator term is local and unchanged.
  *
  * Readings of the paper taken here (each one is also listed in the design notes):
  *   * damping sign: lab8 prints "+ sum n_m gamma_m" inside the bracket; the
@@ -96,6 +107,7 @@ typedef struct {
   int32_t terminator;      /* 0: plain truncation, 1: Markovian terminator */
   int32_t add_reorg;       /* 1: eps_m -> eps_m + lambda_m (Eq. H_ex) */
   int32_t low_temp;        /* 1: lowest-order quantum (low-temperature) correction */
+  int32_t scaled;          /* 1: scaled auxiliaries sigma~_n = sigma_n / S(n) (see the header) */
 } oracle_params;
 
 /* ---------------------------------------------------------------------- */
@@ -216,6 +228,7 @@ typedef struct {
   double* g_rc;      /* N, fs^-1 */
   double* g_phot;    /* N, fs^-1 */
   double* ltc;       /* N, fs^-1: low-temperature correction rate per bath (0: off) */
+  double* scale;     /* N, rad^2/fs^2: s_j of the scaled hierarchy, or NULL (unscaled) */
   int terminator;
   hierarchy hier;
 } model;
@@ -227,6 +240,7 @@ static void model_free(model* m) {
   free(m->g_rc);
   free(m->g_phot);
   free(m->ltc);
+  free(m->scale);
   hier_free(&m->hier);
   memset(m, 0, sizeof(*m));
 }
@@ -274,6 +288,21 @@ static int model_build(model* m, const oracle_params* p) {
       const double x = m->gam[a] / (2.0 * m->kT);
       m->ltc[a] = 2.0 * m->lam[a] * m->kT / m->gam[a] - m->lam[a] * cos(x) / sin(x);
     }
+  if (p->scaled) {
+    m->scale = (double*)calloc((size_t)N, sizeof(double));
+    if (!m->scale) {
+      model_free(m);
+      return -1;
+    }
+    /* s_j = |c_j|, c_j = 2 lambda_j kT - i lambda_j gamma_j */
+    /* s_j = |c_j|, c_j = 2 lambda_j kT - i lambda_j gamma_j; a site without a
+     * bath (lambda_j = 0) never feeds its auxiliaries, and any s_j > 0 is a
+     * valid rescaling there: s_j = 1 */
+    for (int a = 0; a < N; ++a) {
+      m->scale[a] = cabs(2.0 * m->lam[a] * m->kT - I * m->lam[a] * m->gam[a]);
+      if (!(m->scale[a] > 0)) m->scale[a] = 1.0;
+    }
+  }
   if (hier_build(&m->hier, N, p->K) != 0) {
     model_free(m);
     return -1;
@@ -366,10 +395,13 @@ static void rhs_node(const model* m, long i, const cplx* state, cplx* out, cplx*
   for (int j = 0; j < N; ++j) ngam += n[j] * m->gam[j];
   for (size_t e = 0; e < DD; ++e) o[e] -= ngam * x[e];
   for (int j = 0; j < N; ++j) {
+    /* link weights: 1 and n_j, or sqrt((n_j+1) s_j) and sqrt(n_j / s_j) when scaled */
+    const double w_up = m->scale ? sqrt((n[j] + 1) * m->scale[j]) : 1.0;
+    const double w_dn = m->scale ? sqrt(n[j] / m->scale[j]) : (double)n[j];
     /* + i V_j^x sigma_{n+e_j} */
     long up = h->plus[i * N + j];
     if (up >= 0) {
-      add_Vcomm(D, j, I, state + up * DD, o);
+      add_Vcomm(D, j, I * w_up, state + up * DD, o);
     } else if (m->terminator == 1 && level_of(n, N) == h->K) {
       /* sigma_{n+e_j} ~ (n_j + 1) theta_j sigma_n / (sum_k n_k gamma_k + gamma_j) */
       for (size_t e = 0; e < DD; ++e) scratch[e] = 0;
@@ -378,7 +410,7 @@ static void rhs_node(const model* m, long i, const cplx* state, cplx* out, cplx*
     }
     /* + n_j theta_j sigma_{n-e_j} */
     long dn = h->minus[i * N + j];
-    if (dn >= 0) add_theta(m, j, (double)n[j], state + dn * DD, o);
+    if (dn >= 0) add_theta(m, j, w_dn, state + dn * DD, o);
   }
 }
 

@@ -307,6 +307,72 @@ def test_rk4_equals_taylor_polynomial_and_approaches_expm():
 
 
 # ----------------------------------------------------------------------------
+# Scaled hierarchy (the "scaled version of the HEOM" of the introduction):
+# sigma~_n = sigma_n / S(n), S(n) = prod_j sqrt(n_j! s_j^{n_j}), s_j = |c_j|
+# ----------------------------------------------------------------------------
+
+def _scale_of_nodes(p, multi):
+    """S(n) per node, from the multi-indices and s_j = |2 lambda kT - i lambda gamma| (rad^2/fs^2)."""
+    N = int(p["N"])
+    lam = np.broadcast_to(np.asarray(p["lam"], dtype=float), (N,)) * W
+    gam = np.broadcast_to(np.asarray(p["gam"], dtype=float), (N,)) * W
+    kT = KB * p["T"] * W
+    s = np.hypot(2.0 * lam * kT, lam * gam)
+    s = np.where(s > 0, s, 1.0)
+    return np.array([math.prod(math.sqrt(math.factorial(int(k)) * s[j] ** int(k)) for j, k in enumerate(n))
+                     for n in multi])
+
+
+@pytest.mark.parametrize("term", [0, 1])
+def test_scaled_generator_is_a_diagonal_similarity(term):
+    """L~ = S^-1 L S node block by node block: every up weight sqrt((n_j+1) s_j)
+    and down weight sqrt(n_j / s_j) is pinned against the unscaled generator."""
+    w = workloads.dimer()
+    p = dict(w["params"], trap=np.array([0.0, 0.7]), recomb=np.array([0.01, 0.01]), terminator=term,
+             lam=np.array([35.0, 80.0]), gam=np.array([106.0, 50.0]), low_temp=1)
+    N, K = 2, 4
+    nodes = oracle.num_nodes(N, K)
+    D = N + 2
+    dim = nodes * D * D
+
+    def generator(q):
+        L = np.zeros((dim, dim), dtype=complex)
+        for k in range(dim):
+            e = np.zeros(dim, dtype=complex)
+            e[k] = 1.0
+            L[:, k] = oracle.rhs(q, e.reshape(nodes, D, D)).reshape(-1)
+        return L
+
+    L = generator(p)
+    Ls = generator(dict(p, scaled=1))
+    S = np.repeat(_scale_of_nodes(p, oracle.multi_indices(N, K)), D * D)
+    assert S[0] == 1.0 and S.max() / S.min() > 10.0
+    ref = L * S[None, :] / S[:, None]
+    assert np.abs(Ls - ref).max() <= 1e-14 * np.abs(L).max()
+    assert np.abs(Ls - L).max() > 1e-3 * np.abs(L).max()  # the rescaling did change the links
+
+
+def test_scaled_propagation_gives_the_same_rho_and_rescaled_auxiliaries():
+    N = 3
+    H = workloads.fmo_like_hamiltonian(N, 1234)
+    p = dict(N=N, K=3, H=H, lam=np.array([35.0, 20.0, 60.0]), gam=np.array([106.0, 80.0, 150.0]), T=150.0,
+             trap=np.array([0.0, 0.0, 1.0]), recomb=np.full(N, 1e-3), terminator=1)
+    rho0 = workloads.pure_state(N, 0)
+    a = oracle.propagate(p, rho0, 1.0, 300, 50, want_state=True)
+    b = oracle.propagate(dict(p, scaled=1), rho0, 1.0, 300, 50, want_state=True)
+    for k in ("pops", "eta", "loss", "tmean"):
+        assert np.abs(a[k] - b[k]).max() < 1e-13, k
+    S = _scale_of_nodes(p, a["multi"])
+    assert np.abs(b["state"] - a["state"] / S[:, None, None]).max() < 1e-13 * np.abs(a["state"] / S[:, None, None]).max()
+    # the rescaled auxiliaries are of comparable size across levels
+    lev = a["multi"].sum(axis=1)
+    mag = lambda st, l: np.abs(st[lev == l]).max()
+    spread_plain = max(mag(a["state"], l) for l in range(4)) / min(mag(a["state"], l) for l in range(4))
+    spread_scaled = max(mag(b["state"], l) for l in range(4)) / min(mag(b["state"], l) for l in range(4))
+    assert spread_scaled < spread_plain
+
+
+# ----------------------------------------------------------------------------
 # Physics: long-time state of the isolated dimer is close to Gibbs
 # (Sec. "Trapping time for different temperatures": agreement above 100 K)
 # ----------------------------------------------------------------------------
