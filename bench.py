@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-scan measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-trace measurement")
     ap.add_argument("--no-large", action="store_true", help="skip the 24-site large-hierarchy measurement")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the scaled-hierarchy and low-temperature variants of the headline workload")
     ap.add_argument("--serving-requests", type=int, default=400,
                     help="requests replayed from the serving trace (the full trace has 2000)")
     ap.add_argument("--cpu-sample-steps", type=int, default=0, help="RK4 steps of the oracle sample (0: auto)")
@@ -404,6 +406,25 @@ def main():
     pops64 = d_pops.view(nout, N).cpu().numpy()
     eta64 = d_el.view(nout, 2)[:, 0].cpu().numpy()
 
+    # ---- variants of the headline solve: scaled hierarchy, low-temperature correction
+    variants = {}
+    if not args.no_variants:
+        L = results["fp32"]["launch"]
+        for name, key in (("scaled_hierarchy", "scaled"), ("low_temperature_correction", "low_temp")):
+            cv = heom.Context(dict(p, **{key: 1}), "fp32", stream=stream)
+            cv.set_launch(mode=L["mode"], team_ctas=L["team_ctas"], block_threads=L["block_threads"],
+                          node_threads=L["node_threads"])
+            timed_device(cv, 0, 1)
+            pv = timed_device(cv, 2, 0)
+            pops_v = d_pops.view(nout, N).cpu().numpy()
+            v = units_per_solve * len(pv) / (sum(pv) * 1e-3)
+            variants[name] = {"value": v, "unit": UNIT, "ms_per_solve": statistics.mean(pv),
+                              "vs_plain_mixed": v / (value / world),
+                              "max_abs_pop_diff_vs_plain_mixed": float(np.abs(pops_v - pops_gpu).max())}
+            cv.close()
+        variants["scaled_hierarchy"]["note"] = "same rho as the plain path up to float rounding"
+        variants["low_temperature_correction"]["note"] = "a change of the model: the difference is its effect"
+
     # ---- roofline of the dominant kernel (the persistent engine launch)
     launch_ms = statistics.mean(per_kernel)
     bytes_per_launch = algorithmic_bytes_per_node_step(N, 4) * nodes * nsteps
@@ -448,6 +469,7 @@ def main():
                      "note": "the 1 MB working set is L2-resident: the launch is bound by the latency of its "
                              "40 000 dependent stages, not by a bandwidth"},
         "eta_10ps": float(eta_gpu[-1]),
+        "variants": variants,
         "trapping_time_10ps_fs": t_mean_fs,
     }
     if rank == 0 and not args.no_batched:

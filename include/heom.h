@@ -24,7 +24,8 @@
  *   * the trapping time <t> (Eq. trappingtime) and the t_max stop rule of the
  *     section on trapping times (heom_trapping_time, heom_set_stop);
  *   * optionally, the lowest-order quantum correction to the high-temperature
- *     baths (HEOM_FLAG_LOW_TEMP).
+ *     baths (HEOM_FLAG_LOW_TEMP), and the scaled hierarchy the introduction
+ *     mentions (HEOM_FLAG_SCALED).
  * Readings taken where the paper is ambiguous: damping term
  * -sum_m n_m gamma_m sigma_n (the printed sign in lab8 would be unstable);
  * theta_m = i (2 lambda_m k_B T V_m^x - i lambda_m gamma_m V_m^o) (the printed
@@ -80,6 +81,20 @@ extern "C" {
                                 -sum_j c_j V_j^x V_j^x sigma_n on every node, c_j the Markovian
                                 weight of the Matsubara terms, 2 lambda_j k_B T / gamma_j -
                                 lambda_j cot(gamma_j / (2 k_B T)) (hbar = 1) */
+#define HEOM_FLAG_SCALED 2   /* scaled hierarchy (the paper's introduction names it, citing Zhu et al.,
+                                without the formula): the auxiliaries are stored as
+                                sigma~_n = sigma_n / prod_j sqrt(n_j! s_j^{n_j}), s_j = |2 lambda_j k_B T
+                                - i lambda_j gamma_j| (1 where lambda_j = 0), the rescaling of Shi et al.,
+                                J. Chem. Phys. 130, 084105 (2009).  The up link of site j then carries
+                                sqrt((n_j+1) s_j) and the down link sqrt(n_j / s_j) instead of 1 and n_j;
+                                rho, eta, loss and <t> are unchanged up to rounding, while the
+                                auxiliaries of different depths become of comparable size (the
+                                first step towards filtering small ones, which this library does
+                                not do).  heom_get_state/heom_set_state
+                                exchange sigma~_n.  Not with the register node view of
+                                HEOM_FP32_MIXED (node_threads 1 or 2) nor with mode 2: the default
+                                launch shape avoids them, and heom_set_launch asking for them fails
+                                at propagate time with HEOM_EUNSUPPORTED */
 
 /* largest supported number of sites and of hierarchy nodes per instance */
 #define HEOM_MAX_SITES 24
@@ -97,7 +112,7 @@ typedef struct heom_params {
   int32_t precision;         /* HEOM_FP64 or HEOM_FP32_MIXED */
   int32_t terminator;        /* HEOM_TERM_NONE or HEOM_TERM_MARKOV */
   int32_t add_reorg_to_H;    /* 0: H used as given; 1: lambda_m added to H_mm (Eq. H_ex) */
-  int32_t flags;             /* 0 or HEOM_FLAG_LOW_TEMP */
+  int32_t flags;             /* 0 or an OR of HEOM_FLAG_LOW_TEMP and HEOM_FLAG_SCALED */
 } heom_params;
 
 typedef struct heom_ctx heom_ctx;     /* one propagated hierarchy */
@@ -350,7 +365,7 @@ void heom_server_destroy(heom_server* s);
  * (N = 7: up to depth 8 in HEOM_FP64 and depth 9 in HEOM_FP32_MIXED; N = 8:
  * depth 6 and 7) are
  * rejected with HEOM_EINVAL and a message giving the bytes needed; only
- * N <= 8 is supported.
+ * N <= 8 is supported, and HEOM_FLAG_SCALED is not (HEOM_EUNSUPPORTED).
  *
  * Inputs: params (host, read during the call) and d_rho0, a device buffer of
  * N*N complex doubles whose upper triangle and diagonal define the Hermitian

@@ -61,7 +61,9 @@ constexpr int kStatusTimeout = 1;
 // Per-instance device descriptor (host fills it; see heom_runtime.cu).
 struct Inst {
   int32_t N, K, M, Mpad;
-  int32_t complex_h, terminator, pad0, pad1;
+  int32_t complex_h, terminator;
+  int32_t wstride;     // scaled hierarchy: K + 2, the row length of wsc
+  int32_t pad1;
   const int32_t* up;   // [N][Mpad] index of n + e_j or -1
   const int32_t* dn;   // [N][Mpad] (n_j << 24) | index of n - e_j, or -1
   void* y;             // [N*N][Mpad] packed state, element-major (R)
@@ -75,6 +77,7 @@ struct Inst {
   void* w0b;
   const void* coef;    // flat coefficient block, see CoefLayout below
   const void* ngam;    // [Mpad] sum_j n_j gamma_j per node (R)
+  const void* wsc;     // scaled hierarchy (HEOM_FLAG_SCALED): link weights (R), see scaled_up; else null
   double* acc;         // [8] eta, loss, xi = int eta dt, elapsed time (fs), steps done by the last call
                        // (read at the start of a call, written at its end)
   void* parts;         // [32] slots of kPartBytes: partial (eta, loss, xi) sums per unit group,
@@ -606,6 +609,23 @@ __device__ __forceinline__ void load_row(const R* __restrict__ p, R* out) {
   }
 }
 
+// Link weights of the scaled hierarchy.  The auxiliaries are stored as
+// sigma~_n = sigma_n / S(n), S(n) = prod_j sqrt(n_j! s_j^{n_j}) with s_j the
+// modulus of the bath amplitude 2 lambda_j kT - i lambda_j gamma_j (Shi et
+// al., J. Chem. Phys. 130, 084105 (2009); the paper's introduction names the
+// scaled hierarchy).  In these variables the up link of site j carries
+// S(n+e_j)/S(n) = sqrt((n_j+1) s_j) and the down link n_j S(n-e_j)/S(n) =
+// sqrt(n_j / s_j); the host tabulates both per site and n_j:
+// w[j * 2S + n] = sqrt((n+1) s_j), w[j * 2S + S + n] = sqrt(n / s_j), S = K + 2.
+template <typename R>
+__device__ __forceinline__ R scaled_up(const R* __restrict__ w, int S, int j, R nj) {
+  return __ldg(w + j * 2 * S + (int)nj);
+}
+template <typename R>
+__device__ __forceinline__ R scaled_dn(const R* __restrict__ w, int S, int j, R nj) {
+  return __ldg(w + j * 2 * S + S + (int)nj);
+}
+
 // Right-hand side of unit u (pair (a, b) or diagonal a) of one node.
 // Returns the real part in re and, for pairs, the imaginary part in im.
 // J is symmetric and Ji antisymmetric, so all the coefficients of a unit sit
@@ -618,9 +638,11 @@ __device__ __forceinline__ void load_row(const R* __restrict__ p, R* out) {
 // node and arithmetic is cheap (FP32, unit groups G <= 2).  Otherwise each
 // term is skipped where it is absent, which saves FP64 instructions (1/64
 // rate) and the latency of unneeded loads when a thread runs one unit.
-template <int N, int u, typename R, bool CPLX, bool BF, class V>
+// SC: scaled hierarchy, link weights from wsc (row length ws); branching form only.
+template <int N, int u, typename R, bool CPLX, bool BF, bool SC, class V>
 __device__ __forceinline__ void unit_rhs(const V& v, const R* __restrict__ cf, R ngam, bool term, const R* tc, R& re,
-                                         R& im) {
+                                         R& im, const R* __restrict__ wsc, int ws) {
+  static_assert(!(SC && BF), "the scaled hierarchy uses the branching form");
   using L = CoefLayout<R>;
   constexpr int NP = N * (N - 1) / 2;
   constexpr int JS = L::JS(N);
@@ -701,12 +723,24 @@ __device__ __forceinline__ void unit_rhs(const V& v, const R* __restrict__ cf, R
       im += n_a * (al_a * dar + be_a * dai) + n_b * (be_b * dbi - al_b * dbr);
     } else {
       if (ua != -1) {
-        re -= v.template G<pba>(ua);
-        im += v.template G<pab>(ua);
+        R gr = v.template G<pba>(ua), gi = v.template G<pab>(ua);
+        if constexpr (SC) {
+          const R w = scaled_up(wsc, ws, a, v.template Nj<a>());
+          gr *= w;
+          gi *= w;
+        }
+        re -= gr;
+        im += gi;
       }
       if (ub != -1) {
-        re += v.template G<pba>(ub);
-        im -= v.template G<pab>(ub);
+        R gr = v.template G<pba>(ub), gi = v.template G<pab>(ub);
+        if constexpr (SC) {
+          const R w = scaled_up(wsc, ws, b, v.template Nj<b>());
+          gr *= w;
+          gi *= w;
+        }
+        re += gr;
+        im -= gi;
       }
       if (term) {
         const R ca = (v.template Nj<a>() + R(1)) / (ngam + cf[L::gam(N) + a]);
@@ -715,14 +749,14 @@ __device__ __forceinline__ void unit_rhs(const V& v, const R* __restrict__ cf, R
         im += ca * (-al_a * yi + be_a * x) + cb * (-al_b * yi - be_b * x);
       }
       if (da != -1) {
-        const R n_a = v.template Nj<a>();
+        const R n_a = SC ? scaled_dn(wsc, ws, a, v.template Nj<a>()) : v.template Nj<a>();
         const R yr = v.template G<pab>(da);
         const R yy = v.template G<pba>(da);
         re += n_a * (be_a * yr - al_a * yy);
         im += n_a * (al_a * yr + be_a * yy);
       }
       if (db != -1) {
-        const R n_b = v.template Nj<b>();
+        const R n_b = SC ? scaled_dn(wsc, ws, b, v.template Nj<b>()) : v.template Nj<b>();
         const R yr = v.template G<pab>(db);
         const R yy = v.template G<pba>(db);
         re += n_b * (be_b * yr + al_b * yy);
@@ -755,7 +789,10 @@ __device__ __forceinline__ void unit_rhs(const V& v, const R* __restrict__ cf, R
     if constexpr (BF) {
       re += R(2) * v.template Nj<a>() * sa[3] * v.template G0<paa>(da);
     } else {
-      if (da != -1) re += R(2) * v.template Nj<a>() * sa[3] * v.template G<paa>(da);
+      if (da != -1) {
+        const R n_a = SC ? scaled_dn(wsc, ws, a, v.template Nj<a>()) : v.template Nj<a>();
+        re += R(2) * n_a * sa[3] * v.template G<paa>(da);
+      }
     }
   }
 }
@@ -795,7 +832,7 @@ struct Staging {
 // results first go to shared memory and are copied out after the last unit,
 // so no global store separates the loads of one unit from those of the next
 // (STG; without it the results are stored where they are computed).
-template <int N, typename R, bool MIXED, bool CPLX, int GS, int GI, bool ROOT, bool STG, bool BF, class V>
+template <int N, typename R, bool MIXED, bool CPLX, int GS, int GI, bool ROOT, bool STG, bool BF, bool SC, class V>
 __device__ __forceinline__ void node_units(const Inst& I, const R* __restrict__ cf, const double* __restrict__ cfd,
                                            const StageCoef<R>& P, const V& v, R ngam, int s, bool root,
                                            uint64_t umask, OutStep os, EtaAcc<R>& ea, const Staging<R>& sg) {
@@ -831,7 +868,7 @@ __device__ __forceinline__ void node_units(const Inst& I, const R* __restrict__ 
       if (!in_group<0, 0, u>(umask)) return;
     }
     R re, im;
-    unit_rhs<N, u, R, CPLX, BF>(v, cf, ngam, term, tc, re, im);
+    unit_rhs<N, u, R, CPLX, BF, SC>(v, cf, ngam, term, tc, re, im, static_cast<const R*>(I.wsc), I.wstride);
     if constexpr (u < NP) {
       constexpr int a = pair_a(N, u);
       constexpr int b = pair_b(N, u);
@@ -947,9 +984,9 @@ __device__ __forceinline__ void unit_pair_of(int N, int u, int& a, int& b) {
   b = a + 1 + u;
 }
 
-template <int N, typename R, bool CPLX, class V>
+template <int N, typename R, bool CPLX, bool SC, class V>
 __device__ __forceinline__ void unit_rhs_rt(const V& v, const R* __restrict__ cf, R ngam, bool term, int a, int b,
-                                            R& re, R& im) {
+                                            R& re, R& im, const R* __restrict__ wsc, int ws) {
   using L = CoefLayout<R>;
   constexpr int JS = L::JS(N);
   // packed element (k, l): Re sigma_kl for k <= l, Im sigma_lk for k > l
@@ -982,12 +1019,24 @@ __device__ __forceinline__ void unit_rhs_rt(const V& v, const R* __restrict__ cf
     const R al_a = sa[2], be_a = sa[3], al_b = sb[2], be_b = sb[3];
     const int ua = v.Upr(a), ub = v.Upr(b);
     if (ua != -1) {
-      re -= v.Gr(pba, ua);
-      im += v.Gr(pab, ua);
+      R gr = v.Gr(pba, ua), gi = v.Gr(pab, ua);
+      if constexpr (SC) {
+        const R w = scaled_up(wsc, ws, a, v.Njr(a));
+        gr *= w;
+        gi *= w;
+      }
+      re -= gr;
+      im += gi;
     }
     if (ub != -1) {
-      re += v.Gr(pba, ub);
-      im -= v.Gr(pab, ub);
+      R gr = v.Gr(pba, ub), gi = v.Gr(pab, ub);
+      if constexpr (SC) {
+        const R w = scaled_up(wsc, ws, b, v.Njr(b));
+        gr *= w;
+        gi *= w;
+      }
+      re += gr;
+      im -= gi;
     }
     if (term) {
       const R ca = (v.Njr(a) + R(1)) / (ngam + cf[L::gam(N) + a]);
@@ -997,13 +1046,13 @@ __device__ __forceinline__ void unit_rhs_rt(const V& v, const R* __restrict__ cf
     }
     const int da = v.Dnr(a), db = v.Dnr(b);
     if (da != -1) {
-      const R n_a = v.Njr(a);
+      const R n_a = SC ? scaled_dn(wsc, ws, a, v.Njr(a)) : v.Njr(a);
       const R yr = v.Gr(pab, da), yy = v.Gr(pba, da);
       re += n_a * (be_a * yr - al_a * yy);
       im += n_a * (al_a * yr + be_a * yy);
     }
     if (db != -1) {
-      const R n_b = v.Njr(b);
+      const R n_b = SC ? scaled_dn(wsc, ws, b, v.Njr(b)) : v.Njr(b);
       const R yr = v.Gr(pab, db), yy = v.Gr(pba, db);
       re += n_b * (be_b * yr + al_b * yy);
       im += n_b * (be_b * yy - al_b * yr);
@@ -1018,12 +1067,12 @@ __device__ __forceinline__ void unit_rhs_rt(const V& v, const R* __restrict__ cf
     }
     re -= (ngam + R(2) * cf[L::gd(N) + a]) * x;
     const int da = v.Dnr(a);
-    if (da != -1) re += R(2) * v.Njr(a) * sa[3] * v.Gr(paa, da);
+    if (da != -1) re += R(2) * (SC ? scaled_dn(wsc, ws, a, v.Njr(a)) : v.Njr(a)) * sa[3] * v.Gr(paa, da);
   }
 }
 
 // node_units for load views: the units in umask, one compact body.
-template <int N, typename R, bool MIXED, bool CPLX, class V>
+template <int N, typename R, bool MIXED, bool CPLX, bool SC, class V>
 __device__ __forceinline__ void node_units_rt(const Inst& I, const R* __restrict__ cf,
                                               const double* __restrict__ cfd, const StageCoef<R>& P, const V& v,
                                               R ngam, int s, bool root, uint64_t umask, OutStep os,
@@ -1038,7 +1087,7 @@ __device__ __forceinline__ void node_units_rt(const Inst& I, const R* __restrict
     if (u < NP) unit_pair_of(N, u, a, b);
     else a = b = u - NP;
     R re, im;
-    unit_rhs_rt<N, R, CPLX>(v, cf, ngam, term, a, b, re, im);
+    unit_rhs_rt<N, R, CPLX, SC>(v, cf, ngam, term, a, b, re, im, static_cast<const R*>(I.wsc), I.wstride);
     const int pr = a * N + b, pi = b * N + a;
     if (MIXED && root) {
       if constexpr (MIXED) {
@@ -1132,7 +1181,7 @@ __device__ __forceinline__ CachedUnit<R> cache_unit(const Inst& I, int warp, int
 }
 
 // The one unit of a cached item, one RK4 stage (the per-unit part of node_units_rt).
-template <int N, typename R, bool MIXED, bool CPLX>
+template <int N, typename R, bool MIXED, bool CPLX, bool SC>
 __device__ __forceinline__ void cached_unit_stage(const Inst& I, const R* __restrict__ cf,
                                                   const double* __restrict__ cfd, const StageCoef<R>& P,
                                                   const CachedView<N, R>& v, const CachedUnit<R>& c, int s,
@@ -1152,7 +1201,7 @@ __device__ __forceinline__ void cached_unit_stage(const Inst& I, const R* __rest
     }
   }
   R re, im;
-  unit_rhs_rt<N, R, CPLX>(v, cf, c.ng, c.term, a, b, re, im);
+  unit_rhs_rt<N, R, CPLX, SC>(v, cf, c.ng, c.term, a, b, re, im, static_cast<const R*>(I.wsc), I.wstride);
   if (MIXED && c.root) {
     if constexpr (MIXED) {
       if (a == b && s == 3) ea.add(I, a, rin);
@@ -1311,9 +1360,12 @@ __host__ __device__ constexpr int engine_dyn_bytes(int N, int block, int rsize, 
   return (reg && rsize == 4) ? (block / 32) * N * N * 32 * rsize : 0;
 }
 
-template <int N, typename R, bool MIXED, bool CPLX, bool REG>
+// SC: scaled hierarchy (link weights from Inst::wsc); not with the FP32
+// register view, whose branch-free units take no weights.
+template <int N, typename R, bool MIXED, bool CPLX, bool REG, bool SC = false>
 __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, (sizeof(R) == 8 && !REG) ? 2 : 1)
     heom_engine_kernel(EngineArgs A) {
+  static_assert(!(SC && REG && sizeof(R) == 4), "no scaled FP32 register view");
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ __align__(16) unsigned char s_coef[CoefLayout<R>::bytes(kMaxSmallN) + 64];
   __shared__ FF s_rootff[kMaxSmallN * kMaxSmallN];
@@ -1411,7 +1463,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, (sizeof(R) == 8 &&
         GlobalArrays<R> ga{arr[in_sel], arr[out_sel], arr[0], I.up, I.dn, I.Mpad};
         if constexpr (CACHE_OK) {
           if (cached) {
-            if (cu.valid) cached_unit_stage<N, R, MIXED, CPLX>(I, cf, cfd, P, CachedView<N, R>(ga, cu), cu, s, os, ea);
+            if (cu.valid) cached_unit_stage<N, R, MIXED, CPLX, SC>(I, cf, cfd, P, CachedView<N, R>(ga, cu), cu, s, os, ea);
           }
         }
         for (int it = warp; it < items && !(CACHE_OK && cached); it += W) {
@@ -1427,19 +1479,22 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, (sizeof(R) == 8 &&
           // unit code costs more in instruction fetch than the root branches).
           constexpr bool BF = REG && sizeof(R) == 4;
           if constexpr (!REG && sizeof(R) == 4) {
-            node_units_rt<N, R, MIXED, CPLX>(I, cf, cfd, P, v, ng, s, n == 0, s_umask[g], os, ea);
+            node_units_rt<N, R, MIXED, CPLX, SC>(I, cf, cfd, P, v, ng, s, n == 0, s_umask[g], os, ea);
           } else if constexpr (!BF) {
-            node_units<N, R, MIXED, CPLX, 0, 0, true, false, false>(I, cf, cfd, P, v, ng, s, n == 0, s_umask[g],
-                                                                    os, ea, sg);
+            node_units<N, R, MIXED, CPLX, 0, 0, true, false, false, SC>(I, cf, cfd, P, v, ng, s, n == 0,
+                                                                        s_umask[g], os, ea, sg);
           } else if (nb == 0) {
-            node_units<N, R, MIXED, CPLX, 0, 0, true, true, true>(I, cf, cfd, P, v, ng, s, n == 0, s_umask[g], os,
-                                                                  ea, sg);
+            node_units<N, R, MIXED, CPLX, 0, 0, true, true, true, false>(I, cf, cfd, P, v, ng, s, n == 0,
+                                                                         s_umask[g], os, ea, sg);
           } else if (G == 1) {
-            node_units<N, R, MIXED, CPLX, 1, 0, false, true, true>(I, cf, cfd, P, v, ng, s, false, 0, os, ea, sg);
+            node_units<N, R, MIXED, CPLX, 1, 0, false, true, true, false>(I, cf, cfd, P, v, ng, s, false, 0, os, ea,
+                                                                          sg);
           } else if (g == 0) {  // G == 2
-            node_units<N, R, MIXED, CPLX, 2, 0, false, true, true>(I, cf, cfd, P, v, ng, s, false, 0, os, ea, sg);
+            node_units<N, R, MIXED, CPLX, 2, 0, false, true, true, false>(I, cf, cfd, P, v, ng, s, false, 0, os, ea,
+                                                                          sg);
           } else {
-            node_units<N, R, MIXED, CPLX, 2, 1, false, true, true>(I, cf, cfd, P, v, ng, s, false, 0, os, ea, sg);
+            node_units<N, R, MIXED, CPLX, 2, 1, false, true, true, false>(I, cf, cfd, P, v, ng, s, false, 0, os, ea,
+                                                                          sg);
           }
         }
         if (s == 2 && slot >= 0) ea.step_xi(I);
@@ -1594,7 +1649,7 @@ __global__ void __launch_bounds__(512) heom_smem_kernel(EngineArgs A, int B) {
           const int l = (nb << 5) + lane;
           if (l >= nloc) continue;
           const SmemView<N, REG> v(sa, l);
-          node_units<N, float, true, CPLX, 0, 0, true, false, false>(I, cf, cfd, P, v, sng[l], s, rank == 0 && l == 0,
+          node_units<N, float, true, CPLX, 0, 0, true, false, false, false>(I, cf, cfd, P, v, sng[l], s, rank == 0 && l == 0,
                                                                      s_umask[g], os, ea,
                                                                      Staging<float>{nullptr, nullptr, nullptr});
         }

@@ -12,15 +12,23 @@ const void* engine_kernel_f64_real(int N, bool reg);
 const void* engine_kernel_f64_cplx(int N, bool reg);
 const void* engine_kernel_f32_real(int N, bool reg);
 const void* engine_kernel_f32_cplx(int N, bool reg);
+// Scaled hierarchies (HEOM_FLAG_SCALED), N = 1..8, load views only.
+const void* engine_kernel_scaled_f64(int N, bool cplx);
+const void* engine_kernel_scaled_f32(int N, bool cplx);
 // Large-N engine (9..24 sites).
-const void* large_kernel(bool fp64, bool cplx);
+const void* large_kernel(bool fp64, bool cplx, bool scaled);
 // Distributed-shared-memory engine (mixed precision only).
 const void* smem_kernel_f32_real(int N, bool reg);
 const void* smem_kernel_f32_cplx(int N, bool reg);
 inline const void* smem_kernel(bool cplx, bool reg, int N) {
   return cplx ? smem_kernel_f32_cplx(N, reg) : smem_kernel_f32_real(N, reg);
 }
-inline const void* engine_kernel(bool fp64, bool cplx, bool reg, int N) {
+// nullptr where there is no such kernel (N > 8, or a scaled register view)
+inline const void* engine_kernel(bool fp64, bool cplx, bool reg, int N, bool scaled = false) {
+  if (scaled) {
+    if (reg) return nullptr;
+    return fp64 ? engine_kernel_scaled_f64(N, cplx) : engine_kernel_scaled_f32(N, cplx);
+  }
   if (fp64) return cplx ? engine_kernel_f64_cplx(N, reg) : engine_kernel_f64_real(N, reg);
   return cplx ? engine_kernel_f32_cplx(N, reg) : engine_kernel_f32_real(N, reg);
 }

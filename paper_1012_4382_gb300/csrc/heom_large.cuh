@@ -27,7 +27,8 @@ namespace heom {
 // an SM, so one CTA's loads overlap the other's arithmetic.
 constexpr int kLargeTile = 16;
 
-template <typename R, bool MIXED, bool CPLX>
+// SC: scaled hierarchy, link weights from Inst::wsc (see scaled_up).
+template <typename R, bool MIXED, bool CPLX, bool SC = false>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) heom_large_kernel(EngineArgs A) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ Inst s_inst;
@@ -275,8 +276,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) heom_large_kernel
               const int ac = a < N ? a : N - 1;  // clamped for addressing; outputs with a >= N are dropped
               const R* sa = cf + L::site(N) + 4 * ac;
               const R eps_a = sa[0], gh_a = sa[1], al_a = sa[2], be_a = sa[3];
-              const R na = da[i] < 0 ? R(0) : R(da[i] >> 24);
+              R na = da[i] < 0 ? R(0) : R(da[i] >> 24);
               const int dai = da[i] < 0 ? -1 : (da[i] & 0xFFFFFF);
+              R wua = R(1);  // up-link weight of row a (scaled hierarchy)
+              if constexpr (SC) {
+                wua = scaled_up(static_cast<const R*>(I.wsc), I.wstride, ac, na);
+                na = scaled_dn(static_cast<const R*>(I.wsc), I.wstride, ac, na);
+              }
               const R ca = tca[i];
 #pragma unroll
               for (int j = j0; j < j0 + 2; ++j) {
@@ -290,7 +296,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) heom_large_kernel
                 const R eps_b = sb[0], gh_b = sb[1], al_b = sb[2], be_b = sb[3];
                 const R x = Re_(a, b), yi = Im_(a, b);
                 const int dbj = db[j] < 0 ? -1 : (db[j] & 0xFFFFFF);
-                const R nb = db[j] < 0 ? R(0) : R(db[j] >> 24);
+                R nb = db[j] < 0 ? R(0) : R(db[j] >> 24);
+                R wub = R(1);
+                if constexpr (SC) {
+                  wub = scaled_up(static_cast<const R*>(I.wsc), I.wstride, bc, nb);
+                  nb = scaled_dn(static_cast<const R*>(I.wsc), I.wstride, bc, nb);
+                }
                 // up-couplings i V_j^x sigma_{n+e_j}: j = a gives +i, j = b gives -i
                 const R uar = ld_global_or0(win + (pr * Mp + ua[i]), keep && a != b && ua[i] >= 0);
                 const R uai = ld_global_or0(win + (pi * Mp + ua[i]), keep && a != b && ua[i] >= 0);
@@ -307,8 +318,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) heom_large_kernel
                   const R c = ng + gh_a + gh_b;
                   r += d * yi - c * x;
                   m -= d * x + c * yi;
-                  r += ubi - uai;
-                  m += uar - ubr;
+                  if constexpr (SC) {
+                    r += wub * ubi - wua * uai;
+                    m += wua * uar - wub * ubr;
+                  } else {
+                    r += ubi - uai;
+                    m += uar - ubr;
+                  }
                   const R cbf = tcb[j];
                   r += ca * (-al_a * x - be_a * yi) + cbf * (-al_b * x + be_b * yi);
                   m += ca * (-al_a * yi + be_a * x) + cbf * (-al_b * yi - be_b * x);

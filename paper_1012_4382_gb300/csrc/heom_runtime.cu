@@ -240,6 +240,8 @@ struct Instance {
   int64_t M = 0;
   int Mpad = 0;
   int complex_h = 0, terminator = 0;
+  int scaled = 0;            // HEOM_FLAG_SCALED: link weights follow the coefficient block
+  size_t wsc_offset = 0;     // byte offset of the weights in coef
   std::shared_ptr<Tables> tab;
   DevBuf y, wa, wb, root64, coef, acc, stage, ngam;
   std::vector<unsigned char> coef_host;
@@ -325,11 +327,46 @@ void write_coefficients(const heom_params& p, unsigned char* out, int* complex_h
   *complex_h = cplx;
 }
 
-// The same into a host vector (the instance's copy of its coefficients).
+// Scale s_a of the scaled hierarchy (HEOM_FLAG_SCALED), rad^2/fs^2: the
+// modulus of the bath amplitude 2 lambda kT - i lambda gamma whose powers the
+// auxiliaries are divided by, sigma~_n = sigma_n / prod_j sqrt(n_j! s_j^{n_j})
+// (Shi et al., J. Chem. Phys. 130, 084105 (2009)); 1 for a site without a
+// bath, whose auxiliaries stay zero whatever the scale.
+double scaled_hierarchy_scale(const heom_params& p, int a) {
+  const double kT = kBoltzmannCmPerK * p.T_kelvin * kCmToRadPerFs;
+  const double lam = p.lambda[a] * kCmToRadPerFs;
+  const double gam = p.gamma[a] * kCmToRadPerFs;
+  const double s = std::hypot(2.0 * lam * kT, lam * gam);
+  return s > 0.0 ? s : 1.0;
+}
+
+// The coefficient block into a host vector (the instance's copy of its
+// coefficients); for a scaled hierarchy followed, 16-byte aligned, by the link
+// weights w[j][0][n] = sqrt((n+1) s_j) (up link of site j at n_j = n) and
+// w[j][1][n] = sqrt(n / s_j) (down link), n = 0..K+1, whose byte offset goes
+// to *wsc_offset (0 when unscaled).
 template <typename R>
-void fill_coefficients(const heom_params& p, std::vector<unsigned char>& out, int* complex_h) {
-  out.assign(CoefLayout<R>::bytes(p.N), 0);
+void fill_coefficients(const heom_params& p, std::vector<unsigned char>& out, int* complex_h, size_t* wsc_offset) {
+  const size_t base = CoefLayout<R>::bytes(p.N);
+  *wsc_offset = 0;
+  if (!(p.flags & HEOM_FLAG_SCALED)) {
+    out.assign(base, 0);
+    write_coefficients<R>(p, out.data(), complex_h);
+    return;
+  }
+  const size_t off = (base + 15) / 16 * 16;
+  const int S = p.K + 2;
+  out.assign(off + sizeof(R) * 2 * (size_t)S * p.N, 0);
   write_coefficients<R>(p, out.data(), complex_h);
+  R* w = reinterpret_cast<R*>(out.data() + off);
+  for (int j = 0; j < p.N; ++j) {
+    const double sj = scaled_hierarchy_scale(p, j);
+    for (int n = 0; n < S; ++n) {
+      w[(size_t)j * 2 * S + n] = (R)std::sqrt((n + 1) * sj);
+      w[(size_t)j * 2 * S + S + n] = (R)std::sqrt(n / sj);
+    }
+  }
+  *wsc_offset = off;
 }
 
 int validate(const heom_params* p, int idx) {
@@ -347,7 +384,8 @@ int validate(const heom_params* p, int idx) {
     return fail(HEOM_EINVAL, "params[%d]: unknown terminator %d", idx, p->terminator);
   if (p->add_reorg_to_H != 0 && p->add_reorg_to_H != 1)
     return fail(HEOM_EINVAL, "params[%d]: add_reorg_to_H must be 0 or 1", idx);
-  if (p->flags & ~HEOM_FLAG_LOW_TEMP) return fail(HEOM_EINVAL, "params[%d]: unknown flags 0x%x", idx, p->flags);
+  if (p->flags & ~(HEOM_FLAG_LOW_TEMP | HEOM_FLAG_SCALED))
+    return fail(HEOM_EINVAL, "params[%d]: unknown flags 0x%x", idx, p->flags);
   const int N = p->N;
   double scale = 0.0;
   for (int i = 0; i < 2 * N * N; ++i) {
@@ -498,7 +536,22 @@ struct Engine {
     return HEOM_OK;
   }
 
+  // Default launch shape for the instances with N sites.  Scaled hierarchies
+  // (N <= 8) need a load view (node_threads >= 3) in mode 0 or 1: where any
+  // instance of this N is scaled the plain default is moved there.
   LaunchCfg default_cfg(int N, int count) const {
+    LaunchCfg c = default_cfg_plain(N, count);
+    bool sc = false;
+    for (auto& in : inst) sc |= (in->N == N && in->scaled);
+    if (sc && N <= heom::kMaxSmallN) {
+      if (c.mode == 2) c.mode = 0;
+      const int U = N * (N + 1) / 2;
+      if (c.G <= 2) c.G = std::max(3, std::min(8, U));
+    }
+    return c;
+  }
+
+  LaunchCfg default_cfg_plain(int N, int count) const {
     LaunchCfg c;
     int64_t Mmax = 0;
     for (auto& in : inst)
@@ -565,10 +618,11 @@ struct Engine {
     in->M = heom::num_nodes(p.N, p.K);
     in->Mpad = (int)((in->M + 31) / 32 * 32);
     in->terminator = p.terminator;
+    in->scaled = (p.flags & HEOM_FLAG_SCALED) ? 1 : 0;
     if (prec == HEOM_FP64)
-      fill_coefficients<double>(p, in->coef_host, &in->complex_h);
+      fill_coefficients<double>(p, in->coef_host, &in->complex_h, &in->wsc_offset);
     else
-      fill_coefficients<float>(p, in->coef_host, &in->complex_h);
+      fill_coefficients<float>(p, in->coef_host, &in->complex_h, &in->wsc_offset);
     auto key = std::make_pair(p.N, p.K);
     auto it = tables->find(key);
     if (it == tables->end()) {
@@ -698,6 +752,8 @@ struct Engine {
                                                                               : CoefLayout<float>::dbl_offset(in.N))));
       d.coef = in.coef.p;
       d.ngam = in.ngam.p;
+      d.wsc = in.scaled ? in.coef.as<unsigned char>() + in.wsc_offset : nullptr;
+      d.wstride = in.K + 2;
       d.acc = in.acc.as<double>();
       d.out_pops = d_pops ? d_pops + pop_off : nullptr;
       d.out_el = d_el ? d_el + 2 * row_off : nullptr;
@@ -719,6 +775,8 @@ struct Engine {
     struct Group {
       int N;
       int cplx;
+      int sc;          // scaled hierarchies
+
       int B = 0;       // nodes per CTA (mode 2)
       int dyn = 0;     // dynamic shared memory per CTA
       LaunchCfg c;
@@ -726,12 +784,14 @@ struct Engine {
       std::vector<int32_t> first, list;
     };
     std::vector<Group> groups;
-    std::map<std::pair<int, int>, std::vector<int>> byN;
-    for (int i = 0; i < count; ++i) byN[std::make_pair(inst[i]->N, inst[i]->complex_h)].push_back(i);
+    std::map<std::tuple<int, int, int>, std::vector<int>> byN;
+    for (int i = 0; i < count; ++i)
+      byN[std::make_tuple(inst[i]->N, inst[i]->complex_h, inst[i]->scaled)].push_back(i);
     for (auto& kv : byN) {
       Group g;
-      g.N = kv.first.first;
-      g.cplx = kv.first.second;
+      g.N = std::get<0>(kv.first);
+      g.cplx = std::get<1>(kv.first);
+      g.sc = std::get<2>(kv.first);
       g.c = cfg[g.N];
       std::vector<int>& ids = kv.second;
       if (g.N > heom::kMaxSmallN) {
@@ -753,7 +813,7 @@ struct Engine {
       if (g.c.mode == 1) {
         g.nteams = 1;
       } else {
-        int maxc = max_active_teams(g.N, g.cplx, g.c, g.dyn);
+        int maxc = max_active_teams(g.N, g.cplx, g.sc, g.c, g.dyn);
         if (maxc < 1) return HEOM_ECUDA;
         g.nteams = std::max(1, std::min<int>((int)ids.size(), maxc));
       }
@@ -826,7 +886,7 @@ struct Engine {
         A.team_ctas = g.c.team_ctas;
         A.gsync = d_gsync.as<unsigned>();
         A.status = d_status.as<int>();
-        rc = launch(g.N, g.cplx, g.c, g.nteams, A, g.B, g.dyn);
+        rc = launch(g.N, g.cplx, g.sc, g.c, g.nteams, A, g.B, g.dyn);
       }
       cudaGraph_t graph = nullptr;
       const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
@@ -874,15 +934,22 @@ struct Engine {
       A.team_ctas = g.c.team_ctas;
       A.gsync = d_gsync.as<unsigned>();
       A.status = d_status.as<int>();
-      TRY(launch(g.N, g.cplx, g.c, g.nteams, A, g.B, g.dyn));
+      TRY(launch(g.N, g.cplx, g.sc, g.c, g.nteams, A, g.B, g.dyn));
     }
     return HEOM_OK;
   }
 
-  const void* kernel_for(int N, int cplx, const LaunchCfg& c) const {
-    if (N > heom::kMaxSmallN) return c.mode == 2 ? nullptr : heom::large_kernel(prec == HEOM_FP64, cplx != 0);
-    if (c.mode == 2) return prec == HEOM_FP64 ? nullptr : heom::smem_kernel(cplx != 0, c.G <= 2, N);
-    return heom::engine_kernel(prec == HEOM_FP64, cplx != 0, c.G <= 2, N);
+  // The kernel of a launch shape, or nullptr where none is built: mode 2 for
+  // FP64 or N > 8; scaled hierarchies in mode 2 or with the register view
+  // (node_threads <= 2) for N <= 8.
+  const void* kernel_for(int N, int cplx, int sc, const LaunchCfg& c) const {
+    if (N > heom::kMaxSmallN) return c.mode == 2 ? nullptr : heom::large_kernel(prec == HEOM_FP64, cplx != 0, sc != 0);
+    if (c.mode == 2) return (prec == HEOM_FP64 || sc) ? nullptr : heom::smem_kernel(cplx != 0, c.G <= 2, N);
+    return heom::engine_kernel(prec == HEOM_FP64, cplx != 0, c.G <= 2, N, sc != 0);
+  }
+  static const char* no_kernel_reason(int N, int sc) {
+    if (sc && N <= heom::kMaxSmallN) return " (scaled hierarchies take modes 0 and 1 with node_threads >= 3)";
+    return "";
   }
 
   // Nodes per CTA when a cluster of `ctas` CTAs holds M nodes (mode 2).
@@ -897,9 +964,14 @@ struct Engine {
     return optin - 4096;  // the kernel's static shared memory
   }
 
-  int max_active_teams(int N, int cplx, const LaunchCfg& c, int dyn = 0) {
-    const void* k = kernel_for(N, cplx, c);
-    if (!k) return fail(HEOM_EUNSUPPORTED, "no engine kernel for N=%d (launch mode %d)", N, c.mode);
+  // Teams of this shape that fit on the GPU at once; 0 on error (message set).
+  int max_active_teams(int N, int cplx, int sc, const LaunchCfg& c, int dyn = 0) {
+    const void* k = kernel_for(N, cplx, sc, c);
+    if (!k) {
+      fail(HEOM_EUNSUPPORTED, "no engine kernel for N=%d, launch mode %d, node_threads %d%s", N, c.mode, c.G,
+           no_kernel_reason(N, sc));
+      return 0;
+    }
     if (c.team_ctas > 8) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     if (dyn > 0) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
     cudaLaunchConfig_t lc = {};
@@ -926,9 +998,11 @@ struct Engine {
     return n;
   }
 
-  int launch(int N, int cplx, const LaunchCfg& c, int nteams, EngineArgs& A, int B = 0, int dyn = 0) {
-    const void* k = kernel_for(N, cplx, c);
-    if (!k) return fail(HEOM_EUNSUPPORTED, "no engine kernel for N=%d (launch mode %d)", N, c.mode);
+  int launch(int N, int cplx, int sc, const LaunchCfg& c, int nteams, EngineArgs& A, int B = 0, int dyn = 0) {
+    const void* k = kernel_for(N, cplx, sc, c);
+    if (!k)
+      return fail(HEOM_EUNSUPPORTED, "no engine kernel for N=%d, launch mode %d, node_threads %d%s", N, c.mode, c.G,
+                  no_kernel_reason(N, sc));
     if (c.mode == 1) {
       int per_sm = 0;
       if (dyn > 0) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
@@ -1326,7 +1400,7 @@ int heom_autotune(heom_ctx* ctx, int64_t trial_steps, double* best_us_per_step) 
     const int dyn = large ? heom::large_smem_bytes(in.N, (int)e.rsize())
                           : (c.mode == 2 ? heom::smem_dyn_bytes(in.N, Engine::smem_slice(in.M, c.team_ctas))
                                          : heom::engine_dyn_bytes(in.N, c.block, (int)e.rsize(), c.G <= 2));
-    if (c.mode != 1 && e.max_active_teams(in.N, in.complex_h, c, dyn) < 1) {
+    if (c.mode != 1 && e.max_active_teams(in.N, in.complex_h, in.scaled, c, dyn) < 1) {
       t_err.clear();
       continue;
     }
@@ -1524,6 +1598,8 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
   TRY(validate(params, 0));
   if (params->N > heom::kMaxSmallN)
     return fail(HEOM_EINVAL, "the allocation-free entry point takes at most %d sites", heom::kMaxSmallN);
+  if (params->flags & HEOM_FLAG_SCALED)
+    return fail(HEOM_EUNSUPPORTED, "the allocation-free entry point does not take HEOM_FLAG_SCALED");
   if (!d_rho0) return fail(HEOM_EINVAL, "d_rho0 is NULL");
   if (nsteps < 0) return fail(HEOM_EINVAL, "nsteps < 0");
   if (out_every < 1) return fail(HEOM_EINVAL, "out_every must be >= 1");
@@ -1817,7 +1893,10 @@ size_t request_bytes(const heom_params& p, bool tables_cached) {
   const int64_t M = heom::num_nodes(p.N, p.K);
   const size_t Mpad = (size_t)((M + 31) / 32 * 32);
   const size_t NN = (size_t)p.N * p.N;
-  size_t b = 3 * r(NN * Mpad * rs) + r(Mpad * rs) + r(3 * 8 * NN + 32 * 16) + r(4096) + r(4 * 8) + r(2 * 8 * NN);
+  size_t coef = rs == 8 ? CoefLayout<double>::bytes(p.N) : CoefLayout<float>::bytes(p.N);
+  if (p.flags & HEOM_FLAG_SCALED) coef = (coef + 15) / 16 * 16 + rs * 2 * (size_t)(p.K + 2) * p.N;
+  size_t b = 3 * r(NN * Mpad * rs) + r(Mpad * rs) + r(3 * 8 * NN + 32 * heom::kPartBytes) + r(coef) +
+             r(kAccDoubles * 8) + r(2 * 8 * NN);
   if (!tables_cached) b += 2 * r(4 * (size_t)p.N * Mpad);
   return b;
 }

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(HERE, "libheom.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, 1, 2, 3, 4, 5
 FP64, FP32_MIXED = 0, 1
 FLAG_LOW_TEMP = 1  # heom_params.flags: low-temperature correction
+FLAG_SCALED = 2  # heom_params.flags: scaled hierarchy (auxiliaries divided by prod_j sqrt(n_j! s_j^n_j))
 TERM_NONE, TERM_MARKOV = 0, 1
 MAX_SITES = 24
 
@@ -181,7 +182,8 @@ class _Keep:
                 raise ValueError("rate arrays need N entries")
         self.c = _Params(N, int(p["K"]), _ptr(self.H), _ptr(self.lam), _ptr(self.gam), float(p["T"]),
                          _ptr(self.trap), _ptr(self.recomb), int(precision), int(p.get("terminator", 0)),
-                         int(p.get("add_reorg", 0)), FLAG_LOW_TEMP if p.get("low_temp", 0) else 0)
+                         int(p.get("add_reorg", 0)),
+                         (FLAG_LOW_TEMP if p.get("low_temp", 0) else 0) | (FLAG_SCALED if p.get("scaled", 0) else 0))
 
 
 def _precision(precision):

@@ -80,3 +80,12 @@ def test_static_entry_point_rejects_oversized_problems(lib):
     rc = lib.heom_propagate_static(ctypes.byref(keep.c), d_rho0.data_ptr(), 1.0, 10, 10, None, None, None, None)
     assert rc == heom.EINVAL
     assert b"static area" in lib.heom_last_error()
+
+
+def test_static_entry_point_rejects_scaled_hierarchies(lib):
+    import torch
+    w = workloads.fmo_trap(K=2)
+    keep = heom._Keep(dict(w["params"], scaled=1), heom.FP64)
+    d_rho0 = torch.zeros((7, 7), dtype=torch.complex128, device="cuda")
+    rc = lib.heom_propagate_static(ctypes.byref(keep.c), d_rho0.data_ptr(), 1.0, 10, 10, None, None, None, None)
+    assert rc == heom.EUNSUPPORTED
