@@ -604,6 +604,9 @@ def bench_batched(heom, torch, stream, steps=0):
             "max_abs_eta_diff_vs_fp64": eta_err}
 
 
+SERVING_LOW_RATE = 12.0  # req/s, about half the measured capacity of the mix
+
+
 def bench_serving(count):
     """Serving: Poisson arrivals at 200 requests/s, N ~ U{2..8}, depth ~ U{3..8},
     1-20 ps at 1 fs, mixed precision, continuous batching with memory
@@ -613,6 +616,12 @@ def bench_serving(count):
     r = serving.run_trace(tr, "fp32", device_bytes=16 << 30, streams=32, time_limit_s=120.0)
     r["workload"] = ("Poisson 200 req/s, N~U{2..8}, K~U{3..8}, 1-20 ps at 1 fs, fp32 mixed; first %d requests "
                      "of the seeded trace" % count)
+    # the same request mix below saturation: the latency of a request that does not queue
+    low = workloads.serving_trace(count=max(1, count // 2), rate_per_s=SERVING_LOW_RATE)
+    r2 = serving.run_trace(low, "fp32", device_bytes=16 << 30, streams=32, time_limit_s=120.0)
+    r["below_saturation"] = {k: r2[k] for k in ("requests", "completed", "offered_req_per_s", "achieved_req_per_s",
+                                                "p50_latency_s", "p99_latency_s", "mean_latency_s", "max_concurrent")}
+    r["below_saturation"]["workload"] = "the same mix at Poisson %g req/s" % SERVING_LOW_RATE
     return r
 
 
