@@ -810,6 +810,9 @@ struct Engine {
       } else {
         g.dyn = heom::engine_dyn_bytes(g.N, g.c.block, (int)rsize(), g.c.G <= 2);
       }
+      if (!kernel_for(g.N, g.cplx, g.sc, g.c))
+        return fail(HEOM_EUNSUPPORTED, "no engine kernel for N=%d, launch mode %d, node_threads %d%s", g.N, g.c.mode,
+                    g.c.G, no_kernel_reason(g.N, g.sc));
       if (g.c.mode == 1) {
         g.nteams = 1;
       } else {
