@@ -1939,12 +1939,17 @@ struct heom_server {
     while (c < 16 && (int64_t)c * 256 < M) c <<= 1;
     return c;
   }
-  static LaunchCfg launch_for(int prec, int N, int64_t M, int max_dyn) {
+  // Scaled hierarchies (N <= 8) take a load view in device memory.
+  static LaunchCfg launch_for(int prec, int N, int64_t M, int max_dyn, bool scaled) {
     LaunchCfg c;
     c.mode = 0;
     c.team_ctas = team_for(M);
     c.block = prec == HEOM_FP64 ? 256 : 512;
     c.G = 2;
+    if (scaled && N <= heom::kMaxSmallN) {
+      c.G = std::max(3, std::min(8, N * (N + 1) / 2));
+      return c;
+    }
     if (prec == HEOM_FP32_MIXED && N <= heom::kMaxSmallN &&
         heom::smem_dyn_bytes(N, Engine::smem_slice(M, c.team_ctas)) <= max_dyn)
       c.mode = 2;
@@ -1966,7 +1971,7 @@ struct heom_server {
     if (rc != HEOM_OK) return rc;
     int64_t Mmax = 0;
     for (auto& in : eng->inst) Mmax = std::max<int64_t>(Mmax, in->M);
-    for (auto& in : eng->inst) eng->cfg[in->N] = launch_for(eng->prec, in->N, Mmax, max_dyn_smem());
+    for (auto& in : eng->inst) eng->cfg[in->N] = launch_for(eng->prec, in->N, Mmax, max_dyn_smem(), in->scaled != 0);
     std::vector<double> dts;
     std::vector<int64_t> steps;
     for (size_t k = 0; k < ids.size(); ++k) {
@@ -2050,8 +2055,8 @@ struct heom_server {
     std::vector<int> free_streams;
     for (size_t k = 0; k < launches.size(); ++k)
       if (!launches[k].busy) free_streams.push_back((int)k);
-    std::map<std::tuple<int, int, int, int>, std::vector<int64_t>> groups;
-    std::vector<std::tuple<int, int, int, int>> order;
+    std::map<std::tuple<int, int, int, int, int>, std::vector<int64_t>> groups;
+    std::vector<std::tuple<int, int, int, int, int>> order;
     size_t budget = arena.in_use;
     std::set<std::pair<int, int>> new_tables;
     const int max_dyn = max_dyn_smem();
@@ -2062,8 +2067,9 @@ struct heom_server {
       const size_t need = request_bytes(q.p, cached) + 8192;
       if (budget + need > arena.bytes) break;
       const int64_t M = heom::num_nodes(q.p.N, q.p.K);
-      const LaunchCfg c = launch_for(q.p.precision, q.p.N, M, max_dyn);
-      const auto gkey = std::make_tuple(q.p.precision, q.p.N, c.team_ctas, c.mode);
+      const bool sc = (q.p.flags & HEOM_FLAG_SCALED) != 0;
+      const LaunchCfg c = launch_for(q.p.precision, q.p.N, M, max_dyn, sc);
+      const auto gkey = std::make_tuple(q.p.precision, q.p.N, c.team_ctas, c.mode, (int)sc);
       if (!groups.count(gkey)) {
         if (groups.size() == free_streams.size()) break;  // no stream for a new group
         order.push_back(gkey);
