@@ -27,18 +27,6 @@ namespace heom {
 // an SM, so one CTA's loads overlap the other's arithmetic.
 constexpr int kLargeTile = 16;
 
-// FP32 tile layout: element (i, j) of node `node` at
-// ((i * JS/4 + j/4) * 16 + node) * 4 + j % 4, i.e. four consecutive columns
-// of one node form one 16-byte word, and the 16 nodes' words of a column
-// group are consecutive (a warp's 16-byte loads of one column group cover
-// 256 contiguous bytes).
-__device__ __forceinline__ int full_index(int JS, int i, int j, int node) {
-  return ((i * (JS >> 2) + (j >> 2)) * kLargeTile + node) * 4 + (j & 3);
-}
-__device__ __forceinline__ float f4_at(const float4& v, int c) {
-  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
-}
-
 // SC: scaled hierarchy, link weights from Inst::wsc (see scaled_up).
 template <typename R, bool MIXED, bool CPLX, bool SC = false>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) heom_large_kernel(EngineArgs A) {
@@ -164,13 +152,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) heom_large_kernel
                   // packed (r, c): Re sigma_rc for r <= c, Im sigma_cr for r > c
                   const int rq = rr[q], cq = cc[q];
                   if (rq < cq) {
-                    tile[full_index(JS, rq, cq, jn)] = v[q];
-                    tile[full_index(JS, cq, rq, jn)] = v[q];
+                    tile[(rq * JS + cq) * TN + jn] = v[q];
+                    tile[(cq * JS + rq) * TN + jn] = v[q];
                   } else if (rq > cq) {
-                    tileA[full_index(JS, cq, rq, jn)] = v[q];
-                    tileA[full_index(JS, rq, cq, jn)] = -v[q];
+                    tileA[(cq * JS + rq) * TN + jn] = v[q];
+                    tileA[(rq * JS + cq) * TN + jn] = -v[q];
                   } else {
-                    tile[full_index(JS, rq, rq, jn)] = v[q];
+                    tile[(rq * JS + rq) * TN + jn] = v[q];
                   }
                 } else {
                   tile[pp * TN + jn] = v[q];
@@ -187,8 +175,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) heom_large_kernel
           // packed element (i, j) of this lane's node; 0 outside the N x N matrix
           auto Pk = [&](int i, int j) -> R { return (i < N && j < N) ? tile[(i * N + j) * TN + node] : R(0); };
           // Re sigma_ij and Im sigma_ij (FULL tile: no bounds checks, padding is 0)
-          auto Sf = [&](int i, int j) -> R { return tile[full_index(JS, i, j, node)]; };
-          auto Af = [&](int i, int j) -> R { return tileA[full_index(JS, i, j, node)]; };
+          auto Sf = [&](int i, int j) -> R { return tile[(i * JS + j) * TN + node]; };
+          auto Af = [&](int i, int j) -> R { return tileA[(i * JS + j) * TN + node]; };
           auto Re_ = [&](int i, int j) -> R { return FULL ? Sf(i, j) : Pk(i <= j ? i : j, i <= j ? j : i); };
           auto Im_ = [&](int i, int j) -> R {
             return FULL ? Af(i, j) : (i < j ? Pk(j, i) : (i > j ? -Pk(i, j) : R(0)));
@@ -207,96 +195,42 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) heom_large_kernel
             //   Re += sum_k J(a,k) A(k,b) - A(a,k) J(k,b);  Im -= sum_k J(a,k) S(k,b) - S(a,k) J(k,b)
             //   Re += sum_k Ji(a,k) S(k,b) - S(a,k) Ji(k,b); Im += sum_k Ji(a,k) A(k,b) - A(a,k) Ji(k,b)
             // with S = Re sigma, A = Im sigma; J(a,k) = J(k,a) is read from row k.
-            if constexpr (FULL) {
-              // four k at a time, every operand a 16-byte shared-memory load: rows a of S, A, J
-              // (and Ji) at columns k..k+3, and per k row k of S, A, J (and Ji) at the block's
-              // columns.  Padding rows and columns of the tile are zero, and the coefficient rows
-              // read for padded a (>= N) only feed outputs that are dropped.
-              const float* Jc = reinterpret_cast<const float*>(cf) + L::J(N);
-              const float* Jic = reinterpret_cast<const float*>(cf) + L::Ji(N);
-              const float* tS = reinterpret_cast<const float*>(tile);
-              const float* tA = reinterpret_cast<const float*>(tileA);
-#pragma unroll 1
-              for (int k = 0; k < JS; k += 4) {
-                float4 ja[2], sa[2], aa[2], ia[2];
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                  ja[i] = *reinterpret_cast<const float4*>(Jc + (A0 + i) * JS + k);
-                  sa[i] = *reinterpret_cast<const float4*>(tS + full_index(JS, A0 + i, k, node));
-                  aa[i] = *reinterpret_cast<const float4*>(tA + full_index(JS, A0 + i, k, node));
-                  if constexpr (CPLX) ia[i] = *reinterpret_cast<const float4*>(Jic + (A0 + i) * JS + k);
-                }
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                  const float4 s4 = *reinterpret_cast<const float4*>(tS + full_index(JS, k + kk, B0, node));
-                  const float4 a4 = *reinterpret_cast<const float4*>(tA + full_index(JS, k + kk, B0, node));
-                  const float4 j4 = *reinterpret_cast<const float4*>(Jc + (k + kk) * JS + B0);
-                  const float skb[4] = {s4.x, s4.y, s4.z, s4.w};  // S(k, b)
-                  const float akb[4] = {a4.x, a4.y, a4.z, a4.w};  // A(k, b)
-                  const float jkb[4] = {j4.x, j4.y, j4.z, j4.w};  // J(k, b)
-#pragma unroll
-                  for (int i = 0; i < 2; ++i) {
-                    const float jak = f4_at(ja[i], kk), sak = f4_at(sa[i], kk), aak = f4_at(aa[i], kk);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                      re[i][j] += jak * akb[j] - aak * jkb[j];
-                      im[i][j] -= jak * skb[j] - sak * jkb[j];
-                    }
-                  }
-                  if constexpr (CPLX) {
-                    // Ji(k, a) = -Ji(a, k); Ji(k, b) from row k
-                    const float4 i4 = *reinterpret_cast<const float4*>(Jic + (k + kk) * JS + B0);
-                    const float ikb[4] = {i4.x, i4.y, i4.z, i4.w};
-#pragma unroll
-                    for (int i = 0; i < 2; ++i) {
-                      const float iak = -f4_at(ia[i], kk), sak = f4_at(sa[i], kk), aak = f4_at(aa[i], kk);
-#pragma unroll
-                      for (int j = 0; j < 4; ++j) {
-                        re[i][j] -= iak * skb[j] + sak * ikb[j];
-                        im[i][j] -= iak * akb[j] + aak * ikb[j];
-                      }
-                    }
-                  }
-                }
-              }
-            } else {
 #pragma unroll 2
-              for (int k = 0; k < N; ++k) {
-                R ja[2], jb[4];
-                ja[0] = cf[L::J(N) + k * JS + A0];
-                ja[1] = cf[L::J(N) + k * JS + A0 + 1];
-                load_row<4>(cf + L::J(N) + k * JS + B0, jb);
-                R sak[2], aak[2], skb[4], akb[4];
+            for (int k = 0; k < N; ++k) {
+              R ja[2], jb[4];
+              ja[0] = cf[L::J(N) + k * JS + A0];
+              ja[1] = cf[L::J(N) + k * JS + A0 + 1];
+              load_row<4>(cf + L::J(N) + k * JS + B0, jb);
+              R sak[2], aak[2], skb[4], akb[4];
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                  sak[i] = Re_(A0 + i, k);
-                  aak[i] = Im_(A0 + i, k);
-                }
+              for (int i = 0; i < 2; ++i) {
+                sak[i] = Re_(A0 + i, k);
+                aak[i] = Im_(A0 + i, k);
+              }
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                skb[j] = Re_(B0 + j, k);    // S(k, b) = S(b, k)
+                akb[j] = -Im_(B0 + j, k);   // A(k, b) = -A(b, k)
+              }
+#pragma unroll
+              for (int i = 0; i < 2; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                  skb[j] = Re_(B0 + j, k);    // S(k, b) = S(b, k)
-                  akb[j] = -Im_(B0 + j, k);   // A(k, b) = -A(b, k)
+                  re[i][j] += ja[i] * akb[j] - aak[i] * jb[j];
+                  im[i][j] -= ja[i] * skb[j] - sak[i] * jb[j];
                 }
+              if constexpr (CPLX) {
+                R ia[2], ib[4];  // row k of Ji: Ji(k, a) = -Ji(a, k)
+                ia[0] = cf[L::Ji(N) + k * JS + A0];
+                ia[1] = cf[L::Ji(N) + k * JS + A0 + 1];
+                load_row<4>(cf + L::Ji(N) + k * JS + B0, ib);
 #pragma unroll
                 for (int i = 0; i < 2; ++i)
 #pragma unroll
                   for (int j = 0; j < 4; ++j) {
-                    re[i][j] += ja[i] * akb[j] - aak[i] * jb[j];
-                    im[i][j] -= ja[i] * skb[j] - sak[i] * jb[j];
+                    re[i][j] -= ia[i] * skb[j] + sak[i] * ib[j];
+                    im[i][j] -= ia[i] * akb[j] + aak[i] * ib[j];
                   }
-                if constexpr (CPLX) {
-                  R ia[2], ib[4];  // row k of Ji: Ji(k, a) = -Ji(a, k)
-                  ia[0] = cf[L::Ji(N) + k * JS + A0];
-                  ia[1] = cf[L::Ji(N) + k * JS + A0 + 1];
-                  load_row<4>(cf + L::Ji(N) + k * JS + B0, ib);
-#pragma unroll
-                  for (int i = 0; i < 2; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                      re[i][j] -= ia[i] * skb[j] + sak[i] * ib[j];
-                      im[i][j] -= ia[i] * akb[j] + aak[i] * ib[j];
-                    }
-                }
               }
             }
             // links of the block's rows and columns
