@@ -633,8 +633,7 @@ __device__ __forceinline__ R scaled_dn(const R* __restrict__ w, int S, int j, R 
 // terminator factor (n_j + 1) / (ngam + gamma_j) of a leaf node (term), 0
 // elsewhere.  BF: branch-free form -- absent neighbours read as 0 (predicated
 // loads), n_j is 0 where there is no down link and the terminator terms are
-// evaluated on every node when the hierarchy has a terminator (term is then
-// that uniform switch), so the compiler may issue the loads of several units
+// always evaluated, so the compiler may issue the loads of several units
 // ahead of their arithmetic; worth it where a thread runs many units of a
 // node and arithmetic is cheap (FP32, unit groups G <= 2).  Otherwise each
 // term is skipped where it is absent, which saves FP64 instructions (1/64
@@ -697,15 +696,8 @@ __device__ __forceinline__ void unit_rhs(const V& v, const R* __restrict__ cf, R
     // -i (eps_a - eps_b) sigma_ab, anti-Hermitian part and damping
     const R d = sa[0] - sb[0];
     const R c = ngam + sa[1] + sb[1];
-    if constexpr (BF) {  // multiply-add chains (throughput form)
-      re = fma(d, yi, re);
-      re = fma(-c, x, re);
-      im = fma(-d, x, im);
-      im = fma(-c, yi, im);
-    } else {
-      re += d * yi - c * x;
-      im -= d * x + c * yi;
-    }
+    re += d * yi - c * x;
+    im -= d * x + c * yi;
     const R al_a = sa[2], be_a = sa[3];
     const R al_b = sb[2], be_b = sb[3];
     // up-couplings i V_j^x sigma_{n+e_j}: j = a gives +i, j = b gives -i
@@ -722,12 +714,9 @@ __device__ __forceinline__ void unit_rhs(const V& v, const R* __restrict__ cf, R
       re += ubi - uai;
       im += uar - ubr;
       // terminator: sigma_{n+e_j} ~ (n_j+1)/(ngam+gamma_j) theta_j sigma_n, then i V_j^x of it
-      // (term: the terminator is on for this hierarchy; tc is 0 on nodes below the last level)
-      if (term) {
-        const R ca = tc[a], cb = tc[b];
-        re += ca * (-al_a * x - be_a * yi) + cb * (-al_b * x + be_b * yi);
-        im += ca * (-al_a * yi + be_a * x) + cb * (-al_b * yi - be_b * x);
-      }
+      const R ca = tc[a], cb = tc[b];
+      re += ca * (-al_a * x - be_a * yi) + cb * (-al_b * x + be_b * yi);
+      im += ca * (-al_a * yi + be_a * x) + cb * (-al_b * yi - be_b * x);
       const R n_a = v.template Nj<a>();
       const R n_b = v.template Nj<b>();
       re += n_a * (be_a * dar - al_a * dai) + n_b * (be_b * dbr + al_b * dbi);
@@ -879,9 +868,7 @@ __device__ __forceinline__ void node_units(const Inst& I, const R* __restrict__ 
       if (!in_group<0, 0, u>(umask)) return;
     }
     R re, im;
-    // branch-free units take the hierarchy's terminator switch (uniform), the others the node's
-    unit_rhs<N, u, R, CPLX, BF, SC>(v, cf, ngam, BF ? I.terminator != 0 : term, tc, re, im,
-                                    static_cast<const R*>(I.wsc), I.wstride);
+    unit_rhs<N, u, R, CPLX, BF, SC>(v, cf, ngam, term, tc, re, im, static_cast<const R*>(I.wsc), I.wstride);
     if constexpr (u < NP) {
       constexpr int a = pair_a(N, u);
       constexpr int b = pair_b(N, u);
