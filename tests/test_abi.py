@@ -102,6 +102,12 @@ def test_invalid_parameters_are_rejected_before_any_device_work():
     bad["T"] = -1.0
     with pytest.raises(heom.HeomError):
         heom.Context(bad)
+    # flags: only HEOM_FLAG_LOW_TEMP and HEOM_FLAG_SCALED exist
+    keep = heom._Keep(dict(w["params"], low_temp=1, scaled=1), heom.FP64)
+    keep.c.flags = heom.FLAG_LOW_TEMP | heom.FLAG_SCALED | 8
+    h = heom.ctypes.c_void_p()
+    assert heom.lib().heom_create(heom.ctypes.byref(keep.c), None, heom.ctypes.byref(h)) == heom.EINVAL
+    assert b"unknown flags" in heom.lib().heom_last_error()
 
 
 def test_no_cpu_fallback_without_a_device():
