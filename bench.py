@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -254,15 +255,44 @@ def fp64_peak_tflops(sm_mhz):
     return 152 * 4.0 * sm_mhz * 1e6 / 1e12
 
 
-def oracle_sample(w, steps):
+def cpu_model():
+    """Host CPU model (lscpu, else /proc/cpuinfo), with the architecture."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return "%s (%s)" % (line.split(":", 1)[1].strip(), platform.machine())
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return "%s (%s)" % (line.split(":", 1)[1].strip(), platform.machine())
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def oracle_sample(w, steps, compare=None):
+    """The oracle on the first `steps` steps of workload w, timed on the host
+    cores.  compare: {name: GPU population rows at the workload's output
+    cadence}; the largest difference over the common rows is reported."""
     import oracle
     oracle.build()
     nodes = oracle.num_nodes(w["params"]["N"], w["params"]["K"])
+    every = w["out_every"] if compare else steps
     t0 = time.perf_counter()
-    oracle.propagate(w["params"], w["rho0"], w["dt"], steps, steps)
+    r = oracle.propagate(w["params"], w["rho0"], w["dt"], steps, every)
     dt = time.perf_counter() - t0
-    return {"value": nodes * 4.0 * steps / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "%d RK4 steps of the %d-node workload (%.2f s)" % (steps, nodes, dt)}
+    out = {"value": nodes * 4.0 * steps / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "cpu": cpu_model(), "sample": "%d RK4 steps of the %d-node workload (%.2f s)" % (steps, nodes, dt)}
+    if compare:
+        for name, pops in compare.items():
+            rows = min(len(pops), len(r["pops"]))
+            out["max_abs_pop_diff_%s_vs_oracle" % name] = float(np.abs(pops[:rows] - r["pops"][:rows]).max())
+        out["compared_rows"] = "populations every %g fs over the sample" % (w["out_every"] * w["dt"])
+    return out
 
 
 # ----------------------------------------------------------------- reference
@@ -481,7 +511,7 @@ def main():
     if rank == 0:
         n_sample = args.cpu_sample_steps or 5000  # about 10 s of host work
         if not args.no_cpu:
-            line["cpu_baseline"] = oracle_sample(w, n_sample)
+            line["cpu_baseline"] = oracle_sample(w, n_sample, {"mixed": pops_gpu, "fp64": pops64})
         print(json.dumps(line), flush=True)
     for v in results.values():
         v["ctx"].close()
