@@ -320,7 +320,7 @@ def run_reference(args):
         "config": {"workload": WORKLOAD, "global_batch": 1, "seq_len": None, "parallelism": "replicas",
                    "sample": "each step: %d RK4 steps of the full hierarchy on the host cores" % steps},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
-                         "sample": vals[0]["sample"]},
+                         "cpu": vals[0]["cpu"], "sample": vals[0]["sample"]},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
