@@ -288,6 +288,16 @@ def oracle_sample(w, steps, compare=None):
     out = {"value": nodes * 4.0 * steps / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
            "cpu": cpu_model(), "sample": "%d RK4 steps of the %d-node workload (%.2f s)" % (steps, nodes, dt)}
     if compare:
+        # the same oracle on one host core, on a tenth of the sample
+        n1 = max(1, steps // 10)
+        threads = oracle.num_threads()
+        oracle.set_threads(1)
+        t1 = time.perf_counter()
+        oracle.propagate(w["params"], w["rho0"], w["dt"], n1, n1)
+        t1 = time.perf_counter() - t1
+        oracle.set_threads(threads)
+        out["single_core"] = {"value": nodes * 4.0 * n1 / t1, "unit": UNIT, "cores": 1,
+                              "sample": "%d RK4 steps (%.2f s)" % (n1, t1)}
         for name, pops in compare.items():
             rows = min(len(pops), len(r["pops"]))
             out["max_abs_pop_diff_%s_vs_oracle" % name] = float(np.abs(pops[:rows] - r["pops"][:rows]).max())
