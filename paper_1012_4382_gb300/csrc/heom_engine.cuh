@@ -135,10 +135,7 @@ struct EngineArgs {
   int32_t team_ctas;          // CTAs per team in mode 0
   unsigned* gsync;            // grid barrier counter (mode 1), zero at launch
   int* status;                // error bits
-  unsigned* smslot = nullptr; // [kSmSlots] arrivals per SM (mode 1, FP64), zero at launch; null: unused
 };
-
-constexpr int kSmSlots = 1024;
 
 // ---------------------------------------------------------------- helpers
 
@@ -1395,24 +1392,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, (sizeof(R) == 8 &&
   // SM's FP64 units (FMO-like depth 6: 11.1 -> 8.5 us per stage).  FP32:
   // consecutive per CTA, so the unit groups of a node block share an SM and
   // its L1 (interleaving measured 4.3 -> 5.6 us there).
-  int wic = threadIdx.x >> 5;
-  if constexpr (sizeof(R) == 8) {
-    // The busy warps of a CTA are then its first ones, and warp w runs on
-    // sub-partition w % 4 of the SM: with two such CTAs per SM both would
-    // load the same sub-partitions' FP64 units.  The second CTA to arrive on
-    // an SM takes its warps in reverse order, which balances the four.
-    if (A.mode == 1 && A.smslot) {
-      __shared__ unsigned s_slot;
-      if (threadIdx.x == 0) {
-        unsigned smid;
-        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-        s_slot = atomicAdd(A.smslot + (smid % kSmSlots), 1u);
-      }
-      __syncthreads();
-      if (s_slot & 1u) wic = wpc - 1 - wic;
-    }
-  }
-  const int warp = sizeof(R) == 8 ? wic * team_size + rank : rank * wpc + wic;
+  const int warp = sizeof(R) == 8 ? (threadIdx.x >> 5) * team_size + rank : rank * wpc + (threadIdx.x >> 5);
   const int W = team_size * wpc;
   const int lane = threadIdx.x & 31;
   const int G = A.G;

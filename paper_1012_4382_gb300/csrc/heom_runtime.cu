@@ -469,7 +469,7 @@ struct Engine {
   std::vector<double*> ovr_pops, ovr_el;
   std::vector<int*> ovr_done;
   std::vector<int64_t> ovr_every;
-  DevBuf d_args, d_status, d_gsync, d_smslot, d_out;
+  DevBuf d_args, d_status, d_gsync, d_out;
   PinnedBuf h_args;
   cudaEvent_t args_done = nullptr;
   bool args_pending = false;
@@ -520,7 +520,6 @@ struct Engine {
     CUDA_TRY(cudaEventCreateWithFlags(&args_done, cudaEventDisableTiming));
     TRY(d_status.alloc(sizeof(int) * 4, hooks));
     TRY(d_gsync.alloc(sizeof(unsigned) * 4, hooks));
-    TRY(d_smslot.alloc(sizeof(unsigned) * heom::kSmSlots, hooks));
     CUDA_TRY(cudaMemsetAsync(d_status.p, 0, sizeof(int) * 4, stream));
     for (int i = 0; i < count; ++i) TRY(add_instance(params[i]));
     for (auto& in : inst)
@@ -890,7 +889,6 @@ struct Engine {
         A.team_ctas = g.c.team_ctas;
         A.gsync = d_gsync.as<unsigned>();
         A.status = d_status.as<int>();
-        A.smslot = d_smslot.as<unsigned>();
         rc = launch(g.N, g.cplx, g.sc, g.c, g.nteams, A, g.B, g.dyn);
       }
       cudaGraph_t graph = nullptr;
@@ -939,7 +937,6 @@ struct Engine {
       A.team_ctas = g.c.team_ctas;
       A.gsync = d_gsync.as<unsigned>();
       A.status = d_status.as<int>();
-      A.smslot = d_smslot.as<unsigned>();
       TRY(launch(g.N, g.cplx, g.sc, g.c, g.nteams, A, g.B, g.dyn));
     }
     return HEOM_OK;
@@ -1016,7 +1013,6 @@ struct Engine {
       if (per_sm < 1) return fail(HEOM_ECUDA, "block of %d threads cannot be resident", c.block);
       const int grid = per_sm * sms;
       CUDA_TRY(cudaMemsetAsync(A.gsync, 0, sizeof(unsigned), stream));
-      if (A.smslot) CUDA_TRY(cudaMemsetAsync(A.smslot, 0, sizeof(unsigned) * heom::kSmSlots, stream));
       void* args[] = {&A, &B};
       CUDA_TRY(cudaLaunchCooperativeKernel(k, dim3(grid), dim3(c.block), args, dyn, stream));
       return HEOM_OK;
