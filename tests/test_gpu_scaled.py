@@ -146,3 +146,55 @@ def test_server_runs_scaled_requests():
         r = srv.result(i)
     o = oracle.propagate(w["params"], w["rho0"], 1.0, 50, 10)
     assert np.abs(r["pops"] - o["pops"]).max() < TOL32_POP
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_scaled_stop_rule_and_trapping_time(precision):
+    """The stop rule and <t> read rho only, so the scaled hierarchy stops at the
+    same step and gives the same <t> as the oracle's scaled run."""
+    w = _scaled(workloads.fmo_trap(K=3))
+    p = dict(w["params"], trap=np.full(7, 20.0), recomb=np.full(7, 1.0))
+    w = dict(w, params=p)
+    nsteps, every = 3000, 10
+    o = oracle.propagate(p, w["rho0"], 1.0, nsteps, 1, stop_trace=1e-5)
+    n_stop = o["steps_done"]
+    assert 0 < n_stop < nsteps
+    with heom.Context(p, precision) as c:
+        c.set_stop(1e-5)
+        c.set_rho0(w["rho0"])
+        r = c.propagate(1.0, nsteps, every)
+        t, n = c.trapping_time()
+    assert n == n_stop
+    rows = n_stop // every + 1
+    tp, te = (TOL64, TOL64) if precision == "fp64" else (TOL32_POP, TOL32_ETA)
+    assert np.abs(r["pops"][:rows] - o["pops"][: n_stop + 1: every]).max() < tp
+    assert abs(t - o["tmean"][n_stop]) < 2 * te * n_stop
+
+
+def test_scaled_batch_graph_replay_equals_direct_calls():
+    import torch
+    ws = [_scaled(workloads.random_instance(N, K, seed=930 + N)) for N, K in ((3, 3), (7, 2), (10, 1))]
+    n, every, reps = 40, 10, 2
+    nout = n // every + 1
+    Ns = sum(w["params"]["N"] for w in ws)
+    dev = torch.device("cuda", 0)
+    out = {}
+    for mode in ("direct", "graph"):
+        d_pops = torch.zeros(Ns * nout, dtype=torch.float64, device=dev)
+        with heom.Batch([w["params"] for w in ws], "fp32") as b:
+            b.set_rho0([w["rho0"] for w in ws])
+            if mode == "direct":
+                for _ in range(reps):
+                    b.propagate_device(1.0, n, every, d_pops)
+            else:
+                with b.graph(1.0, n, every, d_pops) as g:
+                    for _ in range(reps):
+                        g.launch()
+                    b.synchronize()
+            b.synchronize()
+            out[mode] = (d_pops.cpu().numpy(), np.array(b.efficiency()[0]))
+    for a, c in zip(out["direct"], out["graph"]):
+        assert np.array_equal(a, c)
+    for i, w in enumerate(ws):
+        o = oracle.propagate(w["params"], w["rho0"], 1.0, reps * n, reps * n)
+        assert abs(out["graph"][1][i] - o["eta"][-1]) < TOL32_ETA
