@@ -144,6 +144,16 @@ int heom_set_allocator(heom_alloc_fn alloc, heom_free_fn release, void* user);
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* heom_last_error(void);
 
+/* Self-test of the bounded device-side wait that every grid-wide stage
+ * barrier uses (the wait behind HEOM_ETIMEOUT): one thread on the current
+ * device waits for a counter that nothing raises, with a limit of limit_ms
+ * (0 < limit_ms <= 1000) instead of the barrier's 2 s.  *timed_out (may be
+ * NULL) is 1 when the wait gave up and raised its status bit, as it must;
+ * *waited_ms (may be NULL) is the probe's device time.  Nothing is faulted:
+ * the kernel returns and the device stays usable.  HEOM_ECUDA without a
+ * device.  Blocking; allocates and frees 256 device bytes. */
+int heom_selftest_bounded_wait(double limit_ms, int32_t* timed_out, double* waited_ms);
+
 /* ------------------------------------------------------- single hierarchy */
 
 /* Creates a context: validates params, converts units, builds the node tables,

@@ -57,6 +57,7 @@ namespace heom {
 constexpr int kMaxSmallN = 8;
 constexpr int kMaxSites = 24;
 constexpr int kStatusTimeout = 1;
+constexpr uint64_t kBarrierLimitNs = 2000000000ull;  // a stage barrier gives up after 2 s
 
 // Per-instance device descriptor (host fills it; see heom_runtime.cu).
 struct Inst {
@@ -176,6 +177,24 @@ __device__ __forceinline__ int ld_volatile(const int* p) {
   return *reinterpret_cast<const volatile int*>(p);
 }
 
+// Spins until *p >= target (acquire loads).  Gives up after limit_ns of
+// global time, sets kStatusTimeout in *status and returns false; also
+// returns false as soon as another thread has set that bit.
+__device__ __forceinline__ bool bounded_wait_geq(const unsigned* p, unsigned target, uint64_t limit_ns, int* status) {
+  const uint64_t t0 = global_timer_ns();
+  unsigned spins = 0;
+  while (ld_acquire_gpu(p) < target) {
+    if ((++spins & 1023u) == 0) {
+      if (ld_volatile(status) & kStatusTimeout) return false;
+      if (global_timer_ns() - t0 > limit_ns) {
+        atomicOr(status, kStatusTimeout);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
 // Barrier between RK4 stages.  Returns false when a bounded wait expired
 // (grid mode only); the caller then leaves the kernel.
 __device__ __forceinline__ bool team_barrier(const EngineArgs& A, unsigned& epoch) {
@@ -193,20 +212,7 @@ __device__ __forceinline__ bool team_barrier(const EngineArgs& A, unsigned& epoc
     ++epoch;
     const unsigned target = epoch * gridDim.x;
     red_release_gpu_add(A.gsync, 1u);
-    int ok = 1;
-    const uint64_t t0 = global_timer_ns();
-    unsigned spins = 0;
-    while (ld_acquire_gpu(A.gsync) < target) {
-      if ((++spins & 1023u) == 0) {
-        if (ld_volatile(A.status) & kStatusTimeout) { ok = 0; break; }
-        if (global_timer_ns() - t0 > 2000000000ull) {  // 2 s without the team arriving
-          atomicOr(A.status, kStatusTimeout);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    s_ok = ok;
+    s_ok = bounded_wait_geq(A.gsync, target, kBarrierLimitNs, A.status) ? 1 : 0;
   }
   __syncthreads();
   return s_ok != 0;

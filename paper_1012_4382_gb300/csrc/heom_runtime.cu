@@ -152,6 +152,12 @@ __device__ __forceinline__ float2 to_ff(double v) {
   return make_float2(h, (float)(v - (double)h));
 }
 
+// One thread waits, through the stage barrier's bounded wait, for a counter
+// that nothing raises (the self-test of heom_selftest_bounded_wait).
+__global__ void bounded_wait_probe_kernel(const unsigned* counter, int* status, uint64_t limit_ns) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) heom::bounded_wait_geq(counter, 1u, limit_ns, status);
+}
+
 template <typename R>
 __global__ void set_root_kernel(R* y, int Mpad, float2* y0, const double* rho, int N, double* acc) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1189,6 +1195,41 @@ struct heom_graph {
 extern "C" {
 
 const char* heom_last_error(void) { return t_err.c_str(); }
+
+int heom_selftest_bounded_wait(double limit_ms, int32_t* timed_out, double* waited_ms) {
+  if (!(limit_ms > 0.0) || !(limit_ms <= 1000.0)) return fail(HEOM_EINVAL, "limit_ms must be in (0, 1000]");
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(HEOM_ECUDA, "no usable CUDA device (%s)", cudaGetErrorString(e));
+  }
+  unsigned char* buf = nullptr;  // counter (stays 0) and status word
+  CUDA_TRY(cudaMalloc(&buf, 256));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int st = 0;
+  float ms = 0.f;
+  cudaError_t ce = cudaMemset(buf, 0, 256);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce == cudaSuccess) ce = cudaEventRecord(e0, 0);
+  if (ce == cudaSuccess) {
+    bounded_wait_probe_kernel<<<1, 32>>>(reinterpret_cast<unsigned*>(buf), reinterpret_cast<int*>(buf + 128),
+                                         (uint64_t)(limit_ms * 1e6));
+    ce = cudaGetLastError();
+  }
+  if (ce == cudaSuccess) ce = cudaEventRecord(e1, 0);
+  if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+  if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+  if (ce == cudaSuccess) ce = cudaMemcpy(&st, buf + 128, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (ce != cudaSuccess) return fail(HEOM_ECUDA, "bounded-wait self-test: %s", cudaGetErrorString(ce));
+  if (timed_out) *timed_out = (st & heom::kStatusTimeout) ? 1 : 0;
+  if (waited_ms) *waited_ms = ms;
+  return HEOM_OK;
+}
 
 int heom_num_nodes(int32_t N, int32_t K, int64_t* out) {
   if (!out) return fail(HEOM_EINVAL, "out is NULL");

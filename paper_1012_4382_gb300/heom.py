@@ -194,6 +194,17 @@ def _precision(precision):
     raise ValueError("precision must be 'fp64' or 'fp32'")
 
 
+def selftest_bounded_wait(limit_ms: float = 20.0):
+    """heom_selftest_bounded_wait: returns (timed_out, waited_ms)."""
+    L = lib()
+    L.heom_selftest_bounded_wait.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_double)]
+    L.heom_selftest_bounded_wait.restype = ctypes.c_int
+    t, ms = ctypes.c_int32(), ctypes.c_double()
+    _check(L.heom_selftest_bounded_wait(float(limit_ms), ctypes.byref(t), ctypes.byref(ms)))
+    return bool(t.value), ms.value
+
+
 def num_nodes(N: int, K: int) -> int:
     out = ctypes.c_int64(0)
     _check(lib().heom_num_nodes(int(N), int(K), ctypes.byref(out)))

@@ -121,3 +121,6 @@ def test_no_cpu_fallback_without_a_device():
     with pytest.raises(heom.HeomError) as e:
         heom.Context(w["params"])
     assert e.value.code == heom.ECUDA
+    with pytest.raises(heom.HeomError) as e:
+        heom.selftest_bounded_wait(20.0)
+    assert e.value.code == heom.ECUDA
