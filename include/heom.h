@@ -90,11 +90,10 @@ extern "C" {
                                 rho, eta, loss and <t> are unchanged up to rounding, while the
                                 auxiliaries of different depths become of comparable size (the
                                 first step towards filtering small ones, which this library does
-                                not do).  heom_get_state/heom_set_state
-                                exchange sigma~_n.  Not with the register node view of
-                                HEOM_FP32_MIXED (node_threads 1 or 2) nor with mode 2: the default
-                                launch shape avoids them, and heom_set_launch asking for them fails
-                                at propagate time with HEOM_EUNSUPPORTED */
+                                not do).  heom_get_state/heom_set_state exchange sigma~_n.  For
+                                N <= 8 not with the register node view (node_threads 1 or 2) nor
+                                with mode 2: the default launch shape avoids them, and a launch
+                                shape set to them fails at propagate time with HEOM_EUNSUPPORTED */
 
 /* largest supported number of sites and of hierarchy nodes per instance */
 #define HEOM_MAX_SITES 24
