@@ -606,7 +606,7 @@ def bench_batched(heom, torch, stream, steps=0):
     b.synchronize()
     ms = e0.elapsed_time(e1)
     eta, _ = b.efficiency()
-    launch = b.get_launch() if hasattr(b, "get_launch") else None
+    launch = b.get_launch(ws[0]["params"]["N"])  # every instance has N = 7
     b.close()
     # plain FP64 path: one instance per launch with the default shape; one
     # instance of each depth is timed (the time depends on the depth only) and

@@ -286,6 +286,11 @@ int heom_batch_get_rho(heom_batch* b, int32_t i, double* rho_out);
  * mode 0 or 2, negative keeps the current mode). */
 int heom_batch_set_launch(heom_batch* b, int32_t mode, int32_t team_ctas, int32_t block_threads,
                           int32_t node_threads);
+/* The launch shape used for the batch's instances with N sites (one launch
+ * per site count); HEOM_EINVAL when the batch has no such instance.  Each
+ * output may be NULL. */
+int heom_batch_get_launch(const heom_batch* b, int32_t N, int32_t* mode, int32_t* team_ctas, int32_t* block_threads,
+                          int32_t* node_threads);
 
 void heom_batch_destroy(heom_batch* b);
 

@@ -1591,6 +1591,19 @@ int heom_batch_set_launch(heom_batch* b, int32_t mode, int32_t team_ctas, int32_
   return HEOM_OK;
 }
 
+int heom_batch_get_launch(const heom_batch* b, int32_t N, int32_t* mode, int32_t* team_ctas, int32_t* block_threads,
+                          int32_t* node_threads) {
+  if (!b) return fail(HEOM_EINVAL, "batch is NULL");
+  auto it = b->e.cfg.find(N);
+  if (it == b->e.cfg.end()) return fail(HEOM_EINVAL, "the batch has no instance with N=%d", N);
+  const LaunchCfg& c = it->second;
+  if (mode) *mode = c.mode;
+  if (team_ctas) *team_ctas = c.team_ctas;
+  if (block_threads) *block_threads = c.block;
+  if (node_threads) *node_threads = c.G;
+  return HEOM_OK;
+}
+
 void heom_batch_destroy(heom_batch* b) { delete b; }
 
 }  // extern "C"

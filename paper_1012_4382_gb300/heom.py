@@ -104,6 +104,7 @@ def lib() -> ctypes.CDLL:
             "heom_batch_set_stop": [vp, ctypes.c_double],
             "heom_batch_get_rho": [vp, ctypes.c_int32, _dp],
             "heom_batch_set_launch": [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
+            "heom_batch_get_launch": [vp, ctypes.c_int32, _i32p, _i32p, _i32p, _i32p],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -448,6 +449,13 @@ class Batch:
     def set_launch(self, mode=-1, team_ctas=0, block_threads=0, node_threads=0):
         _check(lib().heom_batch_set_launch(self._h, int(mode), int(team_ctas), int(block_threads),
                                            int(node_threads)))
+
+    def get_launch(self, N):
+        """Launch shape of the instances with N sites."""
+        v = [ctypes.c_int32() for _ in range(4)]
+        _check(lib().heom_batch_get_launch(self._h, int(N), *[ctypes.byref(x) for x in v]))
+        return {"mode": v[0].value, "team_ctas": v[1].value, "block_threads": v[2].value,
+                "node_threads": v[3].value}
 
 
 class Graph:

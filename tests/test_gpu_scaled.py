@@ -125,6 +125,11 @@ def test_batch_of_scaled_and_plain_instances(precision):
     ws += [_scaled(workloads.random_instance(3, 3, seed=910 + i)) for i in range(4)]
     ws += [_scaled(workloads.random_instance(9, 1, seed=920))]
     with heom.Batch([w["params"] for w in ws], precision) as b:
+        shape = b.get_launch(3)
+        assert shape["mode"] != 2 and shape["node_threads"] >= 3  # N = 3 has scaled instances
+        with pytest.raises(heom.HeomError) as e:
+            b.get_launch(4)  # no instance with 4 sites
+        assert e.value.code == heom.EINVAL
         b.set_rho0([w["rho0"] for w in ws])
         rs = b.propagate(1.0, 40, 10)
     tp = TOL64 if precision == "fp64" else TOL32_POP
