@@ -286,6 +286,14 @@ int heom_batch_get_rho(heom_batch* b, int32_t i, double* rho_out);
  * mode 0 or 2, negative keeps the current mode). */
 int heom_batch_set_launch(heom_batch* b, int32_t mode, int32_t team_ctas, int32_t block_threads,
                           int32_t node_threads);
+/* Autotuner for a batch: times `trial_steps` steps of every instance for each
+ * candidate shape (mode 0 and, in HEOM_FP32_MIXED, mode 2; 256 or 512
+ * threads; 1-16 team CTAs; node_threads 1-8), one shape for all site counts;
+ * shapes that cannot run every instance are skipped.  Keeps the fastest,
+ * restores the state it found and returns that shape's time in *best_ms (may
+ * be NULL).  Holds a copy of the batch's state meanwhile. */
+int heom_batch_autotune(heom_batch* b, int64_t trial_steps, double* best_ms);
+
 /* The launch shape used for the batch's instances with N sites (one launch
  * per site count); HEOM_EINVAL when the batch has no such instance.  Each
  * output may be NULL. */

@@ -1591,6 +1591,95 @@ int heom_batch_set_launch(heom_batch* b, int32_t mode, int32_t team_ctas, int32_
   return HEOM_OK;
 }
 
+int heom_batch_autotune(heom_batch* b, int64_t trial_steps, double* best_ms) {
+  if (!b) return fail(HEOM_EINVAL, "batch is NULL");
+  if (trial_steps < 1) return fail(HEOM_EINVAL, "trial_steps must be >= 1");
+  Engine& e = b->e;
+  TRY(e.ensure_device());
+  // snapshot every instance's state (y, root and running-sum buffers, accumulators)
+  const int count = (int)e.inst.size();
+  std::vector<DevBuf> sy(count), sr(count), sa(count);
+  for (int i = 0; i < count; ++i) {
+    Instance& in = *e.inst[i];
+    const size_t arr = (size_t)in.N * in.N * in.Mpad * e.rsize();
+    TRY(sy[i].alloc(arr, e.hooks));
+    TRY(sr[i].alloc(in.root64.bytes, e.hooks));
+    TRY(sa[i].alloc(in.acc.bytes, e.hooks));
+    CUDA_TRY(cudaMemcpyAsync(sy[i].p, in.y.p, arr, cudaMemcpyDeviceToDevice, e.stream));
+    CUDA_TRY(cudaMemcpyAsync(sr[i].p, in.root64.p, in.root64.bytes, cudaMemcpyDeviceToDevice, e.stream));
+    CUDA_TRY(cudaMemcpyAsync(sa[i].p, in.acc.p, in.acc.bytes, cudaMemcpyDeviceToDevice, e.stream));
+  }
+  // candidates: cluster teams on device memory, and on distributed shared memory in mixed precision;
+  // one shape for every site count of the batch
+  std::vector<LaunchCfg> cands;
+  for (int mode : {0, 2}) {
+    if (mode == 2 && e.prec != HEOM_FP32_MIXED) continue;
+    for (int block : {256, 512}) {
+      if (block > e.max_block()) continue;
+      for (int ctas : {1, 2, 4, 8, 16})
+        for (int G : {1, 2, 4, 8}) {
+          LaunchCfg c;
+          c.mode = mode;
+          c.team_ctas = ctas;
+          c.block = block;
+          c.G = G;
+          cands.push_back(c);
+        }
+    }
+  }
+  const std::map<int, LaunchCfg> saved = e.cfg;
+  std::map<int, LaunchCfg> best = saved;
+  float best_t = 1e30f;
+  std::vector<double> dt(count, 1.0);
+  std::vector<int64_t> one(count, 1), steps(count, trial_steps);
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  for (const LaunchCfg& c : cands) {
+    for (auto& kv : e.cfg) kv.second = c;
+    // the shape must run every instance (too little shared memory, no kernel: skipped)
+    if (e.propagate(dt.data(), one.data(), 1, nullptr, nullptr) != HEOM_OK || e.check_status() != HEOM_OK) {
+      cudaGetLastError();
+      t_err.clear();
+      continue;
+    }
+    cudaEventRecord(e0, e.stream);
+    if (e.propagate(dt.data(), steps.data(), trial_steps, nullptr, nullptr) != HEOM_OK) {
+      cudaGetLastError();
+      t_err.clear();
+      continue;
+    }
+    cudaEventRecord(e1, e.stream);
+    if (e.check_status() != HEOM_OK) {
+      t_err.clear();
+      continue;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_t) {
+      best_t = ms;
+      best = e.cfg;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  e.cfg = best;
+  for (int i = 0; i < count; ++i) {
+    Instance& in = *e.inst[i];
+    const size_t arr = (size_t)in.N * in.N * in.Mpad * e.rsize();
+    CUDA_TRY(cudaMemcpyAsync(in.y.p, sy[i].p, arr, cudaMemcpyDeviceToDevice, e.stream));
+    CUDA_TRY(cudaMemcpyAsync(in.root64.p, sr[i].p, in.root64.bytes, cudaMemcpyDeviceToDevice, e.stream));
+    CUDA_TRY(cudaMemcpyAsync(in.acc.p, sa[i].p, in.acc.bytes, cudaMemcpyDeviceToDevice, e.stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(e.stream));
+  if (best_t >= 1e30f) {
+    e.cfg = saved;
+    return fail(HEOM_ECUDA, "no launch shape ran");
+  }
+  if (best_ms) *best_ms = best_t;
+  return HEOM_OK;
+}
+
 int heom_batch_get_launch(const heom_batch* b, int32_t N, int32_t* mode, int32_t* team_ctas, int32_t* block_threads,
                           int32_t* node_threads) {
   if (!b) return fail(HEOM_EINVAL, "batch is NULL");

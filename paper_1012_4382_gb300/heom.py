@@ -105,6 +105,7 @@ def lib() -> ctypes.CDLL:
             "heom_batch_get_rho": [vp, ctypes.c_int32, _dp],
             "heom_batch_set_launch": [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
             "heom_batch_get_launch": [vp, ctypes.c_int32, _i32p, _i32p, _i32p, _i32p],
+            "heom_batch_autotune": [vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -449,6 +450,13 @@ class Batch:
     def set_launch(self, mode=-1, team_ctas=0, block_threads=0, node_threads=0):
         _check(lib().heom_batch_set_launch(self._h, int(mode), int(team_ctas), int(block_threads),
                                            int(node_threads)))
+
+    def autotune(self, trial_steps=20):
+        """Times the candidate launch shapes on the whole batch and keeps the
+        fastest (the state is restored); returns its time in ms."""
+        ms = ctypes.c_double()
+        _check(lib().heom_batch_autotune(self._h, int(trial_steps), ctypes.byref(ms)))
+        return ms.value
 
     def get_launch(self, N):
         """Launch shape of the instances with N sites."""

@@ -352,3 +352,21 @@ def test_unknown_flags_rejected():
     keep.c.flags = 6
     h = heom.ctypes.c_void_p()
     assert heom.lib().heom_create(heom.ctypes.byref(keep.c), None, heom.ctypes.byref(h)) == heom.EINVAL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_autotune_keeps_state_and_result(precision):
+    ws = [workloads.random_instance(N, K, seed=60 + N) for N, K in ((3, 3), (5, 2), (7, 3), (9, 1))]
+    with heom.Batch([w["params"] for w in ws], precision) as b:
+        b.set_rho0([w["rho0"] for w in ws])
+        b.propagate(1.0, 20, 20)
+        ms = b.autotune(trial_steps=5)
+        assert ms > 0
+        for N in (3, 5, 7, 9):
+            shape = b.get_launch(N)
+            assert shape["mode"] in (0, 2) and 1 <= shape["team_ctas"] <= 16
+        rs = b.propagate(1.0, 20, 10)
+    tol = TOL64 if precision == "fp64" else TOL32_POP
+    for w, r in zip(ws, rs):
+        o = oracle.propagate(w["params"], w["rho0"], 1.0, 40, 10)
+        assert np.abs(r["pops"] - o["pops"][2:]).max() < tol
