@@ -150,7 +150,11 @@ def k4_reference():
 def test_launch_shapes_fp64(shape, k4_reference):
     w, o = k4_reference
     if shape["block_threads"] > 256:
-        pytest.skip("the FP64 kernel is compiled for at most 256 threads per block")
+        # the FP64 kernels are compiled for at most 256 threads per block: refused on the host
+        with pytest.raises(heom.HeomError) as e:
+            run_gpu(w, "fp64", launch=shape)
+        assert e.value.code == heom.EINVAL and "block_threads" in str(e.value)
+        return
     g = run_gpu(w, "fp64", launch=shape)
     assert np.abs(g["pops"] - o["pops"]).max() < TOL64
     assert np.abs(g["eta"] - o["eta"]).max() < TOL64
