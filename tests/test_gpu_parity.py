@@ -249,6 +249,23 @@ def test_batch_fp32_matches_oracle():
         assert np.abs(res[i]["eta"] - o["eta"]).max() < TOL32_ETA
 
 
+def test_full_batched_scan_sampled_against_oracle():
+    """The full 256-instance scan in the launch shape the benchmark times (the
+    default), 20 steps; one sampled instance of every depth against the oracle."""
+    ws = workloads.batched_scan(nsteps=20)
+    with heom.Batch([w["params"] for w in ws], "fp32") as b:
+        b.set_rho0([w["rho0"] for w in ws])
+        res = b.propagate(1.0, 20, 10)
+    seen = {}
+    for i, w in enumerate(ws):
+        seen.setdefault(w["params"]["K"], i)
+    assert sorted(seen) == [4, 5, 6, 7, 8]
+    for K, i in seen.items():
+        o = run_oracle(ws[i], nsteps=20, out_every=10)
+        assert np.abs(res[i]["pops"] - o["pops"]).max() < TOL32_POP, K
+        assert np.abs(res[i]["eta"] - o["eta"]).max() < TOL32_ETA, K
+
+
 def test_zero_steps_and_sparse_outputs():
     w = workloads.fmo_trap(K=3, nsteps=25)
     with heom.Context(w["params"], "fp64") as c:
