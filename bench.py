@@ -232,10 +232,43 @@ def l2_copy_gbs(torch, dev):
 
 
 def algorithmic_bytes_per_node_step(N, elem_bytes):
-    """Horner-form RK4 over Hermitian-packed nodes: stage 0 reads y and writes
-    wa; stages 1-3 read the stage input and y and write the output, so a node
-    moves 11 packed arrays of N*N reals per step."""
+    """The implementation's own count -- Horner-form RK4 over Hermitian-packed
+    nodes: stage 0 reads y and writes wa; stages 1-3 read the stage input and
+    y and write the output, so a node moves 11 packed arrays of N*N reals per
+    step."""
     return 11 * N * N * elem_bytes
+
+
+def model_bytes_per_node_stage(N, complex_bytes):
+    """The method's count, used for `frac`: classic RK4 on full complex N x N
+    matrices with three stored arrays (y, z, acc) reads z, y and acc and
+    writes acc and z in every stage, 5 N^2 complex numbers per node-stage;
+    complex_bytes = 8 (FP32 complex) or 16 (FP64 complex).  Neighbour gathers
+    are reads of other nodes' z and count as reuse."""
+    return 5 * N * N * complex_bytes
+
+
+def roofline_block(N, nodes, steps, launch_ms, elem_bytes, peak, peak_kind, traffic, kernel, note=None):
+    """Bandwidth roofline of one launch under both byte counts: `achieved` /
+    `frac` with the method's 5 N^2 s per node-stage (s = complex size), and
+    `achieved_impl` / `frac_impl` with the implementation's 11 N^2 packed
+    reals per node-step; `traffic` is ncu's DRAM bytes per launch."""
+    model = model_bytes_per_node_stage(N, 2 * elem_bytes) * nodes * 4 * steps
+    impl = algorithmic_bytes_per_node_step(N, elem_bytes) * nodes * steps
+    a = model / (launch_ms * 1e-3) / 1e9
+    ai = impl / (launch_ms * 1e-3) / 1e9
+    out = {"bound": "hbm", "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak, "traffic": traffic,
+           "peak_kind": peak_kind, "kernel": kernel, "launch_ms": launch_ms,
+           "bytes_model": "5 N^2 x %d B per node-stage (classic RK4, complex y/z/acc)" % (2 * elem_bytes),
+           "algorithmic_bytes_per_launch": model,
+           "achieved_impl": ai, "frac_impl": ai / peak,
+           "bytes_model_impl": "11 N^2 x %d B per node-step (Horner RK4, Hermitian-packed)" % elem_bytes,
+           "algorithmic_bytes_per_launch_impl": impl}
+    if traffic is not None:
+        out["traffic_vs_impl_bytes"] = traffic / impl
+    if note:
+        out["note"] = note
+    return out
 
 
 def flops_per_node_stage(N, complex_h=False):
@@ -467,10 +500,15 @@ def main():
 
     # ---- roofline of the dominant kernel (the persistent engine launch)
     launch_ms = statistics.mean(per_kernel)
-    bytes_per_launch = algorithmic_bytes_per_node_step(N, 4) * nodes * nsteps
-    achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
     l2_gbs = l2_copy_gbs(torch, dev)
+    roof = roofline_block(N, nodes, nsteps, launch_ms, 4, peak, peak_kind,
+                          traffic_from_profile("engine_fmo7_k6_mixed.md"),
+                          kernel_name(results["fp32"]["launch"], N, "f32"),
+                          "the 1 MB working set is L2-resident: the launch is bound by the latency of its "
+                          "40 000 dependent stages, not by a bandwidth")
+    roof["l2_copy_gbs_measured"] = l2_gbs
+    roof["frac_of_l2_copy"] = roof["achieved"] / l2_gbs
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -496,18 +534,14 @@ def main():
                                    "frac": flops_per_node_stage(N) * nodes * 4 * nsteps
                                    / (statistics.mean(per64_kernel) * 1e-3) / 1e12 / fp64_peak_tflops(2070.0),
                                    "peak_kind": "derived: 152 SMs x 4 FP64 flops/cycle x 2070 MHz",
-                                   "kernel": kernel_name(results["fp64"]["launch"], N, "f64")},
+                                   "kernel": kernel_name(results["fp64"]["launch"], N, "f64"),
+                                   "hbm": roofline_block(N, nodes, nsteps, statistics.mean(per64_kernel), 8, peak,
+                                                         peak_kind, None, kernel_name(results["fp64"]["launch"], N,
+                                                                                      "f64"))},
                       "mixed_vs_fp64_speedup": value / world / fp64_value,
                       "max_abs_pop_diff_vs_mixed": float(np.abs(pops64 - pops_gpu).max()),
                       "abs_eta_diff_vs_mixed": float(abs(eta64[-1] - eta_gpu[-1]))},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic_from_profile("engine_fmo7_k6_mixed.md"), "peak_kind": peak_kind,
-                     "kernel": kernel_name(results["fp32"]["launch"], N, "f32"),
-                     "launch_ms": launch_ms,
-                     "algorithmic_bytes_per_launch": bytes_per_launch,
-                     "l2_copy_gbs_measured": l2_gbs, "frac_of_l2_copy": achieved / l2_gbs,
-                     "note": "the 1 MB working set is L2-resident: the launch is bound by the latency of its "
-                             "40 000 dependent stages, not by a bandwidth"},
+        "roofline": roof,
         "eta_10ps": float(eta_gpu[-1]),
         "variants": variants,
         "trapping_time_10ps_fs": t_mean_fs,
@@ -565,11 +599,8 @@ def bench_large(heom, torch, stream, peak, peak_kind, steps=0):
                 ms.append((e0, e1))
         stream.synchronize()
         t = ms[-1][0].elapsed_time(ms[-1][1])
-        byts = algorithmic_bytes_per_node_step(N, esize) * nodes * w["nsteps"]
-        ach = byts / (t * 1e-3) / 1e9
-        rl = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-              "peak_kind": peak_kind, "traffic": traffic_from_profile("large_trimer_%s.md" % prec),
-              "kernel": "heom_large_kernel<%s>" % prec, "algorithmic_bytes_per_launch": byts}
+        rl = roofline_block(N, nodes, w["nsteps"], t, esize, peak, peak_kind,
+                            traffic_from_profile("large_trimer_%s.md" % prec), "heom_large_kernel<%s>" % prec)
         if prec == "fp64":
             # FP64 runs at 1/64 of the FP32 rate: the arithmetic, not HBM, bounds this launch
             fp = fp64_peak_tflops(2070.0)
@@ -577,7 +608,7 @@ def bench_large(heom, torch, stream, peak, peak_kind, steps=0):
             rl = {"bound": "alu", "achieved": tf, "peak": fp, "unit": "TFLOP/s", "frac": tf / fp,
                   "peak_kind": "derived: 152 SMs x 4 FP64 flops/cycle x 2070 MHz",
                   "traffic": rl["traffic"], "kernel": rl["kernel"], "algorithmic_flops_per_launch": flops,
-                  "hbm": {"achieved": ach, "peak": peak, "frac": ach / peak}}
+                  "hbm": rl}
         out[prec] = {"ms_per_solve": t, "node_rhs_per_s": nodes * 4.0 * w["nsteps"] / (t * 1e-3),
                      "launch": ctx.get_launch(), "roofline": rl,
                      "pop0_end": float(d_pops.view(nout, N)[-1, 0].item())}
@@ -636,9 +667,12 @@ def bench_batched(heom, torch, stream, steps=0):
         ctx.close()
     solves = len(ws) / (ms * 1e-3)
     plain = len(ws) / (plain_ms * 1e-3)
+    peak, peak_kind = peaks()
+    roof = roofline_block(7, nodes, nsteps, ms, 4, peak, peak_kind, traffic_from_profile("engine_batched_scan.md"),
+                          "heom_engine_kernel<7, f32> (batched persistent launch)")
     return {"workload": "256 x N=7 trap, K~U{4..8}, lambda~U(2,200), T~U(77,300), 5 ps, fp32 mixed",
             "solves_per_s": solves, "node_rhs_per_s": nodes * 4.0 * nsteps / (ms * 1e-3),
-            "ms": ms, "total_nodes": nodes, "eta_mean": float(np.mean(eta)), "launch": launch,
+            "ms": ms, "total_nodes": nodes, "eta_mean": float(np.mean(eta)), "launch": launch, "roofline": roof,
             "plain_fp64_solves_per_s": plain, "vs_plain_fp64": solves / plain,
             "plain_fp64_note": "one instance per launch, default shape; one instance of each depth timed",
             "max_abs_eta_diff_vs_fp64": eta_err}

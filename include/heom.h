@@ -63,6 +63,10 @@ extern "C" {
 #define HEOM_ECUDA 3        /* CUDA runtime error or no usable device */
 #define HEOM_ETIMEOUT 4     /* a bounded device-side wait expired; results of that call are invalid */
 #define HEOM_EUNSUPPORTED 5 /* valid request this build does not implement (message says what) */
+#define HEOM_ENONFINITE 6   /* a population, the trace, eta or the loss came out NaN or infinite (checked at
+                               every output row and at the end of each propagate call): the run diverged,
+                               e.g. a time step too large for the bath rates, or the initial state was not
+                               finite; the call's results are not usable */
 
 /* precision of the propagation */
 #define HEOM_FP64 0         /* every array and every operation in double precision */
@@ -146,7 +150,9 @@ const char* heom_last_error(void);
 /* Self-test of the bounded device-side wait that every grid-wide stage
  * barrier uses (the wait behind HEOM_ETIMEOUT): one thread on the current
  * device waits for a counter that nothing raises, with a limit of limit_ms
- * (0 < limit_ms <= 1000) instead of the barrier's 2 s.  *timed_out (may be
+ * (0 < limit_ms <= 1000) instead of the barrier's 2 s.  The counter is preset
+ * to 2^32 - 1 and the awaited count is 1, past the 32-bit wrap, so the probe
+ * also shows that the wait compares counts in a wrap-safe way.  *timed_out (may be
  * NULL) is 1 when the wait gave up and raised its status bit, as it must;
  * *waited_ms (may be NULL) is the probe's device time.  Nothing is faulted:
  * the kernel returns and the device stays usable.  HEOM_ECUDA without a
@@ -157,7 +163,14 @@ int heom_selftest_bounded_wait(double limit_ms, int32_t* timed_out, double* wait
 
 /* Creates a context: validates params, converts units, builds the node tables,
  * allocates the device state on the current CUDA device and sets rho(0) =
- * |0><0| (site index 0).  cuda_stream is a cudaStream_t (NULL: the legacy
+ * |0><0| (site index 0).  Paper: the system Hamiltonian H_ex of Sec. "Model"
+ * (Eq. H_ex; lambda_m added to the site energies only with add_reorg_to_H);
+ * the trapping and radiative-decay rates of App. A1 (Eqs. lab2, lab3), taken
+ * in the equivalent anti-Hermitian form -(i/2) diag(Gamma_RC + Gamma_phot) of
+ * H that the end of App. A1 states; the bath coefficients of App. A2
+ * (theta_m, Eq. labsevena) and the hierarchy of all n with |n| <= K = N_max
+ * (Eq. lab8 and the truncation at the end of App. A2), C(N+K, K) nodes with
+ * 2N neighbour links each (App. B).  cuda_stream is a cudaStream_t (NULL: the legacy
  * default stream); all device work of the context is ordered on it.  The
  * params and their arrays may be freed after the call. */
 int heom_create(const heom_params* params, void* cuda_stream, heom_ctx** out);
@@ -177,7 +190,14 @@ int heom_set_rho0_device(heom_ctx* ctx, const double* d_rho0);
  * rows), the site populations pops_out[nout*N], their sum trace_out[nout]
  * and eta_out[nout] (each may be NULL).  Resumable: a later call continues
  * from the state this one left.  Blocking; returns HEOM_ETIMEOUT if a device
- * wait expired. */
+ * wait expired and HEOM_ENONFINITE if a row came out NaN or infinite.
+ * Paper: every step is one 4th-order Runge-Kutta step (App. B) of the whole
+ * hierarchy, Eq. lab8 with the damping sign read as -sum_m n_m gamma_m, the
+ * up links i V_m^x sigma_{n+e_m}, the down links n_m theta_m sigma_{n-e_m}
+ * (Eq. labsevena) and the commutator with the non-Hermitian H of App. A1;
+ * the sigma matrices stay on the device between calls and only the
+ * populations and eta are copied out (App. B); eta is the integral of
+ * Eq. eta carried as an extra row of the RK4 system. */
 int heom_propagate(heom_ctx* ctx, double dt_fs, int64_t nsteps, int64_t out_every, double* pops_out,
                    double* trace_out, double* eta_out);
 
@@ -187,8 +207,8 @@ int heom_propagate(heom_ctx* ctx, double dt_fs, int64_t nsteps, int64_t out_ever
 int heom_propagate_device(heom_ctx* ctx, double dt_fs, int64_t nsteps, int64_t out_every, double* d_pops,
                           double* d_eta_loss);
 
-/* Waits for the context's stream and reports HEOM_ETIMEOUT / HEOM_ECUDA
- * raised by work queued since the last check. */
+/* Waits for the context's stream and reports HEOM_ETIMEOUT / HEOM_ENONFINITE /
+ * HEOM_ECUDA raised by work queued since the last check. */
 int heom_synchronize(heom_ctx* ctx);
 
 /* eta = <RC|rho|RC> (Eq. eta) and the radiative loss <0|rho|0> at the current
@@ -213,7 +233,9 @@ int heom_trapping_time(heom_ctx* ctx, double* t_mean_fs, int64_t* steps_done);
  * values are HEOM_EINVAL. */
 int heom_set_stop(heom_ctx* ctx, double stop_trace);
 
-/* Current reduced density matrix on the sites, N*N complex.  Blocking. */
+/* Current reduced density matrix on the sites, N*N complex.  Blocking.
+ * Paper: rho = sigma_0, the root of the hierarchy (App. A2), copied from the
+ * device, where the hierarchy lives (App. B). */
 int heom_get_rho(heom_ctx* ctx, double* rho_out);
 
 /* Full state for checkpoints and checks: every node's N*N complex matrix in
@@ -246,7 +268,8 @@ int heom_get_launch(const heom_ctx* ctx, int32_t* mode, int32_t* team_ctas, int3
  * found.  best_us_per_step may be NULL. */
 int heom_autotune(heom_ctx* ctx, int64_t trial_steps, double* best_us_per_step);
 
-/* Releases the context and its device memory (NULL-safe). */
+/* Releases the context and its device memory (NULL-safe).  Paper: the
+ * device-resident sigma matrices and neighbour tables of App. B. */
 void heom_destroy(heom_ctx* ctx);
 
 /* -------------------------------------------------------------- batches */
@@ -254,7 +277,10 @@ void heom_destroy(heom_ctx* ctx);
 /* count independent hierarchies propagated together: every instance with
  * the same N runs in one persistent launch, one thread-block cluster per
  * instance at a time.  All instances must have the same precision.
- * Instances start from rho(0) = |0><0|. */
+ * Instances start from rho(0) = |0><0|.  Each instance is the model of
+ * heom_create (Sec. "Model", App. A1, App. A2); the batch itself has no
+ * counterpart in the paper, which propagates one hierarchy at a time
+ * (its parameter scans of Secs. 3-5 are such batches). */
 int heom_batch_create(const heom_params* params, int32_t count, void* cuda_stream, heom_batch** out);
 int heom_batch_count(const heom_batch* b, int32_t* count);
 
@@ -356,7 +382,9 @@ int heom_server_status(heom_server* s, int64_t request_id, int32_t* state);
 
 /* Results of a finished request: pops_out[nout*N], eta_out[nout],
  * loss_out[nout] (each may be NULL), times_out[2] = seconds from submission
- * to launch and to the progress call that saw it finish. */
+ * to launch and to the progress call that saw it finish.  A failed request
+ * (state 4) returns HEOM_ENONFINITE when its rows came out NaN or infinite,
+ * HEOM_ECUDA when its launch failed. */
 int heom_server_result(heom_server* s, int64_t request_id, double* pops_out, double* eta_out, double* loss_out,
                        double* times_out);
 
@@ -394,17 +422,23 @@ void heom_server_destroy(heom_server* s);
  * rho(0).  Outputs (device, each may be NULL): d_pops[nout*N],
  * d_eta_loss[nout*2] with nout = nsteps/out_every + 1 (rows as in
  * heom_propagate_device), and d_rho_out[N*N complex], rho at the end.
- * The work is queued on cuda_stream (a cudaStream_t; NULL = legacy default
- * stream); the call waits for earlier work on that stream before it stages
- * its inputs and returns once the propagation is queued.
+ * The work runs on cuda_stream (a cudaStream_t; NULL = legacy default
+ * stream), after the work queued there before the call.  The call is
+ * blocking: it waits for its own work to finish and returns its status --
+ * HEOM_ENONFINITE when the run produced NaN or infinite values, HEOM_ETIMEOUT
+ * when a device-side wait expired -- so the outputs are complete when it
+ * returns HEOM_OK.  Because it stages its inputs from host memory that does
+ * not outlive the call and waits for the device, it returns HEOM_EUNSUPPORTED
+ * when cuda_stream is being captured into a CUDA graph.
  *
- * Set-up: the first call on each device looks up the device address of the
- * static array (cudaGetSymbolAddress, with that device current); make that
- * first call before any stream capture.  Every call shares the one array,
- * which keeps the last call's contents; each call clears what must start at
- * zero.  Calls whose work overlaps on the GPU (different streams, or other
- * threads) race on the array and give wrong results: order them on one
- * stream or synchronise between them. */
+ * The address of the static array on the current device is looked up on
+ * every call (cudaGetSymbolAddress, with that device current; this allocates
+ * nothing).  Every call shares the one array, which keeps the last call's
+ * contents; each call clears what must start at zero.  A call holds a
+ * process-wide lock until its work has finished, so calls from several host
+ * threads run one after another; work that reached the array while a call ran
+ * (nothing in this library does) would race with it and corrupt its
+ * results. */
 #define HEOM_STATIC_SCRATCH_BYTES (8u << 20)
 int heom_propagate_static(const heom_params* params, const double* d_rho0, double dt_fs, int64_t nsteps,
                           int64_t out_every, double* d_pops, double* d_eta_loss, double* d_rho_out,

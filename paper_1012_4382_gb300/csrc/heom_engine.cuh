@@ -57,6 +57,7 @@ namespace heom {
 constexpr int kMaxSmallN = 8;
 constexpr int kMaxSites = 24;
 constexpr int kStatusTimeout = 1;
+constexpr int kStatusNonFinite = 2;  // a population, the trace, eta or the loss came out NaN or infinite
 constexpr uint64_t kBarrierLimitNs = 2000000000ull;  // a stage barrier gives up after 2 s
 
 // Per-instance device descriptor (host fills it; see heom_runtime.cu).
@@ -177,13 +178,16 @@ __device__ __forceinline__ int ld_volatile(const int* p) {
   return *reinterpret_cast<const volatile int*>(p);
 }
 
-// Spins until *p >= target (acquire loads).  Gives up after limit_ns of
-// global time, sets kStatusTimeout in *status and returns false; also
-// returns false as soon as another thread has set that bit.
+// Spins until *p has reached target (acquire loads).  The comparison is made
+// on the wrapped difference, (int)(*p - target) < 0 means "not yet", so it
+// stays right when the 32-bit counter and target pass 2^32 during a long
+// launch (the counter never lags the target by 2^31 or more).  Gives up after
+// limit_ns of global time, sets kStatusTimeout in *status and returns false;
+// also returns false as soon as another thread has set that bit.
 __device__ __forceinline__ bool bounded_wait_geq(const unsigned* p, unsigned target, uint64_t limit_ns, int* status) {
   const uint64_t t0 = global_timer_ns();
   unsigned spins = 0;
-  while (ld_acquire_gpu(p) < target) {
+  while ((int)(ld_acquire_gpu(p) - target) < 0) {
     if ((++spins & 1023u) == 0) {
       if (ld_volatile(status) & kStatusTimeout) return false;
       if (global_timer_ns() - t0 > limit_ns) {
@@ -574,11 +578,26 @@ __device__ __forceinline__ void eta_total(const Inst& I, int nslots, double acc0
   }
 }
 
+// Raises kStatusNonFinite (reported as HEOM_ENONFINITE) when v is NaN or
+// infinite: a run that diverged must not come back as a success.
+__device__ __forceinline__ void flag_nonfinite(int* status, double v) {
+  if (!isfinite(v)) atomicOr(status, kStatusNonFinite);
+}
+
+// The eta and loss row `row` (lead thread, one stage after the output step,
+// once the team barrier has ordered the owners' sums and the population row).
+// Every output row is also checked for NaN or infinity: the populations of
+// the row, eta and the loss.
 template <typename R>
-__device__ __forceinline__ void eta_write_row(const Inst& I, int nslots, double acc0, double acc1, int64_t row) {
-  if (!I.out_el) return;
+__device__ __forceinline__ void eta_write_row(const Inst& I, int nslots, double acc0, double acc1, int64_t row,
+                                              int* status) {
   double e, l;
   eta_total<R>(I, nslots, acc0, acc1, e, l);
+  flag_nonfinite(status, e);
+  flag_nonfinite(status, l);
+  if (I.out_pops)
+    for (int a = 0; a < I.N; ++a) flag_nonfinite(status, __ldcg(I.out_pops + row * I.N + a));
+  if (!I.out_el) return;
   I.out_el[2 * row] = e;
   I.out_el[2 * row + 1] = l;
 }
@@ -1332,8 +1351,17 @@ __device__ __forceinline__ bool stop_now(const Inst& I, int N, int* s_flag) {
 // and the totals (eta, loss, xi, elapsed time, steps done) for the next call.
 template <typename R>
 __device__ __forceinline__ void finish_instance(const Inst& I, int nslots, const EtaRows& rows, int64_t done,
-                                                int64_t orow, int N) {
-  if (rows.pending >= 0) eta_write_row<R>(I, nslots, rows.acc0, rows.acc1, rows.pending);
+                                                int64_t orow, int N, int* status) {
+  if (rows.pending >= 0) eta_write_row<R>(I, nslots, rows.acc0, rows.acc1, rows.pending, status);
+  // the site populations at the end of the call, whether or not rows were asked for
+  for (int a = 0; a < N; ++a) {
+    if constexpr (sizeof(R) == 4) {
+      const float* y0 = static_cast<const float*>(I.y0);
+      flag_nonfinite(status, (double)__ldcg(y0 + 2 * (a * N + a)) + (double)__ldcg(y0 + 2 * (a * N + a) + 1));
+    } else {
+      flag_nonfinite(status, (double)__ldcg(static_cast<const R*>(I.y) + (size_t)(a * N + a) * I.Mpad));
+    }
+  }
   if (done < I.nsteps) {
     const int64_t nout = I.nsteps / I.out_every + 1;
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
@@ -1349,6 +1377,8 @@ __device__ __forceinline__ void finish_instance(const Inst& I, int nslots, const
   if (done > 0) {
     double e, l, xs;
     eta_total<R>(I, nslots, rows.acc0, rows.acc1, e, l, &xs);
+    flag_nonfinite(status, e);
+    flag_nonfinite(status, l);
     I.acc[2] += (double)done * I.dt * rows.acc0 + xs;
     I.acc[3] += (double)done * I.dt;
     I.acc[0] = e;
@@ -1460,7 +1490,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, (sizeof(R) == 8 &&
 #pragma unroll 1
       for (int s = 0; s < 4; ++s) {
         if (s == 0 && rows.pending >= 0) {
-          if (lead) eta_write_row<R>(I, nslots, rows.acc0, rows.acc1, rows.pending);
+          if (lead) eta_write_row<R>(I, nslots, rows.acc0, rows.acc1, rows.pending, A.status);
           rows.pending = -1;
         }
         int in_sel, out_sel;
@@ -1515,7 +1545,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512, (sizeof(R) == 8 &&
         break;
       }
     }
-    if (lead) finish_instance<R>(I, nslots, rows, done, orow, N);
+    if (lead) finish_instance<R>(I, nslots, rows, done, orow, N, A.status);
     if (!team_barrier(A, epoch)) return;
     if (lead) signal_done(I);
   }
@@ -1641,7 +1671,7 @@ __global__ void __launch_bounds__(512) heom_smem_kernel(EngineArgs A, int B) {
 #pragma unroll 1
       for (int s = 0; s < 4; ++s) {
         if (s == 0 && rows.pending >= 0) {
-          if (lead) eta_write_row<float>(I, nslots, rows.acc0, rows.acc1, rows.pending);
+          if (lead) eta_write_row<float>(I, nslots, rows.acc0, rows.acc1, rows.pending, A.status);
           rows.pending = -1;
         }
         int in_sel, out_sel;
@@ -1671,7 +1701,7 @@ __global__ void __launch_bounds__(512) heom_smem_kernel(EngineArgs A, int B) {
         break;
       }
     }
-    if (lead) finish_instance<float>(I, nslots, rows, done, orow, N);
+    if (lead) finish_instance<float>(I, nslots, rows, done, orow, N, A.status);
     // write the slice of y back
     float* gyw = static_cast<float*>(I.y);
     for (int idx = threadIdx.x; idx < NN * B; idx += blockDim.x) {

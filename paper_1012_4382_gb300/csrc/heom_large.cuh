@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) heom_large_kernel
 #pragma unroll 1
       for (int s = 0; s < 4; ++s) {
         if (s == 0 && rows.pending >= 0) {
-          if (lead) eta_write_row<R>(I, nslots, rows.acc0, rows.acc1, rows.pending);
+          if (lead) eta_write_row<R>(I, nslots, rows.acc0, rows.acc1, rows.pending, A.status);
           rows.pending = -1;
         }
         int in_sel, out_sel;
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) heom_large_kernel
         break;
       }
     }
-    if (lead) finish_instance<R>(I, nslots, rows, done, orow, N);
+    if (lead) finish_instance<R>(I, nslots, rows, done, orow, N, A.status);
     if (!team_barrier(A, epoch)) return;
     if (lead) signal_done(I);
   }

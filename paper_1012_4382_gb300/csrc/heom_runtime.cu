@@ -153,7 +153,10 @@ __device__ __forceinline__ float2 to_ff(double v) {
 }
 
 // One thread waits, through the stage barrier's bounded wait, for a counter
-// that nothing raises (the self-test of heom_selftest_bounded_wait).
+// that nothing raises (the self-test of heom_selftest_bounded_wait).  The
+// counter holds 2^32 - 1 and the target is 1, i.e. two arrivals past the point
+// where the 32-bit count wraps: a plain "counter < target" test would let the
+// wait through at once, the wrapped comparison keeps it waiting.
 __global__ void bounded_wait_probe_kernel(const unsigned* counter, int* status, uint64_t limit_ns) {
   if (threadIdx.x == 0 && blockIdx.x == 0) heom::bounded_wait_geq(counter, 1u, limit_ns, status);
 }
@@ -1050,6 +1053,10 @@ struct Engine {
       CUDA_TRY(cudaMemset(d_status.p, 0, sizeof(int)));
       if (st & heom::kStatusTimeout)
         return fail(HEOM_ETIMEOUT, "a grid barrier wait expired on the device; the call's results are invalid");
+      if (st & heom::kStatusNonFinite)
+        return fail(HEOM_ENONFINITE,
+                    "the propagation produced a NaN or infinite population, eta or loss (a diverging run or a "
+                    "non-finite initial state)");
       return fail(HEOM_ECUDA, "device status 0x%x", st);
     }
     return HEOM_OK;
@@ -1204,12 +1211,13 @@ int heom_selftest_bounded_wait(double limit_ms, int32_t* timed_out, double* wait
     cudaGetLastError();
     return fail(HEOM_ECUDA, "no usable CUDA device (%s)", cudaGetErrorString(e));
   }
-  unsigned char* buf = nullptr;  // counter (stays 0) and status word
+  unsigned char* buf = nullptr;  // counter (stays at 2^32 - 1) and status word
   CUDA_TRY(cudaMalloc(&buf, 256));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int st = 0;
   float ms = 0.f;
   cudaError_t ce = cudaMemset(buf, 0, 256);
+  if (ce == cudaSuccess) ce = cudaMemset(buf, 0xFF, sizeof(unsigned));
   if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
   if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
   if (ce == cudaSuccess) ce = cudaEventRecord(e0, 0);
@@ -1712,29 +1720,23 @@ namespace {
 
 __device__ __align__(256) unsigned char g_heom_static_scratch[HEOM_STATIC_SCRATCH_BYTES];
 
-constexpr int kStaticMaxDevices = 64;
 std::mutex g_static_mu;
-void* g_static_addr[kStaticMaxDevices] = {};
 int32_t g_static_host_tables[HEOM_STATIC_SCRATCH_BYTES / 8];  // up and down tables, at most half the area
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
-// Device address of the static area on the current device, looked up once per
-// device (with that device current) and cached.  Caller holds g_static_mu.
+// Device address of the static area on the current device.  Looked up on
+// every call (with that device current): the lookup allocates nothing once
+// the module is loaded, and a cached address would go stale if the
+// application reset the device and the module were loaded again elsewhere.
+// Caller holds g_static_mu.
 int static_scratch_address(void** out) {
-  int dev = -1;
-  CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kStaticMaxDevices) return fail(HEOM_EUNSUPPORTED, "device %d beyond %d", dev, kStaticMaxDevices);
-  if (!g_static_addr[dev]) {
-    void* p = nullptr;
-    CUDA_TRY(cudaGetSymbolAddress(&p, g_heom_static_scratch));
-    if (!p) return fail(HEOM_ECUDA, "cudaGetSymbolAddress returned NULL for the static area");
-    g_static_addr[dev] = p;
-  }
-  *out = g_static_addr[dev];
+  void* p = nullptr;
+  CUDA_TRY(cudaGetSymbolAddress(&p, g_heom_static_scratch));
+  if (!p) return fail(HEOM_ECUDA, "cudaGetSymbolAddress returned NULL for the static area");
+  *out = p;
   return HEOM_OK;
 }
-
 
 }  // namespace
 
@@ -1782,11 +1784,24 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
   if (2 * tab_bytes + ngam_bytes > sizeof(g_static_host_tables))
     return fail(HEOM_EINVAL, "node tables exceed the staging area");
 
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  {
+    // the host staging below is pageable memory that a captured graph could not
+    // replay, and the call waits for its own work: no stream capture
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t ce = cudaStreamIsCapturing(stream, &cs);
+    if (ce != cudaSuccess) {
+      cudaGetLastError();
+      return fail(HEOM_EUNSUPPORTED, "the allocation-free entry point cannot run while a stream capture is active (%s)",
+                  cudaGetErrorString(ce));
+    }
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(HEOM_EUNSUPPORTED, "the allocation-free entry point cannot be captured into a CUDA graph");
+  }
   std::lock_guard<std::mutex> lk(g_static_mu);
   void* base_v = nullptr;
   TRY(static_scratch_address(&base_v));
   unsigned char* base = static_cast<unsigned char*>(base_v);
-  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
 
   // host staging: tables, coefficients, descriptor (no heap)
   int32_t* h_up = g_static_host_tables;
@@ -1917,6 +1932,15 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
                                                                             d_rho_out);
     CUDA_TRY(cudaGetLastError());
   }
+  // wait for this call's work and report its status word (a non-finite result)
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  int st = 0;
+  CUDA_TRY(cudaMemcpy(&st, base + o_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st & heom::kStatusTimeout)
+    return fail(HEOM_ETIMEOUT, "a device-side wait expired; the call's results are invalid");
+  if (st & heom::kStatusNonFinite)
+    return fail(HEOM_ENONFINITE, "the propagation produced a NaN or infinite population, eta or loss");
+  if (st) return fail(HEOM_ECUDA, "device status 0x%x", st);
   return HEOM_OK;
 }
 
@@ -2017,6 +2041,7 @@ struct Request {
   std::vector<double> pops, el;
   double t_submit = 0, t_start = 0, t_done = 0;
   std::string err;
+  int err_code = HEOM_ECUDA;      // code heom_server_result returns for a failed request
   size_t host_bytes() const { return sizeof(double) * (size_t)nout * (p.N + 2) + 64; }
   double* h_pops() const { return reinterpret_cast<double*>(host); }
   double* h_el() const { return reinterpret_cast<double*>(host) + nout * p.N; }
@@ -2144,6 +2169,22 @@ struct heom_server {
     return HEOM_OK;
   }
 
+  // Marks a request whose block has finished: done, or failed when a row of
+  // its results is NaN or infinite (a diverging run).
+  static void finish_request(Request& q) {
+    q.pops.assign(q.h_pops(), q.h_pops() + q.nout * q.p.N);
+    q.el.assign(q.h_el(), q.h_el() + 2 * q.nout);
+    q.state = kReqDone;
+    for (double v : q.pops)
+      if (!std::isfinite(v)) q.state = kReqFailed;
+    for (double v : q.el)
+      if (!std::isfinite(v)) q.state = kReqFailed;
+    if (q.state == kReqFailed) {
+      q.err = "non-finite populations or eta: the propagation diverged";
+      q.err_code = HEOM_ENONFINITE;
+    }
+  }
+
   int progress(int32_t* completed) {
     int done = 0;
     // requests whose block has finished
@@ -2153,9 +2194,7 @@ struct heom_server {
         Request& q = *reqs[id];
         if (q.state != kReqRunning) continue;
         if (*reinterpret_cast<volatile int*>(q.h_done()) != 0) {
-          q.pops.assign(q.h_pops(), q.h_pops() + q.nout * q.p.N);
-          q.el.assign(q.h_el(), q.h_el() + 2 * q.nout);
-          q.state = kReqDone;
+          finish_request(q);
           q.t_done = now_s();
           ++done;
         }
@@ -2172,9 +2211,7 @@ struct heom_server {
         if (q.state == kReqRunning) {
           if (e == cudaSuccess && *reinterpret_cast<volatile int*>(q.h_done()) != 0) {
             // finished between the flag scan above and this event query
-            q.pops.assign(q.h_pops(), q.h_pops() + q.nout * q.p.N);
-            q.el.assign(q.h_el(), q.h_el() + 2 * q.nout);
-            q.state = kReqDone;
+            finish_request(q);
           } else {  // the launch ended without the request's flag: it failed
             q.state = kReqFailed;
             q.err = e != cudaSuccess ? cudaGetErrorString(e) : "launch ended before the request finished";
@@ -2350,7 +2387,7 @@ int heom_server_result(heom_server* s, int64_t id, double* pops_out, double* eta
   auto it = s->reqs.find(id);
   if (it == s->reqs.end()) return fail(HEOM_EINVAL, "unknown request %lld", (long long)id);
   Request& q = *it->second;
-  if (q.state == kReqFailed) return fail(HEOM_ECUDA, "request %lld failed: %s", (long long)id, q.err.c_str());
+  if (q.state == kReqFailed) return fail(q.err_code, "request %lld failed: %s", (long long)id, q.err.c_str());
   if (q.state != kReqDone) return fail(HEOM_EINVAL, "request %lld is not finished", (long long)id);
   if (pops_out) memcpy(pops_out, q.pops.data(), sizeof(double) * q.pops.size());
   for (int64_t o = 0; o < q.nout; ++o) {

@@ -19,7 +19,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libheom.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, 1, 2, 3, 4, 5
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ENONFINITE = 0, 1, 2, 3, 4, 5, 6
 FP64, FP32_MIXED = 0, 1
 FLAG_LOW_TEMP = 1  # heom_params.flags: low-temperature correction
 FLAG_SCALED = 2  # heom_params.flags: scaled hierarchy (auxiliaries divided by prod_j sqrt(n_j! s_j^n_j))
