@@ -22,7 +22,8 @@ OBJ = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["heom_kernels_f64_real.cu", "heom_kernels_f64_cplx.cu", "heom_kernels_f32_real.cu",
               "heom_kernels_f32_cplx.cu", "heom_kernels_f32_real_smem.cu", "heom_kernels_f32_cplx_smem.cu",
-              "heom_kernels_scaled_f64.cu", "heom_kernels_scaled_f32.cu", "heom_kernels_large.cu", "heom_runtime.cu"]
+              "heom_kernels_scaled_f64.cu", "heom_kernels_scaled_f32.cu", "heom_kernels_large.cu",
+              "heom_kernels_flow_f32.cu", "heom_kernels_flow_f64.cu", "heom_runtime.cu"]
 CPP_SOURCES = ["heom_index.cpp"]
 
 

@@ -17,6 +17,12 @@ const void* engine_kernel_scaled_f64(int N, bool cplx);
 const void* engine_kernel_scaled_f32(int N, bool cplx);
 // Large-N engine (9..24 sites).
 const void* large_kernel(bool fp64, bool cplx, bool scaled);
+// Dataflow engine (launch mode 3, one hierarchy on the whole GPU), N = 1..8.
+const void* flow_kernel_f32(int N, bool cplx);
+const void* flow_kernel_f64(int N, bool cplx);
+inline const void* flow_kernel(bool fp64, bool cplx, int N) {
+  return fp64 ? flow_kernel_f64(N, cplx) : flow_kernel_f32(N, cplx);
+}
 // Distributed-shared-memory engine (mixed precision only).
 const void* smem_kernel_f32_real(int N, bool reg);
 const void* smem_kernel_f32_cplx(int N, bool reg);

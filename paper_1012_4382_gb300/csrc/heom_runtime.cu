@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "heom.h"
+#include "heom_flow.cuh"
 #include "heom_large.cuh"
 #include "heom_internal.h"
 
@@ -254,10 +255,17 @@ struct Instance {
   std::shared_ptr<Tables> tab;
   DevBuf y, wa, wb, root64, coef, acc, stage, ngam;
   std::vector<unsigned char> coef_host;
+  // dataflow engine (launch mode 3, N <= 8): the model's coefficients in double
+  // (see flow_table), the device copy of the unit table, the tagged stage
+  // buffers and the next call's first tag
+  std::vector<double> flow_src;
+  DevBuf flow_units, flow_tags;
+  unsigned flow_tag = 0;
 };
 
 struct LaunchCfg {
-  int mode = 0;       // 0: cluster teams on device memory, 1: whole grid, 2: cluster teams on shared memory
+  int mode = 0;       // 0: cluster teams on device memory, 1: whole grid, 2: cluster teams on shared
+                      // memory, 3: whole grid, dataflow (block = nodes per CTA x units of a node)
   int team_ctas = 1;
   int block = 256;
   int G = 1;
@@ -376,6 +384,141 @@ void fill_coefficients(const heom_params& p, std::vector<unsigned char>& out, in
     }
   }
   *wsc_offset = off;
+}
+
+// ------------------------------------------------------- dataflow unit table
+//
+// flow_src holds, in rad/fs and 1/fs: J[N][N] = Re H off the diagonal, Ji[N][N]
+// = Im H, eps[N] (mean-shifted site energies), goff[N] = (Gamma_RC + Gamma_phot)/2
+// + c (the off-diagonal damping, c the low-temperature correction), gd[N] =
+// (Gamma_RC + Gamma_phot)/2, alpha[N] = 2 lambda k_B T, beta[N] = lambda gamma,
+// gamma[N], scale[N] (s_j of the scaled hierarchy).
+void fill_flow_src(const heom_params& p, std::vector<double>& v) {
+  const int N = p.N;
+  v.assign((size_t)2 * N * N + 7 * N, 0.0);
+  double* J = v.data();
+  double* Ji = J + N * N;
+  double* eps = Ji + N * N;
+  double *goff = eps + N, *gd = goff + N, *al = gd + N, *be = al + N, *ga = be + N, *sc = ga + N;
+  double mean = 0.0;
+  for (int a = 0; a < N; ++a) mean += p.H[2 * (a * N + a)] + (p.add_reorg_to_H ? p.lambda[a] : 0.0);
+  mean /= N;
+  for (int a = 0; a < N; ++a)
+    for (int b = a + 1; b < N; ++b) {
+      J[a * N + b] = J[b * N + a] = p.H[2 * (a * N + b)] * kCmToRadPerFs;
+      Ji[a * N + b] = p.H[2 * (a * N + b) + 1] * kCmToRadPerFs;
+      Ji[b * N + a] = -Ji[a * N + b];
+    }
+  const double kT = kBoltzmannCmPerK * p.T_kelvin * kCmToRadPerFs;
+  for (int a = 0; a < N; ++a) {
+    const double lam = p.lambda[a] * kCmToRadPerFs, gam = p.gamma[a] * kCmToRadPerFs;
+    const double tr = p.trap_rate ? p.trap_rate[a] * kPerPsToPerFs : 0.0;
+    const double rc = p.recomb_rate ? p.recomb_rate[a] * kPerPsToPerFs : 0.0;
+    eps[a] = (p.H[2 * (a * N + a)] + (p.add_reorg_to_H ? p.lambda[a] : 0.0) - mean) * kCmToRadPerFs;
+    gd[a] = 0.5 * (tr + rc);
+    goff[a] = gd[a] + low_temp_rate(p, a);
+    al[a] = 2.0 * lam * kT;
+    be[a] = lam * gam;
+    ga[a] = gam;
+    sc[a] = scaled_hierarchy_scale(p, a);
+  }
+}
+
+// The own-node part of unit (a, b) of the right-hand side applied to a packed
+// node P (element (k, l): Re sigma_kl for k <= l, Im sigma_lk for k > l):
+// -i[H_eff, sigma]_ab with the site-energy differences and the trap, decay and
+// low-temperature damping, without the node's sum_j n_j gamma_j.
+void flow_unit_apply(int N, const double* src, int a, int b, const double* P, double& re, double& im) {
+  const double* J = src;
+  const double* Ji = J + N * N;
+  const double *eps = Ji + N * N, *goff = eps + N, *gd = goff + N;
+  auto S = [&](int k, int l) { return k <= l ? P[k * N + l] : P[l * N + k]; };
+  auto A = [&](int k, int l) { return k < l ? P[l * N + k] : (k > l ? -P[k * N + l] : 0.0); };
+  re = im = 0.0;
+  if (a != b) {
+    for (int k = 0; k < N; ++k) {
+      const double jak = J[a * N + k], jbk = J[b * N + k], iak = Ji[a * N + k], ibk = Ji[b * N + k];
+      re += jak * A(k, b) - A(a, k) * jbk + iak * S(k, b) + S(a, k) * ibk;
+      im += S(a, k) * jbk - jak * S(k, b) + iak * A(k, b) + A(a, k) * ibk;
+    }
+    const double x = P[a * N + b], yi = P[b * N + a];
+    const double d = eps[a] - eps[b], c = goff[a] + goff[b];
+    re += d * yi - c * x;
+    im -= d * x + c * yi;
+  } else {
+    for (int k = 0; k < N; ++k) re += 2.0 * J[a * N + k] * A(k, a) + 2.0 * Ji[a * N + k] * S(k, a);
+    re -= 2.0 * gd[a] * P[a * N + a];
+  }
+}
+
+// Unit table of the dataflow engine: FlowUnit[U] (pairs in the kernels' order,
+// then diagonals) followed by FlowSite[N].  Each unit's linear form is read
+// off flow_unit_apply on the unit vectors of the packed node.
+int flow_table(const Instance& in, std::vector<unsigned char>& out) {
+  const int N = in.N, NN = N * N, NP = N * (N - 1) / 2, U = NP + N;
+  const double* src = in.flow_src.data();
+  const int nre = heom::flow_nre(N, in.complex_h != 0), nim = heom::flow_nim(N, in.complex_h != 0);
+  out.assign(sizeof(heom::FlowUnit) * U + sizeof(heom::FlowSite) * N, 0);
+  heom::FlowUnit* fu = reinterpret_cast<heom::FlowUnit*>(out.data());
+  std::vector<double> P(NN, 0.0), cr(NN), ci(NN);
+  for (int u = 0; u < U; ++u) {
+    int a, b;
+    if (u < NP) {
+      a = 0;
+      int r = u;
+      while (r >= N - 1 - a) {
+        r -= N - 1 - a;
+        ++a;
+      }
+      b = a + 1 + r;
+    } else {
+      a = b = u - NP;
+    }
+    for (int p = 0; p < NN; ++p) {
+      P[p] = 1.0;
+      flow_unit_apply(N, src, a, b, P.data(), cr[p], ci[p]);
+      P[p] = 0.0;
+    }
+    heom::FlowUnit& f = fu[u];
+    f.a = (uint8_t)a;
+    f.b = (uint8_t)b;
+    const int pab = a * N + b, pba = b * N + a;
+    auto fill = [&](const std::vector<double>& c, uint8_t* idx, double* w, int cap, bool any) -> bool {
+      for (int i = 0; i < cap; ++i) {
+        idx[i] = (uint8_t)pab;
+        w[i] = 0.0;
+      }
+      if (!any) return true;
+      // slot 0: x; slot 1: yi (pairs only: the kernel adds the node's terms there)
+      idx[0] = (uint8_t)pab;
+      w[0] = c[pab];
+      int k = 1;
+      if (a != b) {
+        idx[1] = (uint8_t)pba;
+        w[1] = c[pba];
+        k = 2;
+      }
+      for (int p = 0; p < NN; ++p) {
+        if (p == pab || p == pba || c[p] == 0.0) continue;
+        if (k >= cap) return false;
+        idx[k] = (uint8_t)p;
+        w[k] = c[p];
+        ++k;
+      }
+      return true;
+    };
+    if (!fill(cr, f.ire, f.cre, nre, true) || !fill(ci, f.iim, f.cim, nim, a != b))
+      return fail(HEOM_ECUDA, "dataflow unit table: unit (%d,%d) has more terms than its kernel holds", a, b);
+  }
+  heom::FlowSite* fs = reinterpret_cast<heom::FlowSite*>(out.data() + sizeof(heom::FlowUnit) * U);
+  const double* al = src + 2 * NN + 3 * N;
+  for (int a = 0; a < N; ++a) {
+    fs[a].alpha = al[a];
+    fs[a].beta = al[N + a];
+    fs[a].gamma = al[2 * N + a];
+    fs[a].scale = al[3 * N + a];
+  }
+  return HEOM_OK;
 }
 
 int validate(const heom_params* p, int idx) {
@@ -628,6 +771,7 @@ struct Engine {
     in->Mpad = (int)((in->M + 31) / 32 * 32);
     in->terminator = p.terminator;
     in->scaled = (p.flags & HEOM_FLAG_SCALED) ? 1 : 0;
+    if (p.N <= heom::kMaxSmallN) fill_flow_src(p, in->flow_src);
     if (prec == HEOM_FP64)
       fill_coefficients<double>(p, in->coef_host, &in->complex_h, &in->wsc_offset);
     else
@@ -822,7 +966,9 @@ struct Engine {
       if (!kernel_for(g.N, g.cplx, g.sc, g.c))
         return fail(HEOM_EUNSUPPORTED, "no engine kernel for N=%d, launch mode %d, node_threads %d%s", g.N, g.c.mode,
                     g.c.G, no_kernel_reason(g.N, g.sc));
-      if (g.c.mode == 1) {
+      if (g.c.mode == 3 && count != 1)
+        return fail(HEOM_EUNSUPPORTED, "launch mode 3 (dataflow) propagates a single hierarchy, not a batch");
+      if (g.c.mode == 1 || g.c.mode == 3) {
         g.nteams = 1;
       } else {
         int maxc = max_active_teams(g.N, g.cplx, g.sc, g.c, g.dyn);
@@ -862,7 +1008,7 @@ struct Engine {
     }
     if (graph_args) {
       for (auto& g : groups)
-        if (g.c.mode == 1) return fail(HEOM_EUNSUPPORTED, "CUDA graphs take launch modes 0 and 2");
+        if (g.c.mode == 1 || g.c.mode == 3) return fail(HEOM_EUNSUPPORTED, "CUDA graphs take launch modes 0 and 2");
       std::vector<unsigned char> hg(bytes, 0);
       memcpy(hg.data(), hi.data(), sizeof(Inst) * count);
       for (size_t k = 0; k < groups.size(); ++k) {
@@ -946,8 +1092,69 @@ struct Engine {
       A.team_ctas = g.c.team_ctas;
       A.gsync = d_gsync.as<unsigned>();
       A.status = d_status.as<int>();
+      if (g.c.mode == 3) {
+        TRY(launch_flow(*inst[g.list[0]], g.c, A.insts + g.list[0], A.status, nsteps[g.list[0]]));
+        continue;
+      }
       TRY(launch(g.N, g.cplx, g.sc, g.c, g.nteams, A, g.B, g.dyn));
     }
+    return HEOM_OK;
+  }
+
+  // Nodes per CTA of the dataflow engine for a block of `block` threads.
+  static int flow_nodes_per_cta(int N, int block) { return std::max(1, block / (N * (N + 1) / 2)); }
+
+  // The dataflow engine (mode 3) on one instance: the unit table and the
+  // tagged stage buffers on first use, the tag base, one cooperative launch.
+  int launch_flow(Instance& in, const LaunchCfg& c, const Inst* d_inst, int* d_status, int64_t nsteps) {
+    const int N = in.N, U = N * (N + 1) / 2, NN = N * N;
+    const bool fp64 = prec == HEOM_FP64;
+    const void* k = heom::flow_kernel(fp64, in.complex_h != 0, N);
+    if (!k) return fail(HEOM_EUNSUPPORTED, "launch mode 3 takes at most %d sites", heom::kMaxSmallN);
+    if (nsteps > (int64_t)1 << 29) return fail(HEOM_EINVAL, "launch mode 3 takes at most 2^29 steps per call");
+    const int S = flow_nodes_per_cta(N, c.block);
+    const int threads = S * U;
+    if (threads > heom::kFlowMaxThreads)
+      return fail(HEOM_EINVAL, "launch mode 3: %d nodes x %d units exceed %d threads", S, U, heom::kFlowMaxThreads);
+    const int grid = (int)((in.M + S - 1) / S);
+    const int dyn = heom::flow_smem_bytes(N, S, (int)rsize());
+    const long long wd = fp64 ? 2 : 1;
+    const long long stride = (long long)NN * in.Mpad * wd;
+    if (!in.flow_tags.p) {
+      std::vector<unsigned char> tab;
+      TRY(flow_table(in, tab));
+      TRY(in.flow_units.alloc(tab.size(), hooks));
+      CUDA_TRY(cudaMemcpy(in.flow_units.p, tab.data(), tab.size(), cudaMemcpyHostToDevice));
+      TRY(in.flow_tags.alloc(sizeof(unsigned long long) * (3 * stride + heom::kFlowRing), hooks));
+      CUDA_TRY(cudaMemsetAsync(in.flow_tags.p, 0, in.flow_tags.bytes, stream));
+      in.flow_tag = 0;
+    }
+    const unsigned need = (unsigned)(4 * nsteps + 2);
+    if (in.flow_tag > 0xF0000000u - need) {
+      // the 32-bit tags would wrap: clear the buffers and start again from 0
+      CUDA_TRY(cudaMemsetAsync(in.flow_tags.p, 0, in.flow_tags.bytes, stream));
+      in.flow_tag = 0;
+    }
+    CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    int per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, dyn));
+    if ((int64_t)per_sm * sms < grid)
+      return fail(HEOM_EINVAL,
+                  "launch mode 3: %d CTAs of %d nodes (%d threads) cannot all be resident (%d per SM); use "
+                  "more nodes per CTA or another mode",
+                  grid, S, threads, per_sm);
+    heom::FlowArgs F;
+    F.inst = d_inst;
+    F.units = in.flow_units.as<heom::FlowUnit>();
+    F.tags = in.flow_tags.as<unsigned long long>();
+    F.tag_stride = stride;
+    F.ring = F.tags + 3 * stride;
+    F.status = d_status;
+    F.S = S;
+    F.tag0 = in.flow_tag;
+    in.flow_tag += need;
+    void* args[] = {&F};
+    CUDA_TRY(cudaLaunchCooperativeKernel(k, dim3(grid), dim3(threads), args, dyn, stream));
     return HEOM_OK;
   }
 
@@ -955,6 +1162,7 @@ struct Engine {
   // FP64 or N > 8; scaled hierarchies in mode 2 or with the register view
   // (node_threads <= 2) for N <= 8.
   const void* kernel_for(int N, int cplx, int sc, const LaunchCfg& c) const {
+    if (c.mode == 3) return N > heom::kMaxSmallN ? nullptr : heom::flow_kernel(prec == HEOM_FP64, cplx != 0, N);
     if (N > heom::kMaxSmallN) return c.mode == 2 ? nullptr : heom::large_kernel(prec == HEOM_FP64, cplx != 0, sc != 0);
     if (c.mode == 2) return (prec == HEOM_FP64 || sc) ? nullptr : heom::smem_kernel(cplx != 0, c.G <= 2, N);
     return heom::engine_kernel(prec == HEOM_FP64, cplx != 0, c.G <= 2, N, sc != 0);
@@ -1362,15 +1570,24 @@ int heom_set_launch(heom_ctx* ctx, int32_t mode, int32_t team_ctas, int32_t bloc
   if (team_ctas > 0) n.team_ctas = team_ctas;
   if (block_threads > 0) n.block = block_threads;
   if (node_threads > 0) n.G = node_threads;
-  if (n.mode < 0 || n.mode > 2) return fail(HEOM_EINVAL, "mode must be 0, 1 or 2");
+  if (n.mode < 0 || n.mode > 3) return fail(HEOM_EINVAL, "mode must be 0, 1, 2 or 3");
   if (n.mode == 2 && ctx->e.prec == HEOM_FP64) return fail(HEOM_EINVAL, "mode 2 (shared memory) needs HEOM_FP32_MIXED");
-  if (ctx->e.inst[0]->N > heom::kMaxSmallN && (n.mode == 2 || n.block > 256))
+  const int N = ctx->e.inst[0]->N;
+  if (N > heom::kMaxSmallN && (n.mode == 2 || n.mode == 3 || n.block > 256))
     return fail(HEOM_EINVAL, "hierarchies with more than %d sites take modes 0 and 1 with at most 256 threads",
                 heom::kMaxSmallN);
   if (n.team_ctas < 1 || n.team_ctas > 16) return fail(HEOM_EINVAL, "team_ctas must be 1..16");
-  const int maxb = ctx->e.max_block();
-  if (n.block < 64 || n.block > maxb || n.block % 32)
-    return fail(HEOM_EINVAL, "block_threads must be 64..%d, multiple of 32", maxb);
+  if (n.mode == 3) {
+    // block_threads: the CTA size asked for; a CTA runs block_threads / U whole nodes (U = N(N+1)/2)
+    const int U = N * (N + 1) / 2;
+    if (n.block < U || n.block > heom::kFlowMaxThreads)
+      return fail(HEOM_EINVAL, "mode 3: block_threads must be %d..%d (at least one node of %d units)", U,
+                  heom::kFlowMaxThreads, U);
+  } else {
+    const int maxb = ctx->e.max_block();
+    if (n.block < 64 || n.block > maxb || n.block % 32)
+      return fail(HEOM_EINVAL, "block_threads must be 64..%d, multiple of 32", maxb);
+  }
   if (n.G < 1 || n.G > 32) return fail(HEOM_EINVAL, "node_threads must be 1..32");
   c = n;
   return HEOM_OK;
@@ -1426,6 +1643,18 @@ int heom_autotune(heom_ctx* ctx, int64_t trial_steps, double* best_us_per_step) 
       c.G = G;
       cands.push_back(c);
     }
+    if (!large && G == 1) {
+      // the dataflow engine: S nodes per CTA (its unit groups are fixed: one thread per unit)
+      const int U = in.N * (in.N + 1) / 2;
+      for (int S : {4, 6, 8, 10, 12, 13, 16, 24, 32, 64}) {
+        if (S * U > heom::kFlowMaxThreads) continue;
+        LaunchCfg c;
+        c.mode = 3;
+        c.block = S * U;
+        c.G = 1;
+        cands.push_back(c);
+      }
+    }
     if (e.prec == HEOM_FP32_MIXED && !large)
       for (int block : {256, 512})
         for (int ctas : {1, 2, 4, 8, 16}) {
@@ -1452,7 +1681,7 @@ int heom_autotune(heom_ctx* ctx, int64_t trial_steps, double* best_us_per_step) 
     const int dyn = large ? heom::large_smem_bytes(in.N, (int)e.rsize())
                           : (c.mode == 2 ? heom::smem_dyn_bytes(in.N, Engine::smem_slice(in.M, c.team_ctas))
                                          : heom::engine_dyn_bytes(in.N, c.block, (int)e.rsize(), c.G <= 2));
-    if (c.mode != 1 && e.max_active_teams(in.N, in.complex_h, in.scaled, c, dyn) < 1) {
+    if (c.mode != 1 && c.mode != 3 && e.max_active_teams(in.N, in.complex_h, in.scaled, c, dyn) < 1) {
       t_err.clear();
       continue;
     }
