@@ -61,7 +61,10 @@ def parse():
                     help="requests replayed from the serving trace (the full trace has 2000)")
     ap.add_argument("--cpu-sample-steps", type=int, default=0, help="RK4 steps of the oracle sample (0: auto)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline (profiling runs)")
-    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes (profiling runs)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time every candidate launch shape first and keep the fastest (default: the library's "
+                         "default shapes, the ones the full-horizon parity tests run)")
+    ap.add_argument("--no-autotune", action="store_true", help="accepted for older command lines; the default")
     ap.add_argument("--launch", default="",
                     help="mode,team_ctas,block,node_threads for the mixed path instead of autotuning (profiling runs)")
     ap.add_argument("--solve-steps", type=int, default=0,
@@ -431,7 +434,7 @@ def main():
         if args.launch and prec == "fp32":
             m, c, b, g = (int(x) for x in args.launch.split(","))
             ctx.set_launch(mode=m, team_ctas=c, block_threads=b, node_threads=g)
-        elif not args.no_autotune:
+        elif args.autotune:
             ctx.autotune(trial_steps=200)
         results[prec] = {"ctx": ctx, "launch": ctx.get_launch()}
 
@@ -503,10 +506,12 @@ def main():
     peak, peak_kind = peaks()
     l2_gbs = l2_copy_gbs(torch, dev)
     roof = roofline_block(N, nodes, nsteps, launch_ms, 4, peak, peak_kind,
-                          traffic_from_profile("engine_fmo7_k6_mixed.md"),
+                          traffic_from_profile("flow_fmo7_k6_mixed.md" if results["fp32"]["launch"]["mode"] == 3
+                                               else "engine_fmo7_k6_mixed.md"),
                           kernel_name(results["fp32"]["launch"], N, "f32"),
                           "the 1 MB working set is L2-resident: the launch is bound by the latency of its "
-                          "40 000 dependent stages, not by a bandwidth")
+                          "40 000 dependent stages (one L2 exchange of stage-tagged neighbour words each), not by "
+                          "a bandwidth")
     roof["l2_copy_gbs_measured"] = l2_gbs
     roof["frac_of_l2_copy"] = roof["achieved"] / l2_gbs
 
@@ -568,6 +573,8 @@ def kernel_name(launch, N, prec):
         return "heom_large_kernel<%s>" % prec
     if mode == 2:
         return "heom_smem_kernel<%d> (distributed shared memory)" % N
+    if mode == 3:
+        return "heom_flow_kernel<%d, %s> (dataflow, %d threads per CTA)" % (N, prec, launch.get("block_threads", 0))
     return "heom_engine_kernel<%d, %s>%s" % (N, prec, " (cooperative grid)" if mode == 1 else "")
 
 

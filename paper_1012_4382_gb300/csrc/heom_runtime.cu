@@ -720,8 +720,29 @@ struct Engine {
       return c;
     }
     if (count == 1) {
-      // one hierarchy: the whole GPU with one unit per warp for large enough
-      // hierarchies (measured best on the FMO-like N = 7, depth 6 workload)
+      // one hierarchy of 256 nodes or more: the dataflow engine (mode 3) with one CTA
+      // per SM, S = ceil(M / SMs) nodes each (measured best on the FMO-like N = 7,
+      // depth 6 workload: S = 12, 1.2-1.4 us per RK4 stage in mixed precision), when
+      // all its CTAs fit on the GPU at once
+      if (Mmax >= 256) {
+        const int U = N * (N + 1) / 2;
+        const int S = (int)std::min<int64_t>(heom::kFlowMaxThreads / U, (Mmax + sms - 1) / sms);
+        const void* k = heom::flow_kernel(prec == HEOM_FP64, false, N);
+        int per_sm = 0;
+        if (S >= 1 && k &&
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 heom::flow_smem_bytes(N, S, (int)rsize())) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, S * U, heom::flow_smem_bytes(N, S, (int)rsize())) ==
+                cudaSuccess &&
+            (int64_t)per_sm * sms >= (Mmax + S - 1) / S) {
+          c.mode = 3;
+          c.block = S * U;
+          c.G = 1;
+          c.team_ctas = 1;
+          return c;
+        }
+        cudaGetLastError();
+      }
       if ((prec == HEOM_FP64 && Mmax >= 256) || (prec == HEOM_FP32_MIXED && Mmax >= 1024)) {
         c.mode = 1;
         c.block = max_block();
@@ -1571,6 +1592,12 @@ int heom_set_launch(heom_ctx* ctx, int32_t mode, int32_t team_ctas, int32_t bloc
   if (block_threads > 0) n.block = block_threads;
   if (node_threads > 0) n.G = node_threads;
   if (n.mode < 0 || n.mode > 3) return fail(HEOM_EINVAL, "mode must be 0, 1, 2 or 3");
+  if (block_threads <= 0 && (n.mode == 3) != (c.mode == 3)) {
+    // a block size of the other family of engines does not carry over: take that family's default
+    const int N = ctx->e.inst[0]->N;
+    const int U = N * (N + 1) / 2;
+    n.block = n.mode == 3 ? std::max(U, heom::kFlowMaxThreads / U * U) : ctx->e.max_block();
+  }
   if (n.mode == 2 && ctx->e.prec == HEOM_FP64) return fail(HEOM_EINVAL, "mode 2 (shared memory) needs HEOM_FP32_MIXED");
   const int N = ctx->e.inst[0]->N;
   if (N > heom::kMaxSmallN && (n.mode == 2 || n.mode == 3 || n.block > 256))
