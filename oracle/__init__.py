@@ -44,6 +44,8 @@ def build(force: bool = False) -> str:
         os.replace(tmp, _LIB)
         with open(stamp, "w") as f:
             f.write(" ".join(_FLAGS))
+    from . import redfield  # the secular Redfield comparison model, same flags
+    redfield.build()
     return _LIB
 
 

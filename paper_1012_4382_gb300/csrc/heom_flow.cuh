@@ -133,6 +133,40 @@ __host__ __device__ constexpr int flow_words() {
   return sizeof(R) == 8 ? 2 : 1;
 }
 
+// The eta and loss row `row` from the diagonal owners' running sums in shared
+// memory (the same sums, in the same order, as eta_total reads from the parts
+// slots), and the check of the row for NaN or infinity; the population row
+// is the root's diagonal of the step's y, also in shared memory.
+template <typename R, bool MIXED>
+__device__ __forceinline__ void flow_eta_row(const Inst& I, const EtaAcc<R>* ea, const FF* trace_ff,
+                                             const double* trace_d, int N, double acc0, double acc1, int64_t row,
+                                             int* status) {
+  double e, l;
+  if constexpr (sizeof(R) == 4) {
+    FF se{0.f, 0.f}, sl{0.f, 0.f};
+    for (int k = 0; k < N; ++k) {
+      se = ff_add(se, ea[k].e);
+      sl = ff_add(sl, ea[k].l);
+    }
+    e = acc0 + ff_to_double(se);
+    l = acc1 + ff_to_double(sl);
+  } else {
+    double se = 0.0, sl = 0.0;
+    for (int k = 0; k < N; ++k) {
+      se += ea[k].e;
+      sl += ea[k].l;
+    }
+    e = acc0 + se;
+    l = acc1 + sl;
+  }
+  flag_nonfinite(status, e);
+  flag_nonfinite(status, l);
+  for (int k = 0; k < N; ++k) flag_nonfinite(status, MIXED ? ff_to_double(trace_ff[k]) : trace_d[k]);
+  if (!I.out_el) return;
+  I.out_el[2 * row] = e;
+  I.out_el[2 * row + 1] = l;
+}
+
 // ------------------------------------------------------------------ kernel
 
 template <int N, typename R, bool MIXED, bool CPLX>
@@ -294,7 +328,7 @@ __global__ void __launch_bounds__(kFlowMaxThreads) heom_flow_kernel(FlowArgs A) 
 #pragma unroll 1
     for (int s = 0; s < 4; ++s) {
       if (s == 0 && rows.pending >= 0) {
-        if (lead) eta_write_row<R>(I, N, rows.acc0, rows.acc1, rows.pending, A.status);
+        if (lead) flow_eta_row<R, MIXED>(I, s_ea, s_trace_ff, s_trace_d, N, rows.acc0, rows.acc1, rows.pending, A.status);
         rows.pending = -1;
       }
       const int in_sel = (s == 0) ? 0 : (s == 2 ? 2 : 1);
