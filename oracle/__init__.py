@@ -63,6 +63,7 @@ class _Params(ctypes.Structure):
         ("add_reorg", ctypes.c_int32),
         ("low_temp", ctypes.c_int32),
         ("scaled", ctypes.c_int32),
+        ("keep", ctypes.POINTER(ctypes.c_ubyte)),
     ]
 
 
@@ -121,9 +122,17 @@ class _Keep:
         self.gam = _f64(np.broadcast_to(np.asarray(p["gam"], dtype=np.float64), (N,)), N)
         self.trap = _f64(p.get("trap"), N)
         self.recomb = _f64(p.get("recomb"), N)
+        # keep: optional boolean flags per node in the order of multi_indices(N, K) (the filtered hierarchy)
+        self.keep = None
+        if p.get("keep") is not None:
+            self.keep = np.ascontiguousarray(np.asarray(p["keep"], dtype=np.uint8))
+            if self.keep.size != num_nodes(N, int(p["K"])):
+                raise ValueError("keep needs one flag per node")
+        keep_ptr = (self.keep.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)) if self.keep is not None
+                    else ctypes.cast(None, ctypes.POINTER(ctypes.c_ubyte)))
         self.c = _Params(N, int(p["K"]), _dptr(self.H), _dptr(self.lam), _dptr(self.gam), float(p["T"]),
                          _dptr(self.trap), _dptr(self.recomb), int(p.get("terminator", 0)),
-                         int(p.get("add_reorg", 0)), int(p.get("low_temp", 0)), int(p.get("scaled", 0)))
+                         int(p.get("add_reorg", 0)), int(p.get("low_temp", 0)), int(p.get("scaled", 0)), keep_ptr)
 
 
 def set_threads(n: int) -> None:
@@ -171,7 +180,8 @@ def propagate(params: dict, rho0, dt_fs: float, nsteps: int, out_every: int = 1,
     ``params`` keys: N, K, H (N x N complex, cm^-1), lam, gam (cm^-1, scalar or
     per site), T (K), trap, recomb (ps^-1 per site, optional), terminator
     (0/1), add_reorg (0/1), low_temp (0/1: low-temperature correction),
-    scaled (0/1: rescaled auxiliaries; the state then holds sigma~_n).
+    scaled (0/1: rescaled auxiliaries; the state then holds sigma~_n), keep (optional
+    flags per node in the order of :func:`multi_indices`: nodes flagged 0 are removed).
     Returns a dict with pops [nout, N], trace [nout], eta [nout], loss [nout],
     tmean [nout] (trapping time <t> up to each row, fs), steps_done,
     rho [N, N] complex, and with ``want_state`` the full final state

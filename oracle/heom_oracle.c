@@ -108,6 +108,9 @@ typedef struct {
   int32_t add_reorg;       /* 1: eps_m -> eps_m + lambda_m (Eq. H_ex) */
   int32_t low_temp;        /* 1: lowest-order quantum (low-temperature) correction */
   int32_t scaled;          /* 1: scaled auxiliaries sigma~_n = sigma_n / S(n) (see the header) */
+  const unsigned char* keep; /* NULL, or one flag per node in the order of oracle_multi_indices: a node
+                                with flag 0 is removed from the hierarchy (its matrix stays zero, so
+                                every link to it contributes nothing) -- the filtered hierarchy */
 } oracle_params;
 
 /* ---------------------------------------------------------------------- */
@@ -230,6 +233,7 @@ typedef struct {
   double* ltc;       /* N, fs^-1: low-temperature correction rate per bath (0: off) */
   double* scale;     /* N, rad^2/fs^2: s_j of the scaled hierarchy, or NULL (unscaled) */
   int terminator;
+  const unsigned char* keep; /* the caller's node flags (oracle_params.keep), or NULL: every node */
   hierarchy hier;
 } model;
 
@@ -275,6 +279,7 @@ static int model_build(model* m, const oracle_params* p) {
   }
   m->kT = cm_to_rad_per_fs(OR_KB_CM_PER_K * p->T);
   m->terminator = p->terminator;
+  m->keep = p->keep;
   /* Lowest-order quantum correction (the paper cites Ishizaki-Fleming for it):
    * the Drude-Lorentz correlation function has, besides the exp(-gamma t)
    * term kept in the hierarchy, Matsubara terms
@@ -375,6 +380,7 @@ static void rhs_node(const model* m, long i, const cplx* state, cplx* out, cplx*
   const cplx* x = state + i * DD;
   cplx* o = out + i * DD;
   for (size_t e = 0; e < DD; ++e) o[e] = 0;
+  if (m->keep && !m->keep[i]) return; /* removed from the (filtered) hierarchy */
 
   /* -i [H_ex, sigma_n] */
   add_commutator(m, x, o);

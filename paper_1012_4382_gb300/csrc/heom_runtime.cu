@@ -231,6 +231,23 @@ __global__ void pack_state_kernel(const double* in, R* y, int Mpad, int64_t M, i
 
 int launch_blocks(int64_t work, int threads) { return (int)((work + threads - 1) / threads); }
 
+// Largest element modulus of every node's matrix (packed, element-major):
+// out[n] = max_ab |sigma_n,ab|, one thread per node.
+template <typename R>
+__global__ void node_max_kernel(const R* y, int Mpad, int64_t M, int N, double* out) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= M) return;
+  double mx = 0.0;
+  for (int a = 0; a < N; ++a) {
+    mx = fmax(mx, fabs((double)y[(size_t)(a * N + a) * Mpad + n]));
+    for (int b = a + 1; b < N; ++b) {
+      const double re = (double)y[(size_t)(a * N + b) * Mpad + n], im = (double)y[(size_t)(b * N + a) * Mpad + n];
+      mx = fmax(mx, sqrt(re * re + im * im));
+    }
+  }
+  out[n] = mx;
+}
+
 // --------------------------------------------------------------- structures
 
 struct Tables {
@@ -615,6 +632,7 @@ struct Engine {
   std::shared_ptr<TableCache> tables = std::make_shared<TableCache>();
   std::map<int, LaunchCfg> cfg;  // per N
   double stop_trace = 0.0;        // the stop rule (0: off)
+  const uint8_t* subset_keep = nullptr;  // while a filtered context is created: its node flags
   bool pageable_args = false;     // stage launch descriptors from pageable memory (servers)
   std::vector<unsigned char> h_args_pageable;
   // per-instance output destinations and cadences (servers); empty = contiguous buffers
@@ -799,7 +817,14 @@ struct Engine {
       fill_coefficients<float>(p, in->coef_host, &in->complex_h, &in->wsc_offset);
     auto key = std::make_pair(p.N, p.K);
     auto it = tables->find(key);
-    if (it == tables->end()) {
+    if (subset_keep) {
+      // a filtered hierarchy: private tables over the kept nodes
+      auto t = std::make_shared<Tables>();
+      TRY(build_subset_tables(p, subset_keep, *t));
+      in->M = t->M;
+      in->Mpad = t->Mpad;
+      in->tab = t;
+    } else if (it == tables->end()) {
       auto t = std::make_shared<Tables>();
       t->N = p.N;
       t->K = p.K;
@@ -856,6 +881,54 @@ struct Engine {
     CUDA_TRY(cudaMemsetAsync(in->acc.p, 0, kAccDoubles * sizeof(double), stream));
     CUDA_TRY(cudaStreamSynchronize(stream));  // coef_host must outlive the copy
     inst.push_back(std::move(in));
+    return HEOM_OK;
+  }
+
+  // Node tables of the hierarchy restricted to the nodes with keep[i] != 0
+  // (heom_build_index order): the kept nodes in their order, links to removed
+  // nodes dropped (-1), the set checked to hold the root and to be closed
+  // downwards (every n - e_j of a kept n kept).
+  int build_subset_tables(const heom_params& p, const uint8_t* keep, Tables& t) {
+    const int N = p.N;
+    heom::Index idx;
+    heom::build_index(N, p.K, idx);
+    const int64_t Mfull = idx.M;
+    if (!keep[0]) return fail(HEOM_EINVAL, "the filtered hierarchy must keep the root node (node 0)");
+    std::vector<int32_t> sub(Mfull, -1);
+    int64_t M = 0;
+    for (int64_t i = 0; i < Mfull; ++i)
+      if (keep[i]) {
+        for (int j = 0; j < N; ++j) {
+          const int32_t d = idx.down[(size_t)i * N + j];
+          if (d >= 0 && !keep[d])
+            return fail(HEOM_EINVAL, "the node set is not closed downwards: node %lld is kept, its n - e_%d (node %d) "
+                                     "is not", (long long)i, j, d);
+        }
+        sub[i] = (int32_t)M++;
+      }
+    t.N = N;
+    t.K = p.K;
+    t.M = M;
+    t.Mpad = (int)((M + 31) / 32 * 32);
+    t.multi.assign((size_t)M * N, 0);
+    std::vector<int32_t> up((size_t)N * t.Mpad, -1), dn((size_t)N * t.Mpad, -1);
+    for (int64_t i = 0; i < Mfull; ++i) {
+      const int32_t si = sub[i];
+      if (si < 0) continue;
+      for (int j = 0; j < N; ++j) {
+        t.multi[(size_t)si * N + j] = idx.multi[(size_t)i * N + j];
+        const int32_t u = idx.up[(size_t)i * N + j];
+        up[(size_t)j * t.Mpad + si] = u >= 0 ? sub[u] : -1;
+        const int32_t d = idx.down[(size_t)i * N + j];
+        const int32_t nj = idx.multi[(size_t)i * N + j];
+        dn[(size_t)j * t.Mpad + si] = d < 0 ? -1 : ((nj << 24) | sub[d]);
+      }
+    }
+    TRY(t.up.alloc(up.size() * 4, hooks));
+    TRY(t.dn.alloc(dn.size() * 4, hooks));
+    CUDA_TRY(cudaMemcpyAsync(t.up.p, up.data(), up.size() * 4, cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(cudaMemcpyAsync(t.dn.p, dn.data(), dn.size() * 4, cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(cudaStreamSynchronize(stream));
     return HEOM_OK;
   }
 
@@ -1505,6 +1578,59 @@ int heom_create(const heom_params* params, void* cuda_stream, heom_ctx** out) {
   auto c = std::make_unique<heom_ctx>();
   TRY(c->e.init(params, 1, cuda_stream));
   *out = c.release();
+  return HEOM_OK;
+}
+
+int heom_create_subset(const heom_params* params, const uint8_t* keep, void* cuda_stream, heom_ctx** out) {
+  if (!out) return fail(HEOM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!keep) return fail(HEOM_EINVAL, "keep is NULL");
+  TRY(validate(params, 0));
+  if (params->terminator != HEOM_TERM_NONE)
+    return fail(HEOM_EUNSUPPORTED, "a filtered hierarchy takes the plain truncation (HEOM_TERM_NONE)");
+  auto c = std::make_unique<heom_ctx>();
+  c->e.subset_keep = keep;
+  const int rc = c->e.init(params, 1, cuda_stream);
+  c->e.subset_keep = nullptr;
+  TRY(rc);
+  *out = c.release();
+  return HEOM_OK;
+}
+
+int heom_node_magnitudes(heom_ctx* ctx, double* node_max) {
+  if (!ctx || !node_max) return fail(HEOM_EINVAL, "ctx or node_max is NULL");
+  Engine& e = ctx->e;
+  TRY(e.ensure_device());
+  Instance& in = *e.inst[0];
+  const size_t need = sizeof(double) * (size_t)in.M;
+  if (e.d_out.bytes < need) TRY(e.d_out.alloc(need, e.hooks));
+  if (e.prec == HEOM_FP64)
+    node_max_kernel<double><<<launch_blocks(in.M, 256), 256, 0, e.stream>>>(in.y.as<double>(), in.Mpad, in.M, in.N,
+                                                                          e.d_out.as<double>());
+  else
+    node_max_kernel<float><<<launch_blocks(in.M, 256), 256, 0, e.stream>>>(in.y.as<float>(), in.Mpad, in.M, in.N,
+                                                                         e.d_out.as<double>());
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(e.stream));
+  CUDA_TRY(cudaMemcpy(node_max, e.d_out.p, need, cudaMemcpyDeviceToHost));
+  return HEOM_OK;
+}
+
+int heom_filter_select(int32_t N, int32_t K, const double* node_max, double delta, uint8_t* keep) {
+  int64_t M = 0;
+  TRY(heom_num_nodes(N, K, &M));
+  if (!node_max || !keep) return fail(HEOM_EINVAL, "node_max or keep is NULL");
+  if (!(delta >= 0.0)) return fail(HEOM_EINVAL, "delta must be >= 0 (not NaN)");
+  heom::Index idx;
+  heom::build_index(N, K, idx);
+  for (int64_t i = 0; i < M; ++i) keep[i] = (i == 0 || !(node_max[i] < delta)) ? 1 : 0;
+  // close downwards: nodes are ordered by level, so one pass from the deepest suffices
+  for (int64_t i = M - 1; i > 0; --i)
+    if (keep[i])
+      for (int j = 0; j < N; ++j) {
+        const int32_t d = idx.down[(size_t)i * N + j];
+        if (d >= 0) keep[d] = 1;
+      }
   return HEOM_OK;
 }
 

@@ -106,6 +106,10 @@ def lib() -> ctypes.CDLL:
             "heom_batch_set_launch": [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
             "heom_batch_get_launch": [vp, ctypes.c_int32, _i32p, _i32p, _i32p, _i32p],
             "heom_batch_autotune": [vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)],
+            "heom_node_magnitudes": [vp, _dp],
+            "heom_filter_select": [ctypes.c_int32, ctypes.c_int32, _dp, ctypes.c_double,
+                                   ctypes.POINTER(ctypes.c_uint8)],
+            "heom_create_subset": [ctypes.POINTER(_Params), ctypes.POINTER(ctypes.c_uint8), vp, ctypes.POINTER(vp)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -255,18 +259,48 @@ def use_torch_allocator(enable: bool = True) -> None:
     _hooks = hooks
 
 
-class Context:
-    """One hierarchy resident on the GPU (heom_create ... heom_destroy)."""
+def filter_select(N: int, K: int, node_max, delta: float) -> np.ndarray:
+    """heom_filter_select: node flags (uint8, heom_build_index order) of the
+    filtered hierarchy -- nodes with node_max >= delta, the root, closed downwards."""
+    M = num_nodes(N, K)
+    nm = _f64(node_max)
+    if nm.size != M:
+        raise ValueError("node_max needs one value per node (%d)" % M)
+    keep = np.zeros(M, np.uint8)
+    _check(lib().heom_filter_select(int(N), int(K), _ptr(nm), float(delta),
+                                    keep.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+    return keep
 
-    def __init__(self, params: dict, precision="fp64", stream=None):
+
+class Context:
+    """One hierarchy resident on the GPU (heom_create ... heom_destroy); with
+    `keep` (flags per node of the full hierarchy, heom_build_index order) the
+    filtered hierarchy over the kept nodes (heom_create_subset)."""
+
+    def __init__(self, params: dict, precision="fp64", stream=None, keep=None):
         self._keep = _Keep(params, _precision(precision))
         self.N = int(params["N"])
         self.K = int(params["K"])
         self.precision = _precision(precision)
         self._h = ctypes.c_void_p()
-        _check(lib().heom_create(ctypes.byref(self._keep.c), ctypes.c_void_p(_stream_handle(stream)),
-                                 ctypes.byref(self._h)))
-        self.nodes = num_nodes(self.N, self.K)
+        if keep is None:
+            _check(lib().heom_create(ctypes.byref(self._keep.c), ctypes.c_void_p(_stream_handle(stream)),
+                                     ctypes.byref(self._h)))
+            self.nodes = num_nodes(self.N, self.K)
+        else:
+            self.keep = np.ascontiguousarray(np.asarray(keep, dtype=np.uint8))
+            if self.keep.size != num_nodes(self.N, self.K):
+                raise ValueError("keep needs one flag per node of the full hierarchy")
+            _check(lib().heom_create_subset(ctypes.byref(self._keep.c),
+                                            self.keep.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                            ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(self._h)))
+            self.nodes = int(np.count_nonzero(self.keep))
+
+    def node_magnitudes(self) -> np.ndarray:
+        """heom_node_magnitudes: max_ab |sigma_n,ab| per node of the current state."""
+        out = np.zeros(self.nodes)
+        _check(lib().heom_node_magnitudes(self._h, _ptr(out)))
+        return out
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -1,0 +1,117 @@
+"""Filtered hierarchies on the GPU (heom_node_magnitudes, heom_filter_select,
+heom_create_subset) against the oracle: the node magnitudes of a scaled
+state, and a filtered context in every engine against the oracle propagating
+the same node set (nodes removed from its hierarchy), element by element."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1012_4382_gb300 import build as heom_build
+from paper_1012_4382_gb300 import heom, workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32_POP = 1e-5
+TOL32_ETA = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    heom_build.build()
+
+
+def _perm(N, K):
+    """library node order -> oracle node order"""
+    multi, _, _ = heom.build_index(N, K)
+    pos = {tuple(m): i for i, m in enumerate(oracle.multi_indices(N, K).tolist())}
+    return np.array([pos[tuple(m)] for m in multi.tolist()])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_node_magnitudes_match_the_oracle_state(precision):
+    w = workloads.fmo_trap(K=5, nsteps=300)
+    p = dict(w["params"], scaled=1)
+    with heom.Context(p, precision) as c:
+        c.set_rho0(w["rho0"])
+        c.propagate(1.0, 300, 300)
+        mags = c.node_magnitudes()
+    st = oracle.propagate(p, w["rho0"], 1.0, 300, 300, want_state=True)["state"][:, :7, :7]
+    ref = np.abs(st).reshape(len(st), -1).max(axis=1)[_perm(7, 5)]
+    assert np.abs(mags - ref).max() < (TOL64 if precision == "fp64" else 1e-6)
+
+
+@pytest.fixture(scope="module")
+def pilot():
+    """Filter of the FMO-like depth-5 scaled hierarchy from a 500 fs GPU pilot
+    (magnitudes every 100 fs, FP64), threshold 1e-5."""
+    w = workloads.fmo_trap(K=5, nsteps=400)
+    p = dict(w["params"], scaled=1)
+    mags = None
+    with heom.Context(p, "fp64") as c:
+        c.set_rho0(w["rho0"])
+        for _ in range(5):
+            c.propagate(1.0, 100, 100)
+            m = c.node_magnitudes()
+            mags = m if mags is None else np.maximum(mags, m)
+    keep = heom.filter_select(7, 5, mags, 1e-5)
+    assert 0.2 * len(keep) < keep.sum() < len(keep)  # a real reduction
+    okeep = np.zeros(len(keep), np.uint8)
+    okeep[_perm(7, 5)] = keep
+    o = oracle.propagate(dict(p, keep=okeep), w["rho0"], 1.0, 400, 20, want_state=True)
+    return w, p, keep, o
+
+
+SHAPES = [None, dict(mode=0, team_ctas=4, block_threads=256, node_threads=8),
+          dict(mode=1, team_ctas=1, block_threads=256, node_threads=32), dict(mode=3, block_threads=12 * 28)]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "default" if s is None else "m%d" % s["mode"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_filtered_context_matches_the_filtered_oracle(pilot, precision, shape):
+    w, p, keep, o = pilot
+    with heom.Context(p, precision, keep=keep) as c:
+        assert c.nodes == int(keep.sum())
+        if shape:
+            c.set_launch(**shape)
+        c.set_rho0(w["rho0"])
+        r = c.propagate(1.0, 400, 20)
+        state, _ = c.state()
+    tp, te = (TOL64, TOL64) if precision == "fp64" else (TOL32_POP, TOL32_ETA)
+    assert np.abs(r["pops"] - o["pops"]).max() < tp
+    assert np.abs(r["eta"] - o["eta"]).max() < te
+    kept = np.flatnonzero(keep)
+    ref = o["state"][_perm(7, 5)[kept]][:, :7, :7]
+    assert state.shape == ref.shape
+    assert np.abs(state - ref).max() < (TOL64 if precision == "fp64" else 1e-5)
+
+
+def test_filtered_run_stays_close_to_the_full_hierarchy(pilot):
+    w, p, keep, _ = pilot
+    with heom.Context(p, "fp32", keep=keep) as c:
+        c.set_rho0(w["rho0"])
+        f = c.propagate(1.0, 3000, 30)
+    with heom.Context(p, "fp32") as c:
+        c.set_rho0(w["rho0"])
+        g = c.propagate(1.0, 3000, 30)
+    assert np.abs(f["pops"] - g["pops"]).max() < 1e-4
+    assert np.abs(f["eta"] - g["eta"]).max() < 1e-4
+
+
+def test_filtered_context_rejects_bad_node_sets():
+    w = workloads.fmo_trap(K=3, nsteps=10)
+    M = heom.num_nodes(7, 3)
+    no_root = np.ones(M, np.uint8)
+    no_root[0] = 0
+    with pytest.raises(heom.HeomError) as e:
+        heom.Context(w["params"], "fp32", keep=no_root)
+    assert e.value.code == heom.EINVAL
+    open_set = np.zeros(M, np.uint8)
+    open_set[0] = 1
+    open_set[M - 1] = 1  # a deepest node without its lower neighbours
+    with pytest.raises(heom.HeomError) as e:
+        heom.Context(w["params"], "fp32", keep=open_set)
+    assert e.value.code == heom.EINVAL
+    with pytest.raises(heom.HeomError) as e:
+        heom.Context(dict(w["params"], terminator=1), "fp32", keep=np.ones(M, np.uint8))
+    assert e.value.code == heom.EUNSUPPORTED
