@@ -510,15 +510,16 @@ def main():
             mags = m if mags is None else np.maximum(mags, m)
         pilot.close()
         keep = heom.filter_select(N, K, mags, 1e-5)
-        cf = heom.Context(ps, "fp32", stream=stream, keep=keep)
+        cf = heom.Context(p, "fp32", stream=stream, keep=keep)  # the kept nodes, unscaled
         timed_device(cf, 0, 1)
         pf = timed_device(cf, 2, 0)
         pops_f = d_pops.view(nout, N).cpu().numpy()
         vf = units_per_solve * len(pf) / (sum(pf) * 1e-3)
-        variants["filtered_scaled_hierarchy"] = {
+        variants["filtered_hierarchy"] = {
             "value": vf, "unit": UNIT + " (of the full hierarchy's node count)", "ms_per_solve": statistics.mean(pf),
             "vs_plain_mixed": vf / (value / world), "nodes_kept": int(keep.sum()), "nodes_full": nodes,
-            "threshold": 1e-5, "pilot": "2 ps of the full scaled hierarchy, magnitudes every 250 fs",
+            "threshold": 1e-5, "pilot": "2 ps of the full scaled hierarchy, magnitudes every 250 fs; kept nodes run "
+                                        "unscaled",
             "launch": cf.get_launch(), "max_abs_pop_diff_vs_plain_mixed": float(np.abs(pops_f - pops_gpu).max())}
         cf.close()
         variants["scaled_hierarchy"]["note"] = "same rho as the plain path up to float rounding"
@@ -643,10 +644,42 @@ def bench_large(heom, torch, stream, peak, peak_kind, steps=0):
                      "launch": ctx.get_launch(), "roofline": rl,
                      "pop0_end": float(d_pops.view(nout, N)[-1, 0].item())}
         ctx.close()
+    # the filtered form in mixed precision: a 500 fs pilot of the full scaled hierarchy
+    # (magnitudes every 100 fs), nodes below 1e-5 left out, then the timed 2 ps on the kept nodes
+    pops_full = d_pops.view(nout, N).cpu().numpy()
+    ps = dict(p, scaled=1)
+    pilot = heom.Context(ps, "fp32", stream=stream)
+    pilot.set_rho0(w["rho0"])
+    mags = None
+    for _ in range(5):
+        pilot.propagate(w["dt"], 100, 100)
+        m = pilot.node_magnitudes()
+        mags = m if mags is None else np.maximum(mags, m)
+    pilot.close()
+    keep = heom.filter_select(N, p["K"], mags, 1e-5)
+    cf = heom.Context(p, "fp32", stream=stream, keep=keep)  # the kept nodes, unscaled
+    with torch.cuda.stream(stream):
+        cf.set_rho0_device(rho0)
+        cf.propagate_device(w["dt"], 20, 20)
+        cf.set_rho0_device(rho0)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        cf.propagate_device(w["dt"], w["nsteps"], w["out_every"], d_pops, d_el)
+        f1.record(stream)
+    cf.synchronize()
+    tf = f0.elapsed_time(f1)
+    out["fp32_filtered"] = {
+        "ms_per_solve": tf, "vs_unfiltered_fp32": out["fp32"]["ms_per_solve"] / tf, "nodes_kept": int(keep.sum()),
+        "nodes_full": nodes, "threshold": 1e-5,
+        "pilot": "500 fs of the full scaled hierarchy, magnitudes every 100 fs; kept nodes run unscaled",
+        "launch": cf.get_launch(),
+        "max_abs_pop_diff_vs_unfiltered": float(np.abs(d_pops.view(nout, N).cpu().numpy() - pops_full).max())}
+    cf.close()
     return out
 
 
-def bench_batched(heom, torch, stream, steps=0):
+def bench_batched(heom, torch, stream, steps=0, filter_scan=True):
     """Batched scan: 256 seeded N = 7 trap instances, depth 4..8, lambda and T
     scanned, 5 ps each, mixed precision, one persistent launch."""
     ws = workloads.batched_scan(nsteps=steps) if steps > 0 else workloads.batched_scan()
@@ -695,6 +728,40 @@ def bench_batched(heom, torch, stream, steps=0):
         e64, _ = ctx.efficiency()
         eta_err = max(eta_err, abs(e64 - eta[ids[0]]))
         ctx.close()
+    # the filtered form of the same scan: a 1 ps pilot of every instance's full scaled
+    # hierarchy (magnitudes every 250 fs), nodes below 1e-5 left out, then the timed 5 ps on
+    # the kept nodes; eta against the unfiltered scan
+    filtered = None
+    if filter_scan:
+        pb = heom.Batch([dict(w["params"], scaled=1) for w in ws], "fp32", stream=stream)
+        pb.set_rho0([w["rho0"] for w in ws])
+        mags = [None] * len(ws)
+        for _ in range(4):
+            pb.propagate(1.0, 250, 250)
+            for i in range(len(ws)):
+                m = pb.node_magnitudes(i)
+                mags[i] = m if mags[i] is None else np.maximum(mags[i], m)
+        pb.close()
+        keeps = [heom.filter_select(7, w["params"]["K"], mags[i], 1e-5) for i, w in enumerate(ws)]
+        # the kept auxiliaries are propagated unscaled (the same node set and rho), which runs the
+        # batch's register-view kernels
+        fb = heom.Batch([w["params"] for w in ws], "fp32", stream=stream, keep=keeps)
+        fb.set_rho0([w["rho0"] for w in ws])
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            g0.record(stream)
+            fb.propagate_device(1.0, nsteps, nsteps)
+            g1.record(stream)
+        fb.synchronize()
+        fms = g0.elapsed_time(g1)
+        feta, _ = fb.efficiency()
+        kept = sum(int(k.sum()) for k in keeps)
+        fb.close()
+        filtered = {"solves_per_s": len(ws) / (fms * 1e-3), "ms": fms, "nodes_kept": kept, "nodes_full": nodes,
+                    "vs_unfiltered": ms / fms, "threshold": 1e-5,
+                    "pilot": "1 ps of each full scaled hierarchy, magnitudes every 250 fs; kept nodes run unscaled",
+                    "max_abs_eta_diff_vs_unfiltered": float(np.abs(np.asarray(feta) - np.asarray(eta)).max())}
     solves = len(ws) / (ms * 1e-3)
     plain = len(ws) / (plain_ms * 1e-3)
     peak, peak_kind = peaks()
@@ -705,6 +772,7 @@ def bench_batched(heom, torch, stream, steps=0):
             "ms": ms, "total_nodes": nodes, "eta_mean": float(np.mean(eta)), "launch": launch, "roofline": roof,
             "plain_fp64_solves_per_s": plain, "vs_plain_fp64": solves / plain,
             "plain_fp64_note": "one instance per launch, default shape; one instance of each depth timed",
+            "filtered": filtered,
             "max_abs_eta_diff_vs_fp64": eta_err}
 
 

@@ -329,6 +329,16 @@ void heom_destroy(heom_ctx* ctx);
 int heom_batch_create(const heom_params* params, int32_t count, void* cuda_stream, heom_batch** out);
 int heom_batch_count(const heom_batch* b, int32_t* count);
 
+/* A batch of filtered hierarchies (see heom_create_subset): keep[i] holds the
+ * node flags of instance i over its full hierarchy, or NULL for the full
+ * hierarchy.  heom_batch_num_nodes gives an instance's node count and
+ * heom_batch_node_magnitudes its per-node max |sigma_ab| (as
+ * heom_node_magnitudes; blocking). */
+int heom_batch_create_subset(const heom_params* params, const uint8_t* const* keep, int32_t count, void* cuda_stream,
+                             heom_batch** out);
+int heom_batch_num_nodes(const heom_batch* b, int32_t i, int64_t* out);
+int heom_batch_node_magnitudes(heom_batch* b, int32_t i, double* node_max);
+
 /* rho0_all: the count initial matrices concatenated (sum_i N_i^2 complex). */
 int heom_batch_set_rho0(heom_batch* b, const double* rho0_all);
 

@@ -633,6 +633,7 @@ struct Engine {
   std::map<int, LaunchCfg> cfg;  // per N
   double stop_trace = 0.0;        // the stop rule (0: off)
   const uint8_t* subset_keep = nullptr;  // while a filtered context is created: its node flags
+  const uint8_t* const* subset_keeps = nullptr;  // while a filtered batch is created: per instance (may hold NULL)
   bool pageable_args = false;     // stage launch descriptors from pageable memory (servers)
   std::vector<unsigned char> h_args_pageable;
   // per-instance output destinations and cadences (servers); empty = contiguous buffers
@@ -691,7 +692,10 @@ struct Engine {
     TRY(d_status.alloc(sizeof(int) * 4, hooks));
     TRY(d_gsync.alloc(sizeof(unsigned) * 4, hooks));
     CUDA_TRY(cudaMemsetAsync(d_status.p, 0, sizeof(int) * 4, stream));
-    for (int i = 0; i < count; ++i) TRY(add_instance(params[i]));
+    for (int i = 0; i < count; ++i) {
+      subset_keep = subset_keeps ? subset_keeps[i] : subset_keep;
+      TRY(add_instance(params[i]));
+    }
     for (auto& in : inst)
       if (!cfg.count(in->N)) cfg[in->N] = default_cfg(in->N, count);
     // rho(0) = |0><0| everywhere
@@ -1869,6 +1873,52 @@ int heom_batch_create(const heom_params* params, int32_t count, void* cuda_strea
   auto b = std::make_unique<heom_batch>();
   TRY(b->e.init(params, count, cuda_stream));
   *out = b.release();
+  return HEOM_OK;
+}
+
+int heom_batch_create_subset(const heom_params* params, const uint8_t* const* keep, int32_t count, void* cuda_stream,
+                             heom_batch** out) {
+  if (!out) return fail(HEOM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!keep) return fail(HEOM_EINVAL, "keep is NULL");
+  if (!params || count < 1) return fail(HEOM_EINVAL, "params is NULL or count < 1");
+  for (int i = 0; i < count; ++i)
+    if (keep[i] && params[i].terminator != HEOM_TERM_NONE)
+      return fail(HEOM_EUNSUPPORTED, "params[%d]: a filtered hierarchy takes the plain truncation", i);
+  auto b = std::make_unique<heom_batch>();
+  b->e.subset_keeps = keep;
+  const int rc = b->e.init(params, count, cuda_stream);
+  b->e.subset_keeps = nullptr;
+  b->e.subset_keep = nullptr;
+  TRY(rc);
+  *out = b.release();
+  return HEOM_OK;
+}
+
+int heom_batch_num_nodes(const heom_batch* b, int32_t i, int64_t* out) {
+  if (!b || !out) return fail(HEOM_EINVAL, "batch or out is NULL");
+  if (i < 0 || i >= (int)b->e.inst.size()) return fail(HEOM_EINVAL, "instance %d out of range", i);
+  *out = b->e.inst[i]->M;
+  return HEOM_OK;
+}
+
+int heom_batch_node_magnitudes(heom_batch* b, int32_t i, double* node_max) {
+  if (!b || !node_max) return fail(HEOM_EINVAL, "batch or node_max is NULL");
+  if (i < 0 || i >= (int)b->e.inst.size()) return fail(HEOM_EINVAL, "instance %d out of range", i);
+  Engine& e = b->e;
+  TRY(e.ensure_device());
+  Instance& in = *e.inst[i];
+  const size_t need = sizeof(double) * (size_t)in.M;
+  if (e.d_out.bytes < need) TRY(e.d_out.alloc(need, e.hooks));
+  if (e.prec == HEOM_FP64)
+    node_max_kernel<double><<<launch_blocks(in.M, 256), 256, 0, e.stream>>>(in.y.as<double>(), in.Mpad, in.M, in.N,
+                                                                          e.d_out.as<double>());
+  else
+    node_max_kernel<float><<<launch_blocks(in.M, 256), 256, 0, e.stream>>>(in.y.as<float>(), in.Mpad, in.M, in.N,
+                                                                         e.d_out.as<double>());
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(e.stream));
+  CUDA_TRY(cudaMemcpy(node_max, e.d_out.p, need, cudaMemcpyDeviceToHost));
   return HEOM_OK;
 }
 

@@ -110,6 +110,10 @@ def lib() -> ctypes.CDLL:
             "heom_filter_select": [ctypes.c_int32, ctypes.c_int32, _dp, ctypes.c_double,
                                    ctypes.POINTER(ctypes.c_uint8)],
             "heom_create_subset": [ctypes.POINTER(_Params), ctypes.POINTER(ctypes.c_uint8), vp, ctypes.POINTER(vp)],
+            "heom_batch_create_subset": [ctypes.POINTER(_Params), ctypes.POINTER(ctypes.POINTER(ctypes.c_uint8)),
+                                         ctypes.c_int32, vp, ctypes.POINTER(vp)],
+            "heom_batch_num_nodes": [vp, ctypes.c_int32, _i64p],
+            "heom_batch_node_magnitudes": [vp, ctypes.c_int32, _dp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -390,7 +394,9 @@ class Context:
 class Batch:
     """Many independent hierarchies propagated in persistent launches."""
 
-    def __init__(self, params_list, precision="fp32", stream=None):
+    def __init__(self, params_list, precision="fp32", stream=None, keep=None):
+        """keep: None, or per instance None (full hierarchy) or node flags over its
+        full hierarchy (heom_batch_create_subset)."""
         prec = _precision(precision)
         self._keeps = [_Keep(p, prec) for p in params_list]
         arr = (_Params * len(self._keeps))(*[k.c for k in self._keeps])
@@ -398,8 +404,28 @@ class Batch:
         self.Ns = [int(p["N"]) for p in params_list]
         self.count = len(params_list)
         self._h = ctypes.c_void_p()
-        _check(lib().heom_batch_create(arr, self.count, ctypes.c_void_p(_stream_handle(stream)),
-                                       ctypes.byref(self._h)))
+        if keep is None:
+            _check(lib().heom_batch_create(arr, self.count, ctypes.c_void_p(_stream_handle(stream)),
+                                           ctypes.byref(self._h)))
+        else:
+            self._flags = [None if k is None else np.ascontiguousarray(np.asarray(k, dtype=np.uint8)) for k in keep]
+            ptrs = (ctypes.POINTER(ctypes.c_uint8) * self.count)(
+                *[ctypes.cast(None, ctypes.POINTER(ctypes.c_uint8)) if f is None
+                  else f.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)) for f in self._flags])
+            self._ptrs = ptrs
+            _check(lib().heom_batch_create_subset(arr, ptrs, self.count, ctypes.c_void_p(_stream_handle(stream)),
+                                                  ctypes.byref(self._h)))
+
+    def num_nodes(self, i) -> int:
+        out = ctypes.c_int64()
+        _check(lib().heom_batch_num_nodes(self._h, int(i), ctypes.byref(out)))
+        return int(out.value)
+
+    def node_magnitudes(self, i) -> np.ndarray:
+        """heom_batch_node_magnitudes: max_ab |sigma_n,ab| per node of instance i."""
+        out = np.zeros(self.num_nodes(i))
+        _check(lib().heom_batch_node_magnitudes(self._h, int(i), _ptr(out)))
+        return out
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -115,3 +115,48 @@ def test_filtered_context_rejects_bad_node_sets():
     with pytest.raises(heom.HeomError) as e:
         heom.Context(dict(w["params"], terminator=1), "fp32", keep=np.ones(M, np.uint8))
     assert e.value.code == heom.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_filtered_batch_matches_the_filtered_oracle(pilot, precision):
+    """A batch mixing a filtered instance, the same instance unfiltered and a
+    filtered instance of another size, in the batch's default launch."""
+    w, p, keep, o = pilot
+    w3 = workloads.random_instance(4, 4, seed=31)
+    p3 = dict(w3["params"], scaled=1)
+    M3 = heom.num_nodes(4, 4)
+    keep3 = heom.filter_select(4, 4, np.linspace(1.0, 0.0, M3), 0.5)  # the shallower half, closed downwards
+    with heom.Batch([p, p, p3], precision, keep=[keep, None, keep3]) as b:
+        assert b.num_nodes(0) == int(keep.sum()) and b.num_nodes(1) == heom.num_nodes(7, 5)
+        b.set_rho0([w["rho0"], w["rho0"], w3["rho0"]])
+        res = b.propagate(1.0, 400, 20)
+    tp, te = (TOL64, TOL64) if precision == "fp64" else (TOL32_POP, TOL32_ETA)
+    assert np.abs(res[0]["pops"] - o["pops"]).max() < tp
+    assert np.abs(res[0]["eta"] - o["eta"]).max() < te
+    full = oracle.propagate(p, w["rho0"], 1.0, 400, 20)
+    assert np.abs(res[1]["pops"] - full["pops"]).max() < tp
+    ok3 = np.zeros(M3, np.uint8)
+    ok3[_perm(4, 4)] = keep3
+    o3 = oracle.propagate(dict(p3, keep=ok3), w3["rho0"], 1.0, 400, 20)
+    assert np.abs(res[2]["pops"] - o3["pops"]).max() < tp
+    assert np.abs(res[2]["eta"] - o3["eta"]).max() < te
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_kept_nodes_propagated_unscaled_match_the_oracle(pilot, precision):
+    """The node set chosen from the scaled magnitudes, propagated in the
+    unscaled representation (same auxiliaries, same rho; the batched and
+    large-hierarchy kernels of that form are the fast ones)."""
+    w, p, keep, o_scaled = pilot
+    pu = dict(p, scaled=0)
+    ok = np.zeros(len(keep), np.uint8)
+    ok[_perm(7, 5)] = keep
+    o = oracle.propagate(dict(pu, keep=ok), w["rho0"], 1.0, 400, 20)
+    with heom.Context(pu, precision, keep=keep) as c:
+        c.set_rho0(w["rho0"])
+        r = c.propagate(1.0, 400, 20)
+    tp, te = (TOL64, TOL64) if precision == "fp64" else (TOL32_POP, TOL32_ETA)
+    assert np.abs(r["pops"] - o["pops"]).max() < tp
+    assert np.abs(r["eta"] - o["eta"]).max() < te
+    # the same physics as the scaled filtered run
+    assert np.abs(o["pops"] - o_scaled["pops"]).max() < 1e-12
