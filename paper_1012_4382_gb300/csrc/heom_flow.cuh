@@ -343,8 +343,10 @@ __global__ void __launch_bounds__(kFlowMaxThreads) heom_flow_kernel(FlowArgs A) 
         R re = R(0), im = R(0);
 #pragma unroll
         for (int i = 0; i < NRE; ++i) re += cre[i] * sin[(ire4[i / 4] >> (8 * (i % 4))) & 0xFF];
+        if (pair) {  // a diagonal has no imaginary part; its units fill the last warps of a CTA
 #pragma unroll
-        for (int i = 0; i < NIM; ++i) im += cim[i] * sin[(iim4[i / 4] >> (8 * (i % 4))) & 0xFF];
+          for (int i = 0; i < NIM; ++i) im += cim[i] * sin[(iim4[i / 4] >> (8 * (i % 4))) & 0xFF];
+        }
         FlowWord<R> gr[4], gi[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)

@@ -742,13 +742,17 @@ struct Engine {
       return c;
     }
     if (count == 1) {
-      // one hierarchy of 256 nodes or more: the dataflow engine (mode 3) with one CTA
-      // per SM, S = ceil(M / SMs) nodes each (measured best on the FMO-like N = 7,
-      // depth 6 workload: S = 12, 1.2-1.4 us per RK4 stage in mixed precision), when
-      // all its CTAs fit on the GPU at once
+      // one hierarchy of 256 nodes or more: the dataflow engine (mode 3), when all its
+      // CTAs fit on the GPU at once.  Nodes per CTA, measured on the FMO-like N = 7,
+      // depth 6 hierarchy and a filtered version of it (1225 nodes): in mixed precision
+      // CTAs of about 336 threads (12 nodes at N = 7: 1.25 us per stage for both, 1.45-2.3
+      // with 5-11 or 13 nodes); in FP64, bound by the FP64 pipe, the nodes spread evenly
+      // over all SMs, S = ceil(M / SMs)
       if (Mmax >= 256) {
         const int U = N * (N + 1) / 2;
-        const int S = (int)std::min<int64_t>(heom::kFlowMaxThreads / U, (Mmax + sms - 1) / sms);
+        const int64_t even = (Mmax + sms - 1) / sms;
+        const int S = (int)std::min<int64_t>(heom::kFlowMaxThreads / U,
+                                             prec == HEOM_FP64 ? even : std::max<int64_t>(336 / U, even));
         const void* k = heom::flow_kernel(prec == HEOM_FP64, false, N);
         int per_sm = 0;
         if (S >= 1 && k &&
