@@ -186,11 +186,22 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) heom_large_kernel
             int ab = 0, rem = bk;
             while (rem >= NB - ab) { rem -= NB - ab; ++ab; }
             const int A0 = 4 * ab + 2 * half, B0 = 4 * (ab + rem);
+            // A diagonal block (the same for the whole warp) keeps only its 10 entries
+            // with b >= a: in FP64, whose pipe bounds this kernel, the two lanes of a
+            // node take rows {0, 3} and {1, 2} of it, five entries each, instead of rows
+            // {0, 1} and {2, 3} with eight products each (about 11 % of the product work
+            // of a 24-site node); FP32 is bound by the neighbour gathers and keeps the
+            // plain blocks
+            const bool dblk = sizeof(R) == 8 && rem == 0;
+            const int ra0 = dblk ? 4 * ab + half : A0, ra1 = dblk ? 4 * ab + 3 - half : A0 + 1;
             R re[2][4], im[2][4];
+            R rd[5], id[5];
 #pragma unroll
             for (int i = 0; i < 2; ++i)
 #pragma unroll
               for (int j = 0; j < 4; ++j) re[i][j] = im[i][j] = R(0);
+#pragma unroll
+            for (int e = 0; e < 5; ++e) rd[e] = id[e] = R(0);
             // -i[H, sigma] with the real part J (symmetric) and imaginary part Ji (antisymmetric) of H:
             //   Re += sum_k J(a,k) A(k,b) - A(a,k) J(k,b);  Im -= sum_k J(a,k) S(k,b) - S(a,k) J(k,b)
             //   Re += sum_k Ji(a,k) S(k,b) - S(a,k) Ji(k,b); Im += sum_k Ji(a,k) A(k,b) - A(a,k) Ji(k,b)
@@ -198,19 +209,55 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) heom_large_kernel
 #pragma unroll 2
             for (int k = 0; k < N; ++k) {
               R ja[2], jb[4];
-              ja[0] = cf[L::J(N) + k * JS + A0];
-              ja[1] = cf[L::J(N) + k * JS + A0 + 1];
+              ja[0] = cf[L::J(N) + k * JS + ra0];
+              ja[1] = cf[L::J(N) + k * JS + ra1];
               load_row<4>(cf + L::J(N) + k * JS + B0, jb);
               R sak[2], aak[2], skb[4], akb[4];
 #pragma unroll
               for (int i = 0; i < 2; ++i) {
-                sak[i] = Re_(A0 + i, k);
-                aak[i] = Im_(A0 + i, k);
+                sak[i] = Re_(i ? ra1 : ra0, k);
+                aak[i] = Im_(i ? ra1 : ra0, k);
               }
 #pragma unroll
               for (int j = 0; j < 4; ++j) {
                 skb[j] = Re_(B0 + j, k);    // S(k, b) = S(b, k)
                 akb[j] = -Im_(B0 + j, k);   // A(k, b) = -A(b, k)
+              }
+              if (dblk) {
+                // the five entries (row r, column c) of this lane, picked by selects:
+                // half 0: (0,0) (0,1) (0,2) (0,3) (1,3); half 1: (0,1) (0,2) (0,3) (1,2) (1,3)
+                const bool hf = half != 0;
+                const R J0[5] = {ja[0], ja[0], ja[0], hf ? ja[1] : ja[0], ja[1]};
+                const R S0[5] = {sak[0], sak[0], sak[0], hf ? sak[1] : sak[0], sak[1]};
+                const R A0v[5] = {aak[0], aak[0], aak[0], hf ? aak[1] : aak[0], aak[1]};
+                const R JB[5] = {hf ? jb[1] : jb[0], hf ? jb[2] : jb[1], hf ? jb[3] : jb[2], hf ? jb[2] : jb[3], jb[3]};
+                const R SB[5] = {hf ? skb[1] : skb[0], hf ? skb[2] : skb[1], hf ? skb[3] : skb[2], hf ? skb[2] : skb[3],
+                                 skb[3]};
+                const R AB[5] = {hf ? akb[1] : akb[0], hf ? akb[2] : akb[1], hf ? akb[3] : akb[2], hf ? akb[2] : akb[3],
+                                 akb[3]};
+#pragma unroll
+                for (int e = 0; e < 5; ++e) {
+                  rd[e] = fma(J0[e], AB[e], rd[e]);
+                  rd[e] = fma(-A0v[e], JB[e], rd[e]);
+                  id[e] = fma(-J0[e], SB[e], id[e]);
+                  id[e] = fma(S0[e], JB[e], id[e]);
+                }
+                if constexpr (CPLX) {
+                  R ia[2], ib[4];
+                  ia[0] = cf[L::Ji(N) + k * JS + ra0];
+                  ia[1] = cf[L::Ji(N) + k * JS + ra1];
+                  load_row<4>(cf + L::Ji(N) + k * JS + B0, ib);
+                  const R I0[5] = {ia[0], ia[0], ia[0], hf ? ia[1] : ia[0], ia[1]};
+                  const R IB[5] = {hf ? ib[1] : ib[0], hf ? ib[2] : ib[1], hf ? ib[3] : ib[2], hf ? ib[2] : ib[3], ib[3]};
+#pragma unroll
+                  for (int e = 0; e < 5; ++e) {
+                    rd[e] = fma(-I0[e], SB[e], rd[e]);
+                    rd[e] = fma(-S0[e], IB[e], rd[e]);
+                    id[e] = fma(-I0[e], AB[e], id[e]);
+                    id[e] = fma(-A0v[e], IB[e], id[e]);
+                  }
+                }
+                continue;
               }
               // explicit multiply-add chains: two FMAs per output and term (written as
               // x += a*b - c*d the compiler keeps a separate multiply and add, 1.5x the
@@ -226,8 +273,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) heom_large_kernel
                 }
               if constexpr (CPLX) {
                 R ia[2], ib[4];  // row k of Ji: Ji(k, a) = -Ji(a, k)
-                ia[0] = cf[L::Ji(N) + k * JS + A0];
-                ia[1] = cf[L::Ji(N) + k * JS + A0 + 1];
+                ia[0] = cf[L::Ji(N) + k * JS + ra0];
+                ia[1] = cf[L::Ji(N) + k * JS + ra1];
                 load_row<4>(cf + L::Ji(N) + k * JS + B0, ib);
 #pragma unroll
                 for (int i = 0; i < 2; ++i)
@@ -240,11 +287,28 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) heom_large_kernel
                   }
               }
             }
+            if (dblk) {
+              // the five entries into their places of the 2 x 4 block (rows ra0, ra1); the
+              // places not set hold entries with b < a, which the epilogue drops
+              const bool hf = half != 0;
+              re[0][0] = rd[0];
+              im[0][0] = id[0];
+              re[0][1] = hf ? rd[0] : rd[1];
+              im[0][1] = hf ? id[0] : id[1];
+              re[0][2] = hf ? rd[1] : rd[2];
+              im[0][2] = hf ? id[1] : id[2];
+              re[0][3] = hf ? rd[2] : rd[3];
+              im[0][3] = hf ? id[2] : id[3];
+              re[1][2] = rd[3];
+              im[1][2] = id[3];
+              re[1][3] = rd[4];
+              im[1][3] = id[4];
+            }
             // links of the block's rows and columns
             int ua[2], ub[4], da[2], db[4];
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
-              const int a = A0 + q;
+              const int a = q ? ra1 : ra0;
               ua[q] = a < N ? I.up[a * Mp + n] : -1;
               da[q] = a < N ? I.dn[a * Mp + n] : -1;
             }
@@ -263,7 +327,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) heom_large_kernel
             if (term) {
 #pragma unroll
               for (int q = 0; q < 2; ++q) {
-                const int a = min(A0 + q, N - 1);
+                const int a = min(q ? ra1 : ra0, N - 1);
                 tca[q] = ((da[q] < 0 ? R(0) : R(da[q] >> 24)) + R(1)) / (ng + cf[L::gam(N) + a]);
               }
 #pragma unroll
@@ -279,7 +343,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) heom_large_kernel
             for (int ij = 0; ij < 4; ++ij) {
               const int i = ij >> 1, j0 = 2 * (ij & 1);
               R yr[4], yim[4];
-              const int a = A0 + i;
+              const int a = i ? ra1 : ra0;
               const int ac = a < N ? a : N - 1;  // clamped for addressing; outputs with a >= N are dropped
               const R* sa = cf + L::site(N) + 4 * ac;
               const R eps_a = sa[0], gh_a = sa[1], al_a = sa[2], be_a = sa[3];
