@@ -5,6 +5,7 @@
 // persistent engine launches and the small utility kernels that move rho and
 // the full state in and out.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -32,6 +33,18 @@ using heom::EngineArgs;
 using heom::Inst;
 
 namespace {
+
+// ------------------------------------------------------------------ ranges
+//
+// NVTX ranges (header-only NVTX v3: no-ops unless a profiler is attached)
+// around the library's host calls that queue device work, so that a timeline
+// shows which call a launch belongs to.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ------------------------------------------------------------------ errors
 
@@ -973,6 +986,7 @@ struct Engine {
   static int64_t nout_of(int64_t nsteps, int64_t out_every) { return nsteps / out_every + 1; }
 
   int propagate(const double* dt, const int64_t* nsteps, int64_t out_every, double* d_pops, double* d_el) {
+    NvtxRange range("heom propagate");
     TRY(ensure_device());
     if (out_every < 1) return fail(HEOM_EINVAL, "out_every must be >= 1");
     const int count = (int)inst.size();
@@ -1209,6 +1223,7 @@ struct Engine {
   // The dataflow engine (mode 3) on one instance: the unit table and the
   // tagged stage buffers on first use, the tag base, one cooperative launch.
   int launch_flow(Instance& in, const LaunchCfg& c, const Inst* d_inst, int* d_status, int64_t nsteps) {
+    NvtxRange range("heom dataflow launch");
     const int N = in.N, U = N * (N + 1) / 2, NN = N * N;
     const bool fp64 = prec == HEOM_FP64;
     const void* k = heom::flow_kernel(fp64, in.complex_h != 0, N);
@@ -1321,6 +1336,7 @@ struct Engine {
   }
 
   int launch(int N, int cplx, int sc, const LaunchCfg& c, int nteams, EngineArgs& A, int B = 0, int dyn = 0) {
+    NvtxRange range(c.mode == 1 ? "heom grid launch" : "heom cluster launch");
     const void* k = kernel_for(N, cplx, sc, c);
     if (!k)
       return fail(HEOM_EUNSUPPORTED, "no engine kernel for N=%d, launch mode %d, node_threads %d%s", N, c.mode, c.G,
@@ -1766,6 +1782,7 @@ int heom_get_launch(const heom_ctx* ctx, int32_t* mode, int32_t* team_ctas, int3
 }
 
 int heom_autotune(heom_ctx* ctx, int64_t trial_steps, double* best_us_per_step) {
+  NvtxRange range("heom autotune");
   if (!ctx) return fail(HEOM_EINVAL, "ctx is NULL");
   if (trial_steps < 1) return fail(HEOM_EINVAL, "trial_steps must be >= 1");
   Engine& e = ctx->e;
@@ -2622,6 +2639,7 @@ struct heom_server {
   }
 
   int progress(int32_t* completed) {
+    NvtxRange range("heom server progress");
     int done = 0;
     // requests whose block has finished
     for (auto& L : launches) {
