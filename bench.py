@@ -57,8 +57,8 @@ def parse():
     ap.add_argument("--no-large", action="store_true", help="skip the 24-site large-hierarchy measurement")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the scaled-hierarchy and low-temperature variants of the headline workload")
-    ap.add_argument("--serving-requests", type=int, default=400,
-                    help="requests replayed from the serving trace (the full trace has 2000)")
+    ap.add_argument("--serving-requests", type=int, default=2000,
+                    help="requests replayed from the serving trace (default: the full trace, 2000)")
     ap.add_argument("--cpu-sample-steps", type=int, default=0, help="RK4 steps of the oracle sample (0: auto)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline (profiling runs)")
     ap.add_argument("--autotune", action="store_true",
@@ -776,7 +776,8 @@ def bench_batched(heom, torch, stream, steps=0, filter_scan=True):
             "max_abs_eta_diff_vs_fp64": eta_err}
 
 
-SERVING_LOW_RATE = 12.0  # req/s, about half the measured capacity of the mix
+SERVING_LOW_RATE = 12.0  # req/s, about a quarter of the measured capacity of the mix
+SERVING_CAPACITY_RATE = 40.0  # req/s, just below the measured capacity (about 42 req/s)
 
 
 def bench_serving(count):
@@ -786,14 +787,17 @@ def bench_serving(count):
     from paper_1012_4382_gb300 import serving
     tr = workloads.serving_trace(count=count)
     r = serving.run_trace(tr, "fp32", device_bytes=16 << 30, streams=32, time_limit_s=120.0)
-    r["workload"] = ("Poisson 200 req/s, N~U{2..8}, K~U{3..8}, 1-20 ps at 1 fs, fp32 mixed; first %d requests "
-                     "of the seeded trace" % count)
-    # the same request mix below saturation: the latency of a request that does not queue
-    low = workloads.serving_trace(count=max(1, count // 2), rate_per_s=SERVING_LOW_RATE)
-    r2 = serving.run_trace(low, "fp32", device_bytes=16 << 30, streams=32, time_limit_s=120.0)
-    r["below_saturation"] = {k: r2[k] for k in ("requests", "completed", "offered_req_per_s", "achieved_req_per_s",
-                                                "p50_latency_s", "p99_latency_s", "mean_latency_s", "max_concurrent")}
-    r["below_saturation"]["workload"] = "the same mix at Poisson %g req/s" % SERVING_LOW_RATE
+    r["workload"] = ("Poisson 200 req/s, N~U{2..8}, K~U{3..8}, 1-20 ps at 1 fs, fp32 mixed; %s" %
+                     ("the full seeded trace" if count == 2000 else "first %d requests of the seeded trace" % count))
+    keys = ("requests", "completed", "offered_req_per_s", "achieved_req_per_s", "node_rhs_per_s", "p50_latency_s",
+            "p99_latency_s", "mean_latency_s", "wall_s", "max_concurrent")
+    # the same mix offered at about the capacity, and well below it (the
+    # latency of a request that does not queue)
+    for name, n, rate in (("at_capacity", 400, SERVING_CAPACITY_RATE), ("below_saturation", 200, SERVING_LOW_RATE)):
+        tr2 = workloads.serving_trace(count=min(n, count), rate_per_s=rate)
+        r2 = serving.run_trace(tr2, "fp32", device_bytes=16 << 30, streams=32, time_limit_s=120.0)
+        r[name] = {k: r2[k] for k in keys}
+        r[name]["workload"] = "the same mix at Poisson %g req/s, %d requests" % (rate, min(n, count))
     return r
 
 

@@ -413,7 +413,10 @@ void heom_graph_destroy(heom_graph* g);
  *   - retires launches whose device work has ended, returning their memory
  *     and stream, and
  *   - admits the queued requests that fit in the budget, in arrival order,
- *     into one new launch on a free stream: one thread block per request.
+ *     into new launches on free streams, one per (precision, N, team shape):
+ *     one team of thread blocks per request.  A request whose launch would
+ *     need a stream when none is free keeps its place; later requests that
+ *     join a launch formed in the same call go ahead of it.
  * So requests that arrive while others run start at the next progress call
  * and overlap with them on the device, and each completes as soon as its own
  * block is done.  Node tables are cached per (N, K).  Calls are serialised by

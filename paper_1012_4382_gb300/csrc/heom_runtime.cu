@@ -2408,8 +2408,10 @@ extern "C" int heom_propagate_static(const heom_params* params, const double* d_
 //   * retires every launch whose device work has ended (its device memory goes
 //     back to the budget, its stream is free), and
 //   * admits the queued requests, in arrival order, that fit in the budget into
-//     one new launch on a free stream: one thread block per request, all of them
-//     running concurrently with each other and with earlier launches.
+//     new launches on free streams, one per (precision, N, team shape): one
+//     team of CTAs per request, all of them running concurrently with each
+//     other and with earlier launches (a launch larger than the GPU holds runs
+//     its requests in turn inside the launch).
 // So requests that arrive while others run are admitted at the next progress
 // call and overlap with them on the device; each request completes on its own
 // as soon as its block finishes.  Node tables are cached per (N, K).
@@ -2490,6 +2492,7 @@ struct Request {
   size_t need = 0;
   unsigned char* host = nullptr;  // pinned: pops [nout*N], (eta, loss) [nout*2], done flag
   int launch = -1;                // index of the launch running it
+  LaunchCfg cfg;                  // launch shape, chosen at admission
   bool released = false;          // released by the caller while its launch still runs
   std::vector<double> pops, el;
   double t_submit = 0, t_start = 0, t_done = 0;
@@ -2560,7 +2563,10 @@ struct heom_server {
     while (c < 16 && (int64_t)c * 256 < M) c <<= 1;
     return c;
   }
-  // Scaled hierarchies (N <= 8) take a load view in device memory.
+  // Launch shape of a request.  Scaled hierarchies (N <= 8) take a load view
+  // in device memory.  (Smaller teams -- 2 CTAs, or the fewest whose shared
+  // memory holds the hierarchy -- were measured slower on the serving trace:
+  // the largest requests' service time then sets the makespan.)
   static LaunchCfg launch_for(int prec, int N, int64_t M, int max_dyn, bool scaled) {
     LaunchCfg c;
     c.mode = 0;
@@ -2590,9 +2596,8 @@ struct heom_server {
     for (int64_t id : ids) ps.push_back(reqs[id]->p);
     int rc = eng->init(ps.data(), (int)ps.size(), L.s, &hooks, tables);
     if (rc != HEOM_OK) return rc;
-    int64_t Mmax = 0;
-    for (auto& in : eng->inst) Mmax = std::max<int64_t>(Mmax, in->M);
-    for (auto& in : eng->inst) eng->cfg[in->N] = launch_for(eng->prec, in->N, Mmax, max_dyn_smem(), in->scaled != 0);
+    // every request of a launch has the same shape (the group key holds it)
+    for (auto& in : eng->inst) eng->cfg[in->N] = reqs[ids[0]]->cfg;
     std::vector<double> dts;
     std::vector<int64_t> steps;
     for (size_t k = 0; k < ids.size(); ++k) {
@@ -2685,12 +2690,19 @@ struct heom_server {
     }
     // admit queued requests, in arrival order, while they fit in the budget;
     // each launch holds requests of one precision, site count and team shape
-    // and takes one free stream
+    // and takes one free stream.  A request whose group would need a stream
+    // when none is left keeps its place in the queue, and later requests that
+    // join a group already formed go ahead of it (it gets the next free stream).
     std::vector<int> free_streams;
     for (size_t k = 0; k < launches.size(); ++k)
       if (!launches[k].busy) free_streams.push_back((int)k);
     std::map<std::tuple<int, int, int, int, int>, std::vector<int64_t>> groups;
     std::vector<std::tuple<int, int, int, int, int>> order;
+    std::deque<int64_t> skipped;
+    if (free_streams.empty()) {
+      if (completed) *completed = done;
+      return HEOM_OK;
+    }
     size_t budget = arena.in_use;
     std::set<std::pair<int, int>> new_tables;
     const int max_dyn = max_dyn_smem();
@@ -2705,16 +2717,22 @@ struct heom_server {
       const LaunchCfg c = launch_for(q.p.precision, q.p.N, M, max_dyn, sc);
       const auto gkey = std::make_tuple(q.p.precision, q.p.N, c.team_ctas, c.mode, (int)sc);
       if (!groups.count(gkey)) {
-        if (groups.size() == free_streams.size()) break;  // no stream for a new group
+        if (groups.size() == free_streams.size()) {  // no stream for a new group
+          skipped.push_back(q.id);
+          queue.pop_front();
+          continue;
+        }
         order.push_back(gkey);
       }
       q.host = static_cast<unsigned char*>(harena.alloc(q.host_bytes()));
       if (!q.host) break;
+      q.cfg = c;
       budget += need;
       new_tables.insert(tkey);
       groups[gkey].push_back(q.id);
       queue.pop_front();
     }
+    for (auto it = skipped.rbegin(); it != skipped.rend(); ++it) queue.push_front(*it);
     for (size_t g = 0; g < order.size(); ++g) {
       const int li = free_streams[g];
       std::vector<int64_t>& ids = groups[order[g]];

@@ -67,6 +67,25 @@ def test_results_alone_equal_results_in_the_mix(precision):
         assert np.abs(r["eta"] - o["eta"]).max() < tol[1]
 
 
+def test_admission_does_not_block_on_a_busy_stream():
+    """One stream: the first progress call launches the head request's group
+    and every later request that joins it; a request of another site count
+    keeps its place and starts on the next free stream."""
+    small = workloads.random_instance(3, 3, seed=71)
+    other = workloads.random_instance(5, 3, seed=72)
+    with serving.Server(device_bytes=1 << 30, streams=1) as srv:
+        a = srv.submit(small["params"], small["rho0"], 1.0, 400, 100)
+        b = srv.submit(other["params"], other["rho0"], 1.0, 400, 100)
+        c = srv.submit(small["params"], small["rho0"], 1.0, 400, 100)
+        srv.progress()
+        assert srv.status(b) == serving.QUEUED
+        assert srv.status(a) != serving.QUEUED and srv.status(c) != serving.QUEUED
+        _drain(srv, [a, b, c])
+        assert all(srv.status(i) == serving.DONE for i in (a, b, c))
+        ra, rc = srv.result(a), srv.result(c)
+        assert np.array_equal(ra["pops"], rc["pops"])
+
+
 def test_admission_waits_for_memory():
     reqs = _requests()[:6]
     need = max(heom.num_nodes(w["params"]["N"], w["params"]["K"]) for w in reqs)
