@@ -67,6 +67,8 @@ extern "C" {
                                every output row and at the end of each propagate call): the run diverged,
                                e.g. a time step too large for the bath rates, or the initial state was not
                                finite; the call's results are not usable */
+#define HEOM_EINTERNAL 7    /* an internal consistency check failed (the library's own node tables did not
+                               pass heom_check_node_tables' test after upload); message says where */
 
 /* precision of the propagation */
 #define HEOM_FP64 0         /* every array and every operation in double precision */
@@ -135,6 +137,23 @@ int heom_num_nodes(int32_t N, int32_t K, int64_t* out);
  *   down[i*N + j]  = index of n - e_j, or -1 when n_j = 0.
  * Each output may be NULL.  Arrays hold nodes*N int32 values. */
 int heom_build_index(int32_t N, int32_t K, int32_t* multi, int32_t* up, int32_t* down);
+
+/* Device-side bounds and consistency check of node tables in the layout the
+ * kernels read (App. B: sigma_n couples to sigma_{n+e_j} and sigma_{n-e_j}):
+ * d_up and d_dn are DEVICE int32 arrays [N][Mpad], element (j, n) at
+ * j*Mpad + n; d_up holds the index of n + e_j or -1, d_dn holds
+ * (n_j << 24) | index of n - e_j, or -1 when n_j = 0.  The test, per node
+ * n < M and site j: an up link is -1 or a later node u < M whose down link on
+ * site j is n with n_j(u) = n_j(n) + 1; a down link is -1 or an earlier node
+ * with n_j >= 1 whose up link on site j is n; nodes M..Mpad-1 have no links.
+ * A linked entry is read only after its index is found in range, so corrupt
+ * tables are read in bounds.  Every context, batch and server runs this test
+ * on the tables it uploads (full or filtered) and fails with HEOM_EINTERNAL if
+ * they do not pass.  Returns HEOM_OK, or HEOM_EINVAL with *bad_node (may be
+ * NULL) = the smallest offending node (-1 when the tables pass).  Blocking, on
+ * the legacy default stream; the arrays are only read. */
+int heom_check_node_tables(const int32_t* d_up, const int32_t* d_dn, int64_t M, int32_t Mpad, int32_t N,
+                           int64_t* bad_node);
 
 /* Device memory hooks.  When set, every device allocation of the library goes
  * through alloc/release (e.g. a framework's caching allocator); otherwise

@@ -15,6 +15,7 @@
 #include <deque>
 #include <cstdarg>
 #include <cstdio>
+#include <climits>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -259,6 +260,58 @@ __global__ void node_max_kernel(const R* y, int Mpad, int64_t M, int N, double* 
     }
   }
   out[n] = mx;
+}
+
+// Device-side bounds and consistency check of a node table pair ([N][Mpad]
+// int32, element-major like the state; dn packs n_j in its top byte), run on
+// the tables every kernel will read, before any propagation reads them.  For
+// node n < M and site j: an up link is -1 or a later node u < M whose down
+// link on site j is n with n_j(u) = n_j(n) + 1; a down link is -1 or an
+// earlier node d with n_j >= 1 whose up link on site j is n; padding nodes
+// (M <= n < Mpad) have no links.  A neighbour's entry is read only after its
+// index has been found in range.  bad[0] receives the smallest offending node.
+__global__ void table_check_kernel(const int32_t* up, const int32_t* dn, int M, int Mpad, int N, int* bad) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)N * Mpad) return;
+  const int j = (int)(t / Mpad), n = (int)(t - (int64_t)j * Mpad);
+  const int32_t u = up[t], d = dn[t];
+  bool ok;
+  if (n >= M) {
+    ok = u == -1 && d == -1;
+  } else {
+    ok = d == -1 || (d >= 0 && (d >> 24) >= 1 && (d & 0xFFFFFF) < n);
+    const int nj = d >= 0 ? (d >> 24) : 0;
+    if (ok && d >= 0) ok = up[(int64_t)j * Mpad + (d & 0xFFFFFF)] == n;
+    if (ok && u != -1) {
+      ok = u > n && u < M;
+      if (ok) {
+        const int32_t back = dn[(int64_t)j * Mpad + u];
+        ok = back >= 0 && (back & 0xFFFFFF) == n && (back >> 24) == nj + 1;
+      }
+    }
+  }
+  if (!ok) atomicMin(bad, n);
+}
+
+// Runs table_check_kernel on device tables; HEOM_OK, or `code` naming the
+// first offending node (bad_node may be NULL).
+int check_node_tables(const int32_t* up, const int32_t* dn, int64_t M, int Mpad, int N, cudaStream_t stream,
+                      const Hooks& hooks, int code, int64_t* bad_node) {
+  DevBuf flag;
+  TRY(flag.alloc(sizeof(int), hooks));
+  const int none = INT_MAX;
+  CUDA_TRY(cudaMemcpyAsync(flag.p, &none, sizeof(int), cudaMemcpyHostToDevice, stream));
+  const int64_t work = (int64_t)N * Mpad;
+  if (work > 0)
+    table_check_kernel<<<launch_blocks(work, 256), 256, 0, stream>>>(up, dn, (int)M, Mpad, N, flag.as<int>());
+  CUDA_TRY(cudaGetLastError());
+  int bad = none;
+  CUDA_TRY(cudaMemcpyAsync(&bad, flag.p, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  if (bad_node) *bad_node = bad == none ? -1 : bad;
+  if (bad != none)
+    return fail(code, "node tables (N=%d, %lld nodes) failed the device check at node %d", N, (long long)M, bad);
+  return HEOM_OK;
 }
 
 // --------------------------------------------------------------- structures
@@ -866,7 +919,8 @@ struct Engine {
       TRY(t->dn.alloc(dn.size() * 4, hooks));
       CUDA_TRY(cudaMemcpyAsync(t->up.p, up.data(), up.size() * 4, cudaMemcpyHostToDevice, stream));
       CUDA_TRY(cudaMemcpyAsync(t->dn.p, dn.data(), dn.size() * 4, cudaMemcpyHostToDevice, stream));
-      CUDA_TRY(cudaStreamSynchronize(stream));
+      TRY(check_node_tables(t->up.as<int32_t>(), t->dn.as<int32_t>(), t->M, t->Mpad, p.N, stream, hooks,
+                            HEOM_EINTERNAL, nullptr));
       (*tables)[key] = t;
       in->tab = t;
     } else {
@@ -949,8 +1003,8 @@ struct Engine {
     TRY(t.dn.alloc(dn.size() * 4, hooks));
     CUDA_TRY(cudaMemcpyAsync(t.up.p, up.data(), up.size() * 4, cudaMemcpyHostToDevice, stream));
     CUDA_TRY(cudaMemcpyAsync(t.dn.p, dn.data(), dn.size() * 4, cudaMemcpyHostToDevice, stream));
-    CUDA_TRY(cudaStreamSynchronize(stream));
-    return HEOM_OK;
+    return check_node_tables(t.up.as<int32_t>(), t.dn.as<int32_t>(), t.M, t.Mpad, N, stream, hooks, HEOM_EINTERNAL,
+                             nullptr);
   }
 
   // root buffer `which` (0: y0, 1: wa0, 2: wb0) of the mixed path, N*N float2
@@ -1638,6 +1692,16 @@ int heom_node_magnitudes(heom_ctx* ctx, double* node_max) {
   CUDA_TRY(cudaStreamSynchronize(e.stream));
   CUDA_TRY(cudaMemcpy(node_max, e.d_out.p, need, cudaMemcpyDeviceToHost));
   return HEOM_OK;
+}
+
+int heom_check_node_tables(const int32_t* d_up, const int32_t* d_dn, int64_t M, int32_t Mpad, int32_t N,
+                           int64_t* bad_node) {
+  if (bad_node) *bad_node = -1;
+  if (!d_up || !d_dn) return fail(HEOM_EINVAL, "d_up or d_dn is NULL");
+  if (N < 1 || N > HEOM_MAX_SITES) return fail(HEOM_EINVAL, "N must be 1..%d", HEOM_MAX_SITES);
+  if (M < 1 || Mpad < M || M > HEOM_MAX_NODES)
+    return fail(HEOM_EINVAL, "need 1 <= M <= Mpad and M <= %d", HEOM_MAX_NODES);
+  return check_node_tables(d_up, d_dn, M, Mpad, N, 0, Hooks(), HEOM_EINVAL, bad_node);
 }
 
 int heom_filter_select(int32_t N, int32_t K, const double* node_max, double delta, uint8_t* keep) {

@@ -19,7 +19,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libheom.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ENONFINITE = 0, 1, 2, 3, 4, 5, 6
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ENONFINITE, EINTERNAL = 0, 1, 2, 3, 4, 5, 6, 7
 FP64, FP32_MIXED = 0, 1
 FLAG_LOW_TEMP = 1  # heom_params.flags: low-temperature correction
 FLAG_SCALED = 2  # heom_params.flags: scaled hierarchy (auxiliaries divided by prod_j sqrt(n_j! s_j^n_j))
@@ -74,6 +74,8 @@ def lib() -> ctypes.CDLL:
         sig = {
             "heom_num_nodes": [ctypes.c_int32, ctypes.c_int32, _i64p],
             "heom_build_index": [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p],
+            "heom_check_node_tables": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)],
             "heom_set_allocator": [ALLOC_FN, FREE_FN, vp],
             "heom_create": [ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)],
             "heom_set_rho0": [vp, _dp],
@@ -230,6 +232,34 @@ def build_index(N: int, K: int):
     p = lambda a: a.ctypes.data_as(_i32p)
     _check(lib().heom_build_index(int(N), int(K), p(multi), p(up), p(down)))
     return multi, up, down
+
+
+def device_tables(N: int, K: int):
+    """(up, dn, Mpad) in the device layout the kernels read, as host arrays
+    [N][Mpad]: up = index of n + e_j or -1, dn = (n_j << 24) | index of n - e_j
+    or -1."""
+    multi, up, down = build_index(N, K)
+    M = len(multi)
+    Mpad = (M + 31) // 32 * 32
+    u = np.full((N, Mpad), -1, np.int32)
+    d = np.full((N, Mpad), -1, np.int32)
+    u[:, :M] = up.T
+    d[:, :M] = np.where(down.T >= 0, (multi.T.astype(np.int64) << 24) | down.T, -1).astype(np.int32)
+    return u, d, Mpad
+
+
+def check_node_tables(d_up, d_dn, M: int, Mpad: int, N: int) -> int:
+    """Runs the device-side table check (heom_check_node_tables) on DEVICE
+    int32 tensors [N][Mpad]; returns -1 when they pass, raises HeomError
+    (EINVAL) naming the first offending node otherwise."""
+    bad = ctypes.c_int64(-1)
+    rc = lib().heom_check_node_tables(ctypes.c_void_p(d_up.data_ptr()), ctypes.c_void_p(d_dn.data_ptr()), int(M),
+                                      int(Mpad), int(N), ctypes.byref(bad))
+    if rc != OK:
+        err = HeomError(rc, lib().heom_last_error().decode(errors="replace"))
+        err.bad_node = bad.value
+        raise err
+    return bad.value
 
 
 _hooks = None
