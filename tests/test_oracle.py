@@ -153,6 +153,46 @@ def test_markov_terminator_reduces_truncation_error():
         assert errs[1] < errs[0] / 2
 
 
+@pytest.mark.parametrize("K", [0, 1, 2, 3, 4])
+def test_markov_terminator_keeps_the_exact_long_time_rate(K):
+    """One bath (on site 1) and two uncoupled sites: the (1,2) elements form
+    the chain x_n' = -n g x_n + i x_{n+1} + n c x_{n-1}, c = i a + b, whose
+    infinite-depth solution decays at long times with the Markov rate
+    lambda = i c / g (the t/g term of f(t) in the closed form above).  The
+    vector x_n = (c/g)^n is an exact eigenvector of the infinite chain for
+    that rate, and at the last level the terminator's
+    (n_1 + 1) c x_n / (n_1 g + g) equals its next entry, so a chain cut at any
+    depth K with the terminator keeps the exact rate; without it the rate is
+    off by about (|c|/g^2)^(K+1) g.  Checked on x_0(t2)/x_0(t1) at times where
+    the faster modes (rates near -g, -2g, ...) have died out, against the RK4
+    amplification of that rate.  The (n_j + 1)
+    factor and the sum_k n_k g_k of the denominator enter at every K >= 1."""
+    lam = np.array([2.0, 0.0])
+    gam = np.array([106.0, 60.0])
+    H = np.diag([0.0, 150.0]).astype(complex)
+    rho0 = np.full((2, 2), 0.5, dtype=complex)
+    t1, t2 = 1000, 2000
+    a = 2 * lam[0] * W * KB * 300.0 * W
+    b = lam[0] * gam[0] * W * W
+    g = gam[0] * W
+    # the rate of x_0 (phase of the site-energy difference included); classic RK4
+    # advances an eigenvector of a linear system by the degree-4 Taylor polynomial
+    # P(h lambda) per step exactly, so the expected ratio carries no time-step error
+    rate = -1j * (0.0 - 150.0) * W - (a - 1j * b) / g
+    z = rate * 1.0
+    markov = (1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24) ** (t2 - t1)
+    assert abs(markov - np.exp(rate * (t2 - t1))) < 1e-6  # and it is the continuous rate to RK4 accuracy
+    ratios = []
+    for term in (1, 0):
+        p = dict(N=2, K=K, H=H, lam=lam, gam=gam, T=300.0, terminator=term)
+        x1 = oracle.propagate(p, rho0, 1.0, t1, t1)["rho"][0, 1]
+        x2 = oracle.propagate(p, rho0, 1.0, t2, t2)["rho"][0, 1]
+        ratios.append(x2 / x1)
+    assert abs(ratios[0] - markov) < 1e-8 * abs(markov)
+    # the plain truncation misses it by far more at every depth here
+    assert abs(ratios[1] - markov) > 1e-6 * abs(markov)
+
+
 def test_single_site_trap_and_decay_closed_form():
     """One site with trap rate G_t and radiative rate G_r (ps^-1): the bath
     cannot act (V^x vanishes on a 1x1 block), so rho_11 = exp(-(G_t+G_r) t),
