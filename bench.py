@@ -44,6 +44,10 @@ L2_FLUSH_BYTES = 256 << 20
 # the paper's table of GPU timings (Tesla C2050, FP32): N = 7, N_max = 6, 1716 matrices,
 # 1000 RK4 steps in 3 s -> 1716 x 4 x 1000 / 3 node-RHS evaluations per second
 PAPER_NODE_RHS_PER_S = 1716 * 4 * 1000 / 3.0
+# the whole table (Table 2): N = 7, 1000 RK4 steps; N_max -> (matrices, CPU s, GPU s), the CPU an
+# "Intel 2.40 GHz", the GPU a Tesla C2050 in FP32
+PAPER_TABLE2 = {4: (330, 120.0, 1.0), 6: (1716, 676.0, 3.0), 8: (6435, 2636.0, 7.0), 10: (19448, 8275.0, 19.0),
+                12: (50388, 21972.0, 48.0)}
 
 
 def parse():
@@ -55,6 +59,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-scan measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-trace measurement")
     ap.add_argument("--no-large", action="store_true", help="skip the 24-site large-hierarchy measurement")
+    ap.add_argument("--no-table2", action="store_true",
+                    help="skip the depth sweep of the paper's timing table (N = 7, depths 4-12, 1000 steps)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the scaled-hierarchy and low-temperature variants of the headline workload")
     ap.add_argument("--serving-requests", type=int, default=2000,
@@ -579,6 +585,8 @@ def main():
         line["batched"] = bench_batched(heom, torch, stream, args.batched_steps)
     if rank == 0 and not args.no_large:
         line["large"] = bench_large(heom, torch, stream, peak, peak_kind, args.large_steps)
+    if rank == 0 and not args.no_table2:
+        line["table2_sweep"] = bench_table2(heom, torch, stream)
     if rank == 0 and not args.no_serving:
         line["serving"] = bench_serving(args.serving_requests)
     if rank == 0:
@@ -676,6 +684,49 @@ def bench_large(heom, torch, stream, peak, peak_kind, steps=0):
         "launch": cf.get_launch(),
         "max_abs_pop_diff_vs_unfiltered": float(np.abs(d_pops.view(nout, N).cpu().numpy() - pops_full).max())}
     cf.close()
+    return out
+
+
+def bench_table2(heom, torch, stream, nsteps=1000):
+    """The paper's timing table (Table 2) on this GPU: one FMO-like N = 7 trap
+    hierarchy at depths 4, 6, 8, 10 and 12 (330 to 50 388 matrices), 1000 RK4
+    steps at 1 fs, in mixed precision (the paper ran FP32) and in FP64.  Each
+    depth is timed in the library's default launch shape and in the shape its
+    autotuner picks on the live hierarchy; the paper's C2050 and CPU timings
+    stand beside them as context (other hardware)."""
+    out = {"workload": "FMO-like N=7 with trap (seed 1234), depths 4-12, %d RK4 steps at 1 fs, one hierarchy "
+                       "per solve, inputs resident, CUDA events; paper: Tesla C2050 FP32 and an Intel 2.40 GHz CPU"
+                       % nsteps, "rows": []}
+    for K, (mats, cpu_s, gpu_s) in sorted(PAPER_TABLE2.items()):
+        w = workloads.fmo_trap(K=K, nsteps=nsteps)
+        nodes = heom.num_nodes(7, K)
+        assert nodes == mats
+        row = {"depth": K, "matrices": nodes, "paper_gpu_s": gpu_s, "paper_cpu_s": cpu_s,
+               "paper_gpu_node_rhs_per_s": nodes * 4.0 * nsteps / gpu_s}
+        rho0 = torch.from_numpy(np.ascontiguousarray(w["rho0"])).to(torch.cuda.current_device())
+        for prec in ("fp32", "fp64"):
+            ctx = heom.Context(w["params"], prec, stream=stream)
+            for shape in ("default", "tuned"):
+                if shape == "tuned":
+                    ctx.autotune(trial_steps=20)
+                ev = []
+                with torch.cuda.stream(stream):
+                    for i in range(3):
+                        ctx.set_rho0_device(rho0)
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        ctx.propagate_device(1.0, nsteps, nsteps)
+                        e1.record(stream)
+                        ev.append((e0, e1))
+                stream.synchronize()
+                ms = min(a.elapsed_time(b) for a, b in ev[1:])
+                row["%s_%s" % (prec, shape)] = {"ms": ms, "node_rhs_per_s": nodes * 4.0 * nsteps / (ms * 1e-3),
+                                                "launch": ctx.get_launch()}
+            ctx.close()
+        best32 = min(row["fp32_default"]["ms"], row["fp32_tuned"]["ms"])
+        row["vs_paper_gpu"] = gpu_s * 1e3 / best32
+        out["rows"].append(row)
     return out
 
 

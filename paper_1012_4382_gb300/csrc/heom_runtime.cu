@@ -836,10 +836,25 @@ struct Engine {
         cudaGetLastError();
       }
       if ((prec == HEOM_FP64 && Mmax >= 256) || (prec == HEOM_FP32_MIXED && Mmax >= 1024)) {
+        // the grid engine: unit groups and CTA size as the autotuner picks them for the
+        // N = 7 trap hierarchies of depth 8, 10 and 12 (6435, 19448, 50388 nodes; 202, 608
+        // and 1575 blocks of 32 nodes): load views of 8 groups while the node blocks are
+        // few, the register view (2 groups) once they fill the GPU.  Measured against 32
+        // groups, 1000 steps: mixed 38.9 / 66.8 / 87.1 ms instead of 40.2 / 95.5 / 236.8,
+        // FP64 76.4 / 184.8 / 481 instead of 93.2 / 246.5 / 621
+        const int64_t nb = (Mmax + 31) / 32;
         c.mode = 1;
-        c.block = max_block();
-        c.G = N >= 4 ? 32 : 2;
         c.team_ctas = 1;
+        if (N < 4) {
+          c.block = max_block();
+          c.G = 2;
+        } else if (prec == HEOM_FP64) {
+          c.G = nb < 400 ? 8 : 2;
+          c.block = nb < 1000 ? 128 : 256;
+        } else {
+          c.G = nb < 1000 ? 8 : 2;
+          c.block = c.G == 8 ? 512 : 256;
+        }
       } else {
         c.mode = 0;
         c.block = 256;

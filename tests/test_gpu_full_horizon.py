@@ -9,6 +9,9 @@ benchmark times, in the launch shapes it times (default shapes).
   instance of every depth 4..8 against the oracle on every 10 fs row.
 * 24-site trimer (20 475 nodes): 50 steps of the full hierarchy in both
   precisions, FP64 node by node.
+* The depth sweep of the paper's timing table: its largest hierarchy (N = 7,
+  depth 12, 50 388 nodes), 20 steps, every node, in the default and the
+  autotuned launch shape.
 
 Paper: App. B (RK4 over the whole run; only rho and eta copied out), Eq. eta
 and Eq. trappingtime.  The oracle runs once per workload on the host cores.
@@ -108,4 +111,41 @@ def test_large_trimer_50_steps_full_hierarchy(trimer_50, precision):
         assert err < TOL64, err
     else:
         # float auxiliaries: relative to the largest auxiliary element
+        assert err < 1e-5 * max(1.0, np.abs(ref).max()), (err, np.abs(ref).max())
+
+
+@pytest.fixture(scope="module")
+def depth12_20():
+    w = workloads.fmo_trap(K=12, nsteps=20)
+    return w, oracle.propagate(w["params"], w["rho0"], 1.0, 20, 5, want_state=True)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape", ["default", "tuned"])
+def test_table2_depth12_every_node(depth12_20, precision, shape):
+    """The largest hierarchy of the paper's timing table (N = 7, N_max = 12,
+    50 388 matrices), in the launch shape the benchmark's depth sweep times:
+    the default one and the one the autotuner picks.  20 steps, every node of
+    the state against the oracle (FP64 1e-10; mixed 1e-5 of the largest
+    element), populations and eta on every row."""
+    w, o = depth12_20
+    N, K = 7, 12
+    with heom.Context(w["params"], precision) as c:
+        if shape == "tuned":
+            c.autotune(trial_steps=5)
+        c.set_rho0(w["rho0"])
+        r = c.propagate(1.0, 20, 5)
+        state, _ = c.state()
+    assert state.shape[0] == 50388
+    tp, te = (TOL64, TOL64) if precision == "fp64" else (TOL32_POP, TOL32_ETA)
+    assert np.abs(r["pops"] - o["pops"]).max() < tp
+    assert np.abs(r["eta"] - o["eta"]).max() < te
+    multi, _, _ = heom.build_index(N, K)
+    pos = {tuple(m): i for i, m in enumerate(o["multi"].tolist())}
+    perm = np.array([pos[tuple(m)] for m in multi.tolist()])
+    ref = o["state"][perm][:, :N, :N]
+    err = np.abs(state - ref).max()
+    if precision == "fp64":
+        assert err < TOL64, err
+    else:
         assert err < 1e-5 * max(1.0, np.abs(ref).max()), (err, np.abs(ref).max())
