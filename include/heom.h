@@ -277,16 +277,22 @@ int heom_ctx_num_nodes(const heom_ctx* ctx, int64_t* out);
  * dataflow engine -- the whole GPU, no grid barrier: each CTA keeps a slice
  * of nodes in shared memory, one thread per unit (an off-diagonal pair or a
  * diagonal element) of a node, and neighbour values travel as stage-tagged
- * words that a thread waits for (bounded, HEOM_ETIMEOUT) one by one.  Mode 3
- * is the default for one hierarchy of 256 nodes or more when all its CTAs fit
- * on the GPU at once.  block_threads: multiple of 32, 64..512
+ * words that a thread waits for (bounded, HEOM_ETIMEOUT) one by one.  In
+ * mode 3 team_ctas is the number of nodes each thread carries, 1..6 (more
+ * than one: real H and 4..8 sites only, HEOM_EUNSUPPORTED otherwise), which
+ * lets a hierarchy of up to about 6800 nodes (N = 7) run with all CTAs
+ * resident.  Mode 3 is the default for one hierarchy of 256 nodes or more
+ * when all its CTAs fit on the GPU at once with some number of nodes per
+ * thread (the fewest that fit).  block_threads: multiple of 32, 64..512
  * (64..256 for HEOM_FP64, whose kernels are compiled for that register budget);
- * in mode 3 the CTA size, at most 384, of which every N(N+1)/2 threads make a
- * node (N = 7: 12 nodes in 336 threads); a call whose CTAs cannot all be
- * resident fails with HEOM_EINVAL.  node_threads: threads sharing one node's
- * matrix, 1..32 (1 or 2 keep the node's matrix in registers; not used by
- * mode 3).  A negative mode or a non-positive value keeps the current
- * setting. */
+ * in mode 3 the CTA size, at most 384 with one node per thread and 256 with
+ * more, of which every N(N+1)/2 threads make a row of team_ctas nodes (N = 7,
+ * one node per thread: 12 nodes in 336 threads); a call whose CTAs cannot all
+ * be resident fails with HEOM_EINVAL.  Switching between mode 3 and the
+ * other modes without giving team_ctas or block_threads resets them to that
+ * family's default.  node_threads: threads sharing one node's matrix, 1..32
+ * (1 or 2 keep the node's matrix in registers; not used by mode 3).  A
+ * negative mode or a non-positive value keeps the current setting. */
 int heom_set_launch(heom_ctx* ctx, int32_t mode, int32_t team_ctas, int32_t block_threads, int32_t node_threads);
 int heom_get_launch(const heom_ctx* ctx, int32_t* mode, int32_t* team_ctas, int32_t* block_threads,
                     int32_t* node_threads);

@@ -5,11 +5,12 @@
 // (App. A2 Eqs. labsevena/lab8, App. A1, App. B), with trapping as the
 // anti-Hermitian part of H_eff.
 //
-// Decomposition.  CTA c owns the S consecutive nodes [c*S, c*S + S) and keeps
-// their three stage arrays (y, wa, wb) in shared memory for the whole call,
-// node-major: element p of local node l at l*N*N + p.  Thread (u, l) of the
-// CTA computes unit u (an off-diagonal pair (a, b), two packed reals, or a
-// diagonal a) of node l in every stage.  The part of a unit's right-hand side
+// Decomposition.  CTA c owns the SL = S * NPT consecutive nodes
+// [c*SL, c*SL + SL) and keeps their three stage arrays (y, wa, wb) in shared
+// memory for the whole call, node-major: element p of local node l at
+// l*N*N + p.  Thread (u, l) of the CTA computes unit u (an off-diagonal pair
+// (a, b), two packed reals, or a diagonal a) of the local nodes k*S + l,
+// k = 0..NPT-1, in every stage (NPT nodes per thread, 1 by default).  The part of a unit's right-hand side
 // that involves its own node -- the commutator with H_eff, the site-energy
 // differences, the trap/decay and low-temperature damping -- is a fixed
 // linear form in at most NRE (real part) and NIM (imaginary part) packed
@@ -51,6 +52,12 @@ constexpr int kFlowRing = 64;   // stop-rule decisions kept in flight
 // so that a CTA of 13 nodes at N = 7 (364 threads) fits one SM; real-H kernels
 // do not spill at this budget.
 constexpr int kFlowMaxThreads = 384;
+// Threads per CTA of the kernels whose threads carry several nodes (NPT > 1):
+// eight warps, two per SM sub-partition, so that a thread may hold 255
+// registers (with ten or twelve warps some sub-partition holds three, and its
+// register file allows 168).
+constexpr int kFlowMaxThreadsMulti = 256;
+constexpr int kFlowMaxNpt = 6;
 
 // One unit's own-node linear form (host-built).  Slot 0 of both lists is the
 // unit's own real element x = P[a*N + b]; for a pair, slot 1 is its imaginary
@@ -87,7 +94,7 @@ __host__ __device__ constexpr int flow_nre(int N, bool cplx) {
 __host__ __device__ constexpr int flow_nim(int N, bool cplx) {
   return (cplx ? 4 * N - 4 : 2 * N) < 2 ? 2 : (cplx ? 4 * N - 4 : 2 * N);
 }
-// Dynamic shared memory of a CTA of S nodes.
+// Dynamic shared memory of a CTA whose slice holds S nodes.
 __host__ __device__ constexpr int flow_smem_bytes(int N, int S, int rsize) { return 3 * S * N * N * rsize; }
 
 // ------------------------------------------------------------ tagged words
@@ -168,9 +175,16 @@ __device__ __forceinline__ void flow_eta_row(const Inst& I, const EtaAcc<R>* ea,
 }
 
 // ------------------------------------------------------------------ kernel
-
-template <int N, typename R, bool MIXED, bool CPLX>
-__global__ void __launch_bounds__(kFlowMaxThreads) heom_flow_kernel(FlowArgs A) {
+//
+// NPT nodes per thread: thread (u, l) of CTA c computes unit u of the nodes
+// c*S*NPT + k*S + l, k = 0..NPT-1 (the lanes of a warp stay consecutive nodes
+// of one unit for every k, so the exchange keeps its coalescing).  With
+// NPT > 1 the own-node part and the gathers of node k+1 are issued before the
+// thread waits for the words of node k, so one exchange latency covers all
+// of its nodes.  NPT = 1 runs the steps in the same order as a plain
+// one-node-per-thread kernel.
+template <int N, typename R, bool MIXED, bool CPLX, int NPT = 1>
+__global__ void __launch_bounds__(NPT == 1 ? kFlowMaxThreads : kFlowMaxThreadsMulti) heom_flow_kernel(FlowArgs A) {
   constexpr int NN = N * N;
   constexpr int NP = N * (N - 1) / 2;
   constexpr int U = NP + N;
@@ -187,7 +201,8 @@ __global__ void __launch_bounds__(kFlowMaxThreads) heom_flow_kernel(FlowArgs A) 
   __shared__ FF s_trace_ff[kMaxSmallN];
   __shared__ double s_trace_d[kMaxSmallN];
 
-  const int S = A.S;
+  const int S = A.S;        // threads per unit: nodes of one row of the slice
+  const int SL = S * NPT;   // nodes of the CTA's slice
   const int u = threadIdx.x / S;
   const int l = threadIdx.x - u * S;
   if (threadIdx.x == 0) {
@@ -198,19 +213,34 @@ __global__ void __launch_bounds__(kFlowMaxThreads) heom_flow_kernel(FlowArgs A) 
   __syncthreads();
   const Inst& I = s_inst;
   const int M = I.M, Mp = I.Mpad;
-  const int n = blockIdx.x * S + l;
-  const bool valid = u < U && n < M;
+  int nd[NPT];
+  bool valid[NPT];
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) {
+    nd[k] = blockIdx.x * SL + k * S + l;
+    valid[k] = u < U && nd[k] < M;
+  }
   const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
-  R* const sb = reinterpret_cast<R*>(dsm);  // stage buffer k at sb + k * S * NN
+  R* const sb = reinterpret_cast<R*>(dsm);  // stage buffer k at sb + k * SL * NN
 
-  // ---- the thread's unit, its linear form and its links
+  // ---- the thread's unit and its linear form (shared by its nodes); per node
+  // the slots 0 and 1 of both forms (where the node's damping and terminator
+  // enter), the links and the link weights
   int a = 0, b = 0, pab = 0, pba = 0;
   uint32_t ire4[(NRE + 3) / 4], iim4[(NIM + 3) / 4];
   R cre[NRE], cim[NIM];
-  int hl[4] = {-1, -1, -1, -1};  // up a, up b, down a, down b
-  R cu_a = R(0), cu_b = R(0), pd_a = R(0), qd_a = R(0), pd_b = R(0), qd_b = R(0);
-  const bool root = valid && n == 0;
-  if (valid) {
+  R c0r[NPT], c1r[NPT], c0i[NPT], c1i[NPT];
+  int hl[NPT][4];  // up a, up b, down a, down b
+  R cu_a[NPT], cu_b[NPT], pd_a[NPT], qd_a[NPT], pd_b[NPT], qd_b[NPT];
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) {
+    c0r[k] = c1r[k] = c0i[k] = c1i[k] = R(0);
+    cu_a[k] = cu_b[k] = pd_a[k] = qd_a[k] = pd_b[k] = qd_b[k] = R(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) hl[k][j] = -1;
+  }
+  const bool root = valid[0] && nd[0] == 0;  // only node 0 of a thread can be the root
+  if (valid[0]) {
     const FlowUnit& fu = A.units[u];
     const FlowSite* fs = reinterpret_cast<const FlowSite*>(A.units + U);
     a = fu.a;
@@ -238,73 +268,87 @@ __global__ void __launch_bounds__(kFlowMaxThreads) heom_flow_kernel(FlowArgs A) 
     for (int i = 0; i < NRE; ++i) dre[i] = fu.cre[i];
 #pragma unroll
     for (int i = 0; i < NIM; ++i) dim[i] = fu.cim[i];
-    // node data: links, n_a, n_b, sum_j n_j gamma_j, last level
-    const int ra = I.dn[a * Mp + n], rb = I.dn[b * Mp + n];
-    const int ua = I.up[a * Mp + n], ub = I.up[b * Mp + n];
-    const double na = ra < 0 ? 0.0 : (double)(ra >> 24), nb = rb < 0 ? 0.0 : (double)(rb >> 24);
-    const double ng = (double)static_cast<const R*>(I.ngam)[n];
-    const bool leaf = I.up[n] < 0;
-    const FlowSite sa = fs[a], sb = fs[b];
-    const bool scaled = I.wsc != nullptr;
-    dre[0] -= ng;  // hierarchy damping -sum_j n_j gamma_j on x (and on yi below)
-    if (a != b) {
-      dim[1] -= ng;
-      if (I.terminator && leaf) {
-        // sigma_{n+e_j} ~ (n_j+1)/(ngam+gamma_j) theta_j sigma_n, then i V_j^x of it (j = a, b)
-        const double ca = (na + 1.0) / (ng + sa.gamma), cb = (nb + 1.0) / (ng + sb.gamma);
-        dre[0] += -ca * sa.alpha - cb * sb.alpha;
-        dre[1] += -ca * sa.beta + cb * sb.beta;
-        dim[0] += ca * sa.beta - cb * sb.beta;
-        dim[1] += -ca * sa.alpha - cb * sb.alpha;
-      }
-      // up links i V_j^x sigma_{n+e_j}: re += cu Im(up), im -= cu Re(up); weight 1, or
-      // sqrt((n_j+1) s_j) in the scaled hierarchy
-      hl[0] = ua;
-      hl[1] = ub;
-      cu_a = (R)(-(scaled ? sqrt((na + 1.0) * sa.scale) : 1.0));
-      cu_b = (R)(scaled ? sqrt((nb + 1.0) * sb.scale) : 1.0);
-      // down links n_j theta_j sigma_{n-e_j}: re += p Re - q Im, im += q Re + p Im
-      hl[2] = ra < 0 ? -1 : (ra & 0xFFFFFF);
-      hl[3] = rb < 0 ? -1 : (rb & 0xFFFFFF);
-      const double wa = scaled ? sqrt(na / sa.scale) : na, wb = scaled ? sqrt(nb / sb.scale) : nb;
-      pd_a = (R)(wa * sa.beta);
-      qd_a = (R)(wa * sa.alpha);
-      pd_b = (R)(wb * sb.beta);
-      qd_b = (R)(-wb * sb.alpha);
-    } else {
-      // the up link carries no weight for a diagonal; it is still waited on (see above)
-      hl[0] = ua;
-      hl[2] = ra < 0 ? -1 : (ra & 0xFFFFFF);
-      const double wa = scaled ? sqrt(na / sa.scale) : na;
-      pd_a = (R)(2.0 * wa * sa.beta);
-    }
 #pragma unroll
     for (int i = 0; i < NRE; ++i) cre[i] = (R)dre[i];
 #pragma unroll
     for (int i = 0; i < NIM; ++i) cim[i] = (R)dim[i];
+    const FlowSite sa = fs[a], sbs = fs[b];
+    const bool scaled = I.wsc != nullptr;
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+      if (!valid[k]) continue;
+      const int n = nd[k];
+      // node data: links, n_a, n_b, sum_j n_j gamma_j, last level
+      const int ra = I.dn[a * Mp + n], rb = I.dn[b * Mp + n];
+      const int ua = I.up[a * Mp + n], ub = I.up[b * Mp + n];
+      const double na = ra < 0 ? 0.0 : (double)(ra >> 24), nb = rb < 0 ? 0.0 : (double)(rb >> 24);
+      const double ng = (double)static_cast<const R*>(I.ngam)[n];
+      const bool leaf = I.up[n] < 0;
+      double x0r = dre[0], x1r = dre[1], x0i = dim[0], x1i = dim[1];
+      x0r -= ng;  // hierarchy damping -sum_j n_j gamma_j on x (and on yi below)
+      if (a != b) {
+        x1i -= ng;
+        if (I.terminator && leaf) {
+          // sigma_{n+e_j} ~ (n_j+1)/(ngam+gamma_j) theta_j sigma_n, then i V_j^x of it (j = a, b)
+          const double ca = (na + 1.0) / (ng + sa.gamma), cb = (nb + 1.0) / (ng + sbs.gamma);
+          x0r += -ca * sa.alpha - cb * sbs.alpha;
+          x1r += -ca * sa.beta + cb * sbs.beta;
+          x0i += ca * sa.beta - cb * sbs.beta;
+          x1i += -ca * sa.alpha - cb * sbs.alpha;
+        }
+        // up links i V_j^x sigma_{n+e_j}: re += cu Im(up), im -= cu Re(up); weight 1, or
+        // sqrt((n_j+1) s_j) in the scaled hierarchy
+        hl[k][0] = ua;
+        hl[k][1] = ub;
+        cu_a[k] = (R)(-(scaled ? sqrt((na + 1.0) * sa.scale) : 1.0));
+        cu_b[k] = (R)(scaled ? sqrt((nb + 1.0) * sbs.scale) : 1.0);
+        // down links n_j theta_j sigma_{n-e_j}: re += p Re - q Im, im += q Re + p Im
+        hl[k][2] = ra < 0 ? -1 : (ra & 0xFFFFFF);
+        hl[k][3] = rb < 0 ? -1 : (rb & 0xFFFFFF);
+        const double wa = scaled ? sqrt(na / sa.scale) : na, wb = scaled ? sqrt(nb / sbs.scale) : nb;
+        pd_a[k] = (R)(wa * sa.beta);
+        qd_a[k] = (R)(wa * sa.alpha);
+        pd_b[k] = (R)(wb * sbs.beta);
+        qd_b[k] = (R)(-wb * sbs.alpha);
+      } else {
+        // the up link carries no weight for a diagonal; it is still waited on (see above)
+        hl[k][0] = ua;
+        hl[k][2] = ra < 0 ? -1 : (ra & 0xFFFFFF);
+        const double wa = scaled ? sqrt(na / sa.scale) : na;
+        pd_a[k] = (R)(2.0 * wa * sa.beta);
+      }
+      c0r[k] = (R)x0r;
+      c1r[k] = (R)x1r;
+      c0i[k] = (R)x0i;
+      c1i[k] = (R)x1i;
+    }
   }
   const bool pair = a != b;
 
   // ---- the state: own elements in registers (the Horner base), slice in shared memory
-  R y_r = R(0), y_i = R(0);
+  R y_r[NPT], y_i[NPT];
   const R* gy = static_cast<const R*>(I.y);
-  const int oab = pab * Mp + n, oba = pba * Mp + n;  // element offsets of the thread's outputs
-  if (valid) {
-    y_r = gy[oab];
-    y_i = pair ? gy[oba] : R(0);
-    if constexpr (MIXED) {
-      if (root) {
-        const FF* y0 = static_cast<const FF*>(I.y0);
-        s_ry[pab] = y0[pab];
-        if (pair) s_ry[pba] = y0[pba];
-      }
-    }
-    if (root && !pair) s_ea[a] = EtaAcc<R>{};
-    sb[l * NN + pab] = y_r;
-    if (pair) sb[l * NN + pba] = y_i;
-    flow_store(A.tags + WD * oab, y_r, A.tag0 + 1);
-    if (pair) flow_store(A.tags + WD * oba, y_i, A.tag0 + 1);
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) {
+    y_r[k] = y_i[k] = R(0);
+    if (!valid[k]) continue;
+    const int oab = pab * Mp + nd[k], oba = pba * Mp + nd[k];
+    y_r[k] = gy[oab];
+    y_i[k] = pair ? gy[oba] : R(0);
+    R* own = sb + (k * S + l) * NN;
+    own[pab] = y_r[k];
+    if (pair) own[pba] = y_i[k];
+    flow_store(A.tags + WD * oab, y_r[k], A.tag0 + 1);
+    if (pair) flow_store(A.tags + WD * oba, y_i[k], A.tag0 + 1);
   }
+  if constexpr (MIXED) {
+    if (root) {
+      const FF* y0 = static_cast<const FF*>(I.y0);
+      s_ry[pab] = y0[pab];
+      if (pair) s_ry[pba] = y0[pba];
+    }
+  }
+  if (root && !pair) s_ea[a] = EtaAcc<R>{};
   EtaRows rows;
   rows.acc0 = I.acc[0];
   rows.acc1 = I.acc[1];
@@ -334,123 +378,147 @@ __global__ void __launch_bounds__(kFlowMaxThreads) heom_flow_kernel(FlowArgs A) 
       const int in_sel = (s == 0) ? 0 : (s == 2 ? 2 : 1);
       const int out_sel = (s == 1) ? 2 : (s == 3 ? 0 : 1);
       const unsigned want = A.tag0 + 4u * (unsigned)t + (unsigned)s + 1u;
-      if (valid) {
-        const unsigned long long* tin = A.tags + in_sel * A.tag_stride;
-        // the own-node part first (shared memory), then the neighbours: by the time
-        // the gathers reach L2 their producers have mostly stored (measured: equal
-        // in FP32, 15 % faster in FP64 than gathering first)
-        const R* sin = sb + in_sel * S * NN + l * NN;
-        R re = R(0), im = R(0);
+      const unsigned long long* tin = A.tags + in_sel * A.tag_stride;
+      R re[NPT], im[NPT];
+      FlowWord<R> gr[NPT][4], gi[NPT][4];
+      bool aborted = false;
+      // the own-node part (shared memory), then the neighbours: by the time the
+      // gathers reach L2 their producers have mostly stored (measured: equal in
+      // FP32, 15 % faster in FP64 than gathering first)
+      auto own_and_gather = [&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        re[k] = R(0);
+        im[k] = R(0);
+        if (!valid[k]) return;
+        const R* sin = sb + in_sel * SL * NN + (k * S + l) * NN;
 #pragma unroll
-        for (int i = 0; i < NRE; ++i) re += cre[i] * sin[(ire4[i / 4] >> (8 * (i % 4))) & 0xFF];
+        for (int i = 0; i < NRE; ++i)
+          re[k] += (i == 0 ? c0r[k] : (i == 1 ? c1r[k] : cre[i])) * sin[(ire4[i / 4] >> (8 * (i % 4))) & 0xFF];
         if (pair) {  // a diagonal has no imaginary part; its units fill the last warps of a CTA
 #pragma unroll
-          for (int i = 0; i < NIM; ++i) im += cim[i] * sin[(iim4[i / 4] >> (8 * (i % 4))) & 0xFF];
+          for (int i = 0; i < NIM; ++i)
+            im[k] += (i == 0 ? c0i[k] : (i == 1 ? c1i[k] : cim[i])) * sin[(iim4[i / 4] >> (8 * (i % 4))) & 0xFF];
         }
-        FlowWord<R> gr[4], gi[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (hl[k] >= 0) {
-            gr[k].load(tin + WD * (pab * Mp + hl[k]));
-            gi[k].load(tin + WD * (pba * Mp + hl[k]));
+        for (int j = 0; j < 4; ++j)
+          if (hl[k][j] >= 0) {
+            gr[k][j].load(tin + WD * (pab * Mp + hl[k][j]));
+            gi[k][j].load(tin + WD * (pba * Mp + hl[k][j]));
           }
-        // wait, bounded, until every gathered word carries the previous stage's tag
+      };
+      // wait, bounded, until every gathered word of node k carries the previous stage's tag
+      auto wait_words = [&](auto kc) -> bool {
+        constexpr int k = decltype(kc)::value;
         bool ready = true;
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (hl[k] >= 0) ready = ready & gr[k].ok(want) & gi[k].ok(want);
-        if (!ready) {
-          uint64_t t0 = 0;
-          for (unsigned spins = 1;; ++spins) {
-            // reload every word that is not there yet, then check them all
+        for (int j = 0; j < 4; ++j)
+          if (hl[k][j] >= 0) ready = ready & gr[k][j].ok(want) & gi[k][j].ok(want);
+        if (ready) return true;
+        uint64_t t0 = 0;
+        for (unsigned spins = 1;; ++spins) {
+          // reload every word that is not there yet, then check them all
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-              if (hl[k] >= 0) {
-                if (!gr[k].ok(want)) gr[k].load(tin + WD * (pab * Mp + hl[k]));
-                if (!gi[k].ok(want)) gi[k].load(tin + WD * (pba * Mp + hl[k]));
-              }
-            ready = true;
+          for (int j = 0; j < 4; ++j)
+            if (hl[k][j] >= 0) {
+              if (!gr[k][j].ok(want)) gr[k][j].load(tin + WD * (pab * Mp + hl[k][j]));
+              if (!gi[k][j].ok(want)) gi[k][j].load(tin + WD * (pba * Mp + hl[k][j]));
+            }
+          ready = true;
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-              if (hl[k] >= 0) ready = ready & gr[k].ok(want) & gi[k].ok(want);
-            if (ready) break;
-            if ((spins & 255u) == 0) {
-              if (ld_volatile(A.status) & kStatusTimeout) {
-                s_abort = 1;
-                break;
-              }
-              const uint64_t now = global_timer_ns();
-              if (t0 == 0) {
-                t0 = now;
-              } else if (now - t0 > kBarrierLimitNs) {
-                atomicOr(A.status, kStatusTimeout);
-                s_abort = 1;
-                break;
-              }
+          for (int j = 0; j < 4; ++j)
+            if (hl[k][j] >= 0) ready = ready & gr[k][j].ok(want) & gi[k][j].ok(want);
+          if (ready) return true;
+          if ((spins & 255u) == 0) {
+            if (ld_volatile(A.status) & kStatusTimeout) {
+              s_abort = 1;
+              return false;
+            }
+            const uint64_t now = global_timer_ns();
+            if (t0 == 0) {
+              t0 = now;
+            } else if (now - t0 > kBarrierLimitNs) {
+              atomicOr(A.status, kStatusTimeout);
+              s_abort = 1;
+              return false;
             }
           }
         }
-        if (ready) {
-          const R ur = gr[0].value(), ui = gi[0].value(), vr = gr[1].value(), vi = gi[1].value();
-          const R dr = gr[2].value(), di = gi[2].value(), er = gr[3].value(), ei = gi[3].value();
-          // absent links were never loaded and read as 0
-          re += cu_a * ui + cu_b * vi + pd_a * dr - qd_a * di + pd_b * er - qd_b * ei;
-          im += -cu_a * ur - cu_b * vr + qd_a * dr + pd_a * di + qd_b * er + pd_b * ei;
-          R w_r, w_i;
-          const unsigned tag_out = want + 1u;
-          if (MIXED && root) {
-            if constexpr (MIXED) {
-              const float hh = I.hh[s], hlo = I.hl[s];
-              if (!pair) {
-                // eta, loss and xi rows of the augmented system: the float-float stage input
-                if (s == 3) s_ea[a].add(I, a, s_rw[a]);
-                if (s == 2) s_ea[a].add_xi(I, a, s_rw[a]);
-              }
-              const FF fr = ff_axpy(s_ry[pab], hh, hlo, re);
-              const FF fi = pair ? ff_axpy(s_ry[pba], hh, hlo, im) : FF{0.f, 0.f};
-              w_r = fr.h;
-              w_i = fi.h;
-              if (!pair) s_rw[a] = fr;
-              if (s == 3) {
-                s_ry[pab] = fr;
-                if (pair) s_ry[pba] = fi;
-                if (!pair && os.now && I.out_pops) I.out_pops[os.row * N + a] = ff_to_double(fr);
-              }
+      };
+      // the neighbour terms, the Horner update and the stores of node k
+      auto finish = [&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        const R ur = gr[k][0].value(), ui = gi[k][0].value(), vr = gr[k][1].value(), vi = gi[k][1].value();
+        const R dr = gr[k][2].value(), di = gi[k][2].value(), er = gr[k][3].value(), ei = gi[k][3].value();
+        // absent links were never loaded and read as 0
+        R rr = re[k], mm = im[k];
+        rr += cu_a[k] * ui + cu_b[k] * vi + pd_a[k] * dr - qd_a[k] * di + pd_b[k] * er - qd_b[k] * ei;
+        mm += -cu_a[k] * ur - cu_b[k] * vr + qd_a[k] * dr + pd_a[k] * di + qd_b[k] * er + pd_b[k] * ei;
+        R w_r, w_i;
+        const unsigned tag_out = want + 1u;
+        const bool rt = k == 0 && root;
+        if (MIXED && rt) {
+          if constexpr (MIXED) {
+            const float hh = I.hh[s], hlo = I.hl[s];
+            if (!pair) {
+              // eta, loss and xi rows of the augmented system: the float-float stage input
+              if (s == 3) s_ea[a].add(I, a, s_rw[a]);
+              if (s == 2) s_ea[a].add_xi(I, a, s_rw[a]);
             }
-          } else {
-            if constexpr (!MIXED) {
-              if (root && !pair) {
-                if (s == 3) s_ea[a].add(I, cfd, N, a, (double)sin[pab]);
-                if (s == 2) s_ea[a].add_xi(I, cfd, a, (double)sin[pab]);
-              }
-            }
-            const R h = sizeof(R) == 8 ? (R)I.hd[s] : (R)I.hh[s];
-            w_r = y_r + h * re;
-            w_i = y_i + h * im;
-            if (s == 3 && root && !pair && os.now && I.out_pops) I.out_pops[os.row * N + a] = (double)w_r;
-          }
-          R* sout = sb + out_sel * S * NN + l * NN;
-          unsigned long long* tout = A.tags + out_sel * A.tag_stride;
-          sout[pab] = w_r;
-          flow_store(tout + WD * oab, w_r, tag_out);
-          if (pair) {
-            sout[pba] = w_i;
-            flow_store(tout + WD * oba, w_i, tag_out);
-          }
-          if (s == 3) {
-            y_r = w_r;
-            y_i = w_i;
-          }
-          if (diag_root) {
-            if (s == 2) s_ea[a].step_xi(I);
+            const FF fr = ff_axpy(s_ry[pab], hh, hlo, rr);
+            const FF fi = pair ? ff_axpy(s_ry[pba], hh, hlo, mm) : FF{0.f, 0.f};
+            w_r = fr.h;
+            w_i = fi.h;
+            if (!pair) s_rw[a] = fr;
             if (s == 3) {
-              if (os.now || t + 1 == I.nsteps) s_ea[a].store(I, a);
-              if constexpr (MIXED) s_trace_ff[a] = s_ry[pab];
-              else s_trace_d[a] = (double)w_r;
+              s_ry[pab] = fr;
+              if (pair) s_ry[pba] = fi;
+              if (!pair && os.now && I.out_pops) I.out_pops[os.row * N + a] = ff_to_double(fr);
             }
           }
+        } else {
+          if constexpr (!MIXED) {
+            if (rt && !pair) {
+              const R* sin = sb + in_sel * SL * NN + (k * S + l) * NN;
+              if (s == 3) s_ea[a].add(I, cfd, N, a, (double)sin[pab]);
+              if (s == 2) s_ea[a].add_xi(I, cfd, a, (double)sin[pab]);
+            }
+          }
+          const R h = sizeof(R) == 8 ? (R)I.hd[s] : (R)I.hh[s];
+          w_r = y_r[k] + h * rr;
+          w_i = y_i[k] + h * mm;
+          if (s == 3 && rt && !pair && os.now && I.out_pops) I.out_pops[os.row * N + a] = (double)w_r;
         }
-      }
+        R* sout = sb + out_sel * SL * NN + (k * S + l) * NN;
+        unsigned long long* tout = A.tags + out_sel * A.tag_stride;
+        const int oab = pab * Mp + nd[k], oba = pba * Mp + nd[k];
+        sout[pab] = w_r;
+        flow_store(tout + WD * oab, w_r, tag_out);
+        if (pair) {
+          sout[pba] = w_i;
+          flow_store(tout + WD * oba, w_i, tag_out);
+        }
+        if (s == 3) {
+          y_r[k] = w_r;
+          y_i[k] = w_i;
+        }
+        if (k == 0 && diag_root) {
+          if (s == 2) s_ea[a].step_xi(I);
+          if (s == 3) {
+            if (os.now || t + 1 == I.nsteps) s_ea[a].store(I, a);
+            if constexpr (MIXED) s_trace_ff[a] = s_ry[pab];
+            else s_trace_d[a] = (double)w_r;
+          }
+        }
+      };
+      own_and_gather(std::integral_constant<int, 0>{});
+      static_for<0, NPT>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        if constexpr (k + 1 < NPT) own_and_gather(std::integral_constant<int, k + 1>{});
+        if (valid[k] && !aborted) {
+          if (wait_words(kc)) finish(kc);
+          else aborted = true;
+        }
+      });
       __syncthreads();
       if (s_abort) return;
     }
@@ -506,16 +574,18 @@ __global__ void __launch_bounds__(kFlowMaxThreads) heom_flow_kernel(FlowArgs A) 
     }
   }
   // the state back to device memory (packed, element-major; the root also in float-float)
-  if (valid) {
-    R* gyw = static_cast<R*>(I.y);
-    gyw[oab] = y_r;
-    if (pair) gyw[oba] = y_i;
-    if constexpr (MIXED) {
-      if (root) {
-        FF* y0 = static_cast<FF*>(I.y0);
-        y0[pab] = s_ry[pab];
-        if (pair) y0[pba] = s_ry[pba];
-      }
+  R* gyw = static_cast<R*>(I.y);
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) {
+    if (!valid[k]) continue;
+    gyw[pab * Mp + nd[k]] = y_r[k];
+    if (pair) gyw[pba * Mp + nd[k]] = y_i[k];
+  }
+  if constexpr (MIXED) {
+    if (root) {
+      FF* y0 = static_cast<FF*>(I.y0);
+      y0[pab] = s_ry[pab];
+      if (pair) y0[pba] = s_ry[pba];
     }
   }
   __syncthreads();

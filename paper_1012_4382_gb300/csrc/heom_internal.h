@@ -17,11 +17,12 @@ const void* engine_kernel_scaled_f64(int N, bool cplx);
 const void* engine_kernel_scaled_f32(int N, bool cplx);
 // Large-N engine (9..24 sites).
 const void* large_kernel(bool fp64, bool cplx, bool scaled);
-// Dataflow engine (launch mode 3, one hierarchy on the whole GPU), N = 1..8.
-const void* flow_kernel_f32(int N, bool cplx);
-const void* flow_kernel_f64(int N, bool cplx);
-inline const void* flow_kernel(bool fp64, bool cplx, int N) {
-  return fp64 ? flow_kernel_f64(N, cplx) : flow_kernel_f32(N, cplx);
+// Dataflow engine (launch mode 3, one hierarchy on the whole GPU), N = 1..8,
+// npt nodes per thread (nullptr where that count is not built).
+const void* flow_kernel_f32(int N, bool cplx, int npt);
+const void* flow_kernel_f64(int N, bool cplx, int npt);
+inline const void* flow_kernel(bool fp64, bool cplx, int N, int npt = 1) {
+  return fp64 ? flow_kernel_f64(N, cplx, npt) : flow_kernel_f32(N, cplx, npt);
 }
 // Distributed-shared-memory engine (mixed precision only).
 const void* smem_kernel_f32_real(int N, bool reg);

@@ -1,20 +1,38 @@
-// Instantiations of the dataflow engine (launch mode 3) for N = 1..8, double precision.
+// Instantiations of the dataflow engine (launch mode 3) for N = 1..8, FP64.
+// One node per thread for every N and H; with real H and N >= 4 also 2
+// nodes per thread (hierarchies too large for one node per thread).
 // (One translation unit per precision so they compile in parallel.)
 #include "heom_flow.cuh"
 #include "heom_internal.h"
 
 namespace heom {
 
-const void* flow_kernel_f64(int N, bool cplx) {
+namespace {
+template <int N, typename R, bool MIXED>
+const void* flow_pick(bool cplx, int npt) {
+  if (npt == 1)
+    return cplx ? (const void*)heom_flow_kernel<N, R, MIXED, true, 1> : (const void*)heom_flow_kernel<N, R, MIXED, false, 1>;
+  if constexpr (N >= 4) {
+    if (cplx) return nullptr;
+    switch (npt) {
+      case 2: return (const void*)heom_flow_kernel<N, R, MIXED, false, 2>;
+      default: return nullptr;
+    }
+  }
+  return nullptr;
+}
+}  // namespace
+
+const void* flow_kernel_f64(int N, bool cplx, int npt) {
   switch (N) {
-    case 1: return cplx ? (const void*)heom_flow_kernel<1, double, false, true> : (const void*)heom_flow_kernel<1, double, false, false>;
-    case 2: return cplx ? (const void*)heom_flow_kernel<2, double, false, true> : (const void*)heom_flow_kernel<2, double, false, false>;
-    case 3: return cplx ? (const void*)heom_flow_kernel<3, double, false, true> : (const void*)heom_flow_kernel<3, double, false, false>;
-    case 4: return cplx ? (const void*)heom_flow_kernel<4, double, false, true> : (const void*)heom_flow_kernel<4, double, false, false>;
-    case 5: return cplx ? (const void*)heom_flow_kernel<5, double, false, true> : (const void*)heom_flow_kernel<5, double, false, false>;
-    case 6: return cplx ? (const void*)heom_flow_kernel<6, double, false, true> : (const void*)heom_flow_kernel<6, double, false, false>;
-    case 7: return cplx ? (const void*)heom_flow_kernel<7, double, false, true> : (const void*)heom_flow_kernel<7, double, false, false>;
-    case 8: return cplx ? (const void*)heom_flow_kernel<8, double, false, true> : (const void*)heom_flow_kernel<8, double, false, false>;
+    case 1: return flow_pick<1, double, false>(cplx, npt);
+    case 2: return flow_pick<2, double, false>(cplx, npt);
+    case 3: return flow_pick<3, double, false>(cplx, npt);
+    case 4: return flow_pick<4, double, false>(cplx, npt);
+    case 5: return flow_pick<5, double, false>(cplx, npt);
+    case 6: return flow_pick<6, double, false>(cplx, npt);
+    case 7: return flow_pick<7, double, false>(cplx, npt);
+    case 8: return flow_pick<8, double, false>(cplx, npt);
     default: return nullptr;
   }
 }

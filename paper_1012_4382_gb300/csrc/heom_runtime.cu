@@ -814,26 +814,33 @@ struct Engine {
       // CTAs of about 336 threads (12 nodes at N = 7: 1.25 us per stage for both, 1.45-2.3
       // with 5-11 or 13 nodes); in FP64, bound by the FP64 pipe, the nodes spread evenly
       // over all SMs, S = ceil(M / SMs)
+      // Beyond what one node per thread holds (about 1976 nodes at N = 7), each thread
+      // carries npt = 2..6 nodes of its unit (real H, N >= 4; CTAs of at most 256 threads,
+      // the nodes spread evenly): the fewest nodes per thread with which all CTAs fit.
       if (Mmax >= 256) {
         const int U = N * (N + 1) / 2;
-        const int64_t even = (Mmax + sms - 1) / sms;
-        const int S = (int)std::min<int64_t>(heom::kFlowMaxThreads / U,
-                                             prec == HEOM_FP64 ? even : std::max<int64_t>(336 / U, even));
-        const void* k = heom::flow_kernel(prec == HEOM_FP64, false, N);
-        int per_sm = 0;
-        if (S >= 1 && k &&
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 heom::flow_smem_bytes(N, S, (int)rsize())) == cudaSuccess &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, S * U, heom::flow_smem_bytes(N, S, (int)rsize())) ==
-                cudaSuccess &&
-            (int64_t)per_sm * sms >= (Mmax + S - 1) / S) {
-          c.mode = 3;
-          c.block = S * U;
-          c.G = 1;
-          c.team_ctas = 1;
-          return c;
+        bool cplx_any = false;
+        for (auto& in : inst) cplx_any |= (in->N == N && in->complex_h);
+        for (int npt = 1; npt <= heom::kFlowMaxNpt; ++npt) {
+          const int maxthr = npt == 1 ? heom::kFlowMaxThreads : heom::kFlowMaxThreadsMulti;
+          const int64_t even = (Mmax + (int64_t)sms * npt - 1) / ((int64_t)sms * npt);
+          const int S = (int)std::min<int64_t>(
+              maxthr / U, npt > 1 ? even : (prec == HEOM_FP64 ? even : std::max<int64_t>(336 / U, even)));
+          const void* k = heom::flow_kernel(prec == HEOM_FP64, cplx_any, N, npt);
+          if (S < 1 || !k) continue;
+          const int dyn = heom::flow_smem_bytes(N, S * npt, (int)rsize());
+          int per_sm = 0;
+          if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess &&
+              cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, S * U, dyn) == cudaSuccess &&
+              (int64_t)per_sm * sms >= (Mmax + S * npt - 1) / (S * npt)) {
+            c.mode = 3;
+            c.block = S * U;
+            c.G = 1;
+            c.team_ctas = npt;
+            return c;
+          }
+          cudaGetLastError();
         }
-        cudaGetLastError();
       }
       if ((prec == HEOM_FP64 && Mmax >= 256) || (prec == HEOM_FP32_MIXED && Mmax >= 1024)) {
         // the grid engine: unit groups and CTA size as the autotuner picks them for the
@@ -1295,15 +1302,21 @@ struct Engine {
     NvtxRange range("heom dataflow launch");
     const int N = in.N, U = N * (N + 1) / 2, NN = N * N;
     const bool fp64 = prec == HEOM_FP64;
-    const void* k = heom::flow_kernel(fp64, in.complex_h != 0, N);
-    if (!k) return fail(HEOM_EUNSUPPORTED, "launch mode 3 takes at most %d sites", heom::kMaxSmallN);
+    const int npt = c.team_ctas;  // nodes per thread
+    const void* k = heom::flow_kernel(fp64, in.complex_h != 0, N, npt);
+    if (!k)
+      return fail(HEOM_EUNSUPPORTED,
+                  "launch mode 3 takes at most %d sites, and more than one node per thread only with real H "
+                  "and 4..%d sites (asked: %d nodes per thread)", heom::kMaxSmallN, heom::kMaxSmallN, npt);
     if (nsteps > (int64_t)1 << 29) return fail(HEOM_EINVAL, "launch mode 3 takes at most 2^29 steps per call");
     const int S = flow_nodes_per_cta(N, c.block);
     const int threads = S * U;
-    if (threads > heom::kFlowMaxThreads)
-      return fail(HEOM_EINVAL, "launch mode 3: %d nodes x %d units exceed %d threads", S, U, heom::kFlowMaxThreads);
-    const int grid = (int)((in.M + S - 1) / S);
-    const int dyn = heom::flow_smem_bytes(N, S, (int)rsize());
+    const int maxthr = npt == 1 ? heom::kFlowMaxThreads : heom::kFlowMaxThreadsMulti;
+    if (threads > maxthr)
+      return fail(HEOM_EINVAL, "launch mode 3: %d nodes x %d units exceed %d threads", S, U, maxthr);
+    const int SL = S * npt;  // nodes of a CTA's slice
+    const int grid = (int)((in.M + SL - 1) / SL);
+    const int dyn = heom::flow_smem_bytes(N, SL, (int)rsize());
     const long long wd = fp64 ? 2 : 1;
     const long long stride = (long long)NN * in.Mpad * wd;
     if (!in.flow_tags.p) {
@@ -1327,8 +1340,8 @@ struct Engine {
     if ((int64_t)per_sm * sms < grid)
       return fail(HEOM_EINVAL,
                   "launch mode 3: %d CTAs of %d nodes (%d threads) cannot all be resident (%d per SM); use "
-                  "more nodes per CTA or another mode",
-                  grid, S, threads, per_sm);
+                  "more nodes per CTA or per thread, or another mode",
+                  grid, SL, threads, per_sm);
     heom::FlowArgs F;
     F.inst = d_inst;
     F.units = in.flow_units.as<heom::FlowUnit>();
@@ -1348,7 +1361,8 @@ struct Engine {
   // FP64 or N > 8; scaled hierarchies in mode 2 or with the register view
   // (node_threads <= 2) for N <= 8.
   const void* kernel_for(int N, int cplx, int sc, const LaunchCfg& c) const {
-    if (c.mode == 3) return N > heom::kMaxSmallN ? nullptr : heom::flow_kernel(prec == HEOM_FP64, cplx != 0, N);
+    if (c.mode == 3)
+      return N > heom::kMaxSmallN ? nullptr : heom::flow_kernel(prec == HEOM_FP64, cplx != 0, N, c.team_ctas);
     if (N > heom::kMaxSmallN) return c.mode == 2 ? nullptr : heom::large_kernel(prec == HEOM_FP64, cplx != 0, sc != 0);
     if (c.mode == 2) return (prec == HEOM_FP64 || sc) ? nullptr : heom::smem_kernel(cplx != 0, c.G <= 2, N);
     return heom::engine_kernel(prec == HEOM_FP64, cplx != 0, c.G <= 2, N, sc != 0);
@@ -1821,11 +1835,13 @@ int heom_set_launch(heom_ctx* ctx, int32_t mode, int32_t team_ctas, int32_t bloc
   if (block_threads > 0) n.block = block_threads;
   if (node_threads > 0) n.G = node_threads;
   if (n.mode < 0 || n.mode > 3) return fail(HEOM_EINVAL, "mode must be 0, 1, 2 or 3");
-  if (block_threads <= 0 && (n.mode == 3) != (c.mode == 3)) {
-    // a block size of the other family of engines does not carry over: take that family's default
+  if ((n.mode == 3) != (c.mode == 3)) {
+    // a block size or team size (nodes per thread in mode 3) of the other family of
+    // engines does not carry over: take that family's default
     const int N = ctx->e.inst[0]->N;
     const int U = N * (N + 1) / 2;
-    n.block = n.mode == 3 ? std::max(U, heom::kFlowMaxThreads / U * U) : ctx->e.max_block();
+    if (block_threads <= 0) n.block = n.mode == 3 ? std::max(U, heom::kFlowMaxThreads / U * U) : ctx->e.max_block();
+    if (team_ctas <= 0) n.team_ctas = 1;
   }
   if (n.mode == 2 && ctx->e.prec == HEOM_FP64) return fail(HEOM_EINVAL, "mode 2 (shared memory) needs HEOM_FP32_MIXED");
   const int N = ctx->e.inst[0]->N;
@@ -1834,11 +1850,15 @@ int heom_set_launch(heom_ctx* ctx, int32_t mode, int32_t team_ctas, int32_t bloc
                 heom::kMaxSmallN);
   if (n.team_ctas < 1 || n.team_ctas > 16) return fail(HEOM_EINVAL, "team_ctas must be 1..16");
   if (n.mode == 3) {
-    // block_threads: the CTA size asked for; a CTA runs block_threads / U whole nodes (U = N(N+1)/2)
+    // block_threads: the CTA size asked for; a CTA runs block_threads / U unit rows
+    // (U = N(N+1)/2) of team_ctas nodes each (nodes per thread, 1..kFlowMaxNpt)
     const int U = N * (N + 1) / 2;
-    if (n.block < U || n.block > heom::kFlowMaxThreads)
-      return fail(HEOM_EINVAL, "mode 3: block_threads must be %d..%d (at least one node of %d units)", U,
-                  heom::kFlowMaxThreads, U);
+    if (n.team_ctas > heom::kFlowMaxNpt)
+      return fail(HEOM_EINVAL, "mode 3: team_ctas (nodes per thread) must be 1..%d", heom::kFlowMaxNpt);
+    const int maxthr = n.team_ctas == 1 ? heom::kFlowMaxThreads : heom::kFlowMaxThreadsMulti;
+    if (n.block < U || n.block > maxthr)
+      return fail(HEOM_EINVAL, "mode 3: block_threads must be %d..%d with %d nodes per thread (at least one node "
+                  "of %d units)", U, maxthr, n.team_ctas, U);
   } else {
     const int maxb = ctx->e.max_block();
     if (n.block < 64 || n.block > maxb || n.block % 32)
@@ -1901,15 +1921,22 @@ int heom_autotune(heom_ctx* ctx, int64_t trial_steps, double* best_us_per_step) 
       cands.push_back(c);
     }
     if (!large && G == 1) {
-      // the dataflow engine: S nodes per CTA (its unit groups are fixed: one thread per unit)
+      // the dataflow engine: S nodes per unit row and npt nodes per thread (its unit
+      // groups are fixed: one thread per unit); shapes whose CTAs cannot all be resident
+      // are refused by the launch
       const int U = in.N * (in.N + 1) / 2;
-      for (int S : {4, 6, 8, 10, 12, 13, 16, 24, 32, 64}) {
-        if (S * U > heom::kFlowMaxThreads) continue;
-        LaunchCfg c;
-        c.mode = 3;
-        c.block = S * U;
-        c.G = 1;
-        cands.push_back(c);
+      for (int npt = 1; npt <= heom::kFlowMaxNpt; ++npt) {
+        if (!heom::flow_kernel(e.prec == HEOM_FP64, in.complex_h != 0, in.N, npt)) continue;
+        const int maxthr = npt == 1 ? heom::kFlowMaxThreads : heom::kFlowMaxThreadsMulti;
+        for (int S : {4, 6, 8, 9, 10, 12, 13, 16, 24, 32, 64}) {
+          if (S * U > maxthr) continue;
+          LaunchCfg c;
+          c.mode = 3;
+          c.block = S * U;
+          c.G = 1;
+          c.team_ctas = npt;
+          cands.push_back(c);
+        }
       }
     }
     if (e.prec == HEOM_FP32_MIXED && !large)
