@@ -42,11 +42,11 @@ def test_paper_timing_table_constants():
     """The depth sweep compares with the paper's timing table (Table 2): its
     matrix counts are the hierarchy sizes C(7 + N_max, N_max), and the
     speed-ups it prints (x120, x225, x376, x435, x458) are its CPU times over
-    its GPU times, truncated."""
+    its GPU times to within one (the table rounds some and truncates others)."""
     import math
     assert sorted(bench.PAPER_TABLE2) == [4, 6, 8, 10, 12]
     for K, (mats, cpu_s, gpu_s) in bench.PAPER_TABLE2.items():
         assert mats == math.comb(7 + K, K) == oracle.num_nodes(7, K)
-    speedups = [int(bench.PAPER_TABLE2[K][1] / bench.PAPER_TABLE2[K][2]) for K in (4, 6, 8, 10, 12)]
-    assert speedups == [120, 225, 376, 435, 458]
+    speedups = [bench.PAPER_TABLE2[K][1] / bench.PAPER_TABLE2[K][2] for K in (4, 6, 8, 10, 12)]
+    assert np.all(np.abs(np.array(speedups) - [120, 225, 376, 435, 458]) < 1.0)
     assert bench.PAPER_NODE_RHS_PER_S == bench.PAPER_TABLE2[6][0] * 4 * 1000 / bench.PAPER_TABLE2[6][2]
