@@ -178,11 +178,12 @@ __device__ __forceinline__ void flow_eta_row(const Inst& I, const EtaAcc<R>* ea,
 //
 // NPT nodes per thread: thread (u, l) of CTA c computes unit u of the nodes
 // c*S*NPT + k*S + l, k = 0..NPT-1 (the lanes of a warp stay consecutive nodes
-// of one unit for every k, so the exchange keeps its coalescing).  With
-// NPT > 1 the own-node part and the gathers of node k+1 are issued before the
-// thread waits for the words of node k, so one exchange latency covers all
-// of its nodes.  NPT = 1 runs the steps in the same order as a plain
-// one-node-per-thread kernel.
+// of one unit for every k, so the exchange keeps its coalescing).  A thread
+// first runs the own-node parts and issues the gathers of all its nodes
+// (independent chains the compiler interleaves), then waits for and updates
+// them node by node, so one exchange latency covers all of its nodes.
+// NPT = 1 runs the steps in the same order as a plain one-node-per-thread
+// kernel.
 template <int N, typename R, bool MIXED, bool CPLX, int NPT = 1>
 __global__ void __launch_bounds__(NPT == 1 ? kFlowMaxThreads : kFlowMaxThreadsMulti) heom_flow_kernel(FlowArgs A) {
   constexpr int NN = N * N;
@@ -510,10 +511,11 @@ __global__ void __launch_bounds__(NPT == 1 ? kFlowMaxThreads : kFlowMaxThreadsMu
           }
         }
       };
-      own_and_gather(std::integral_constant<int, 0>{});
+      // every node's own-node part and gathers first (independent chains the
+      // compiler interleaves), then the waits and updates node by node
+      static_for<0, NPT>([&](auto kc) { own_and_gather(kc); });
       static_for<0, NPT>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
-        if constexpr (k + 1 < NPT) own_and_gather(std::integral_constant<int, k + 1>{});
         if (valid[k] && !aborted) {
           if (wait_words(kc)) finish(kc);
           else aborted = true;

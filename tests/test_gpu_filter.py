@@ -160,3 +160,28 @@ def test_kept_nodes_propagated_unscaled_match_the_oracle(pilot, precision):
     assert np.abs(r["eta"] - o["eta"]).max() < te
     # the same physics as the scaled filtered run
     assert np.abs(o["pops"] - o_scaled["pops"]).max() < 1e-12
+
+
+def test_filtered_depth8_runs_several_nodes_per_thread():
+    """A filtered depth-8 hierarchy of about 4000 kept nodes: too many for one
+    node per thread of the dataflow engine, so the default carries several;
+    every kept node against the oracle on the same node set."""
+    w = workloads.fmo_trap(K=8, nsteps=30)
+    p = w["params"]
+    M = heom.num_nodes(7, 8)
+    keep = heom.filter_select(7, 8, np.linspace(1.0, 0.0, M), 0.38)  # the first ~62 %, closed downwards
+    assert 3000 < keep.sum() < 5000
+    with heom.Context(p, "fp32", keep=keep) as c:
+        L = c.get_launch()
+        assert L["mode"] == 3 and L["team_ctas"] > 1, L
+        c.set_rho0(w["rho0"])
+        r = c.propagate(1.0, 30, 10)
+        st, _ = c.state()
+    okeep = np.zeros(M, np.uint8)
+    okeep[_perm(7, 8)] = keep
+    o = oracle.propagate(dict(p, keep=okeep), w["rho0"], 1.0, 30, 10, want_state=True)
+    assert np.abs(r["pops"] - o["pops"]).max() < TOL32_POP
+    assert np.abs(r["eta"] - o["eta"]).max() < TOL32_ETA
+    kept = np.flatnonzero(keep)
+    ref = o["state"][_perm(7, 8)][kept][:, :7, :7]
+    assert np.abs(st - ref).max() < 1e-5

@@ -350,6 +350,21 @@ def test_autotune_keeps_state_and_result():
     assert np.abs(r["pops"] - o["pops"]).max() < TOL64
 
 
+def test_autotune_over_nodes_per_thread_keeps_state_and_result():
+    """Depth 7 (3432 nodes) in mixed precision: the autotuner's candidates
+    include the dataflow engine with several nodes per thread; whichever it
+    keeps, the state is restored and the run matches the oracle."""
+    w = workloads.fmo_trap(K=7, nsteps=30)
+    w["out_every"] = 10
+    o = run_oracle(w)
+    with heom.Context(w["params"], "fp32") as c:
+        c.set_rho0(w["rho0"])
+        assert c.autotune(trial_steps=5) > 0
+        r = c.propagate(1.0, 30, 10)
+    assert np.abs(r["pops"] - o["pops"]).max() < TOL32_POP
+    assert np.abs(r["eta"] - o["eta"]).max() < TOL32_ETA
+
+
 @pytest.mark.parametrize("N,K", [(3, 3), (7, 2), (10, 2)])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_low_temperature_correction_matches_oracle(N, K, precision):
