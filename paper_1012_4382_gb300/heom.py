@@ -407,6 +407,8 @@ class Context:
         _check(lib().heom_set_state(self._h, _ptr(s), _ptr(_f64(extra))))
 
     def set_launch(self, mode=-1, team_ctas=0, block_threads=0, node_threads=0):
+        """heom_set_launch; in mode 3 (dataflow engine) team_ctas is the number of
+        nodes each thread carries (1..6)."""
         _check(lib().heom_set_launch(self._h, int(mode), int(team_ctas), int(block_threads), int(node_threads)))
 
     def get_launch(self):
