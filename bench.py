@@ -7,8 +7,10 @@ node-RHS evaluations per second (nodes x 4 RK4 stages x steps / time) of the
 mixed-precision path (float right-hand sides, float-float accumulation of
 rho_0, populations and eta); the plain FP64 path is timed beside it on the
 same input.  Beside it: the batched scan (256 instances in one launch) against
-plain FP64 solves of the same instances, the serving trace, and the 24-site
-large hierarchy (HBM-resident) with its own bandwidth roofline.
+plain FP64 solves of the same 256 instances, the serving trace, the 24-site
+large hierarchy (HBM-resident) with its own bandwidth roofline, and the depth
+sweep of the paper's timing table (N = 7, depths 4-12, 1000 steps) beside the
+paper's own numbers.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Multi-GPU (N > 1) runs are replicas launched by torchrun: every rank solves
