@@ -186,3 +186,95 @@ def run_trace(trace, precision="fp32", device_bytes=8 << 30, streams=32, keep_re
     if keep_results:
         out["results"] = results
     return out
+
+
+# ------------------------------------------------------------ JSON-configured runs
+#
+# python -m paper_1012_4382_gb300.serving --config run.json
+#
+# run.json:
+#   {"precision": "fp32" | "fp64",          (default fp32)
+#    "device_bytes": 8589934592, "streams": 32,
+#    "trace": {"rate_per_s": 200, "count": 2000, "seed": 1234}      a seeded synthetic trace
+#             or "requests.jsonl"                                    one request per line (below),
+#    "results": "out.jsonl"}                 optional: per-request populations and eta
+#
+# A request line: {"arrival_s": 0.01, "N": 3, "K": 4, "H": [[...]] (N x N, cm^-1; real, or
+# [re, im] pairs), "lam": [...], "gam": [...] (cm^-1, per site or one value), "T": 300,
+# "trap": [...], "recomb": [...] (ps^-1, optional), "terminator": 0, "low_temp": 0,
+# "initial_site": 0, "dt": 1.0, "nsteps": 1000, "out_every": 100}.
+
+_PARAM_KEYS = ("N", "K", "lam", "gam", "T", "trap", "recomb", "terminator", "add_reorg", "low_temp", "scaled")
+
+
+def request_from_json(d: dict) -> dict:
+    """One trace entry (the form run_trace takes) from a request line."""
+    N = int(d["N"])
+    H = np.asarray(d["H"], dtype=np.float64)
+    if H.shape == (N, N, 2):
+        H = H[..., 0] + 1j * H[..., 1]
+    elif H.shape != (N, N):
+        raise ValueError("H must be N x N (real) or N x N x 2 ([re, im]), got %r" % (H.shape,))
+    params = {"H": np.asarray(H, dtype=np.complex128)}
+    for k in _PARAM_KEYS:
+        if k in d:
+            v = d[k]
+            params[k] = np.asarray(v, dtype=np.float64) if isinstance(v, list) else v
+    for k in ("lam", "gam"):
+        if np.ndim(params[k]) == 0:
+            params[k] = np.full(N, float(params[k]))
+    s = int(d.get("initial_site", 0))
+    if not 0 <= s < N:
+        raise ValueError("initial_site %d outside 0..%d" % (s, N - 1))
+    rho0 = np.zeros((N, N), dtype=np.complex128)
+    rho0[s, s] = 1.0
+    return {"arrival_s": float(d.get("arrival_s", 0.0)), "params": params, "rho0": rho0,
+            "dt": float(d.get("dt", 1.0)), "nsteps": int(d["nsteps"]), "out_every": int(d.get("out_every", d["nsteps"]))}
+
+
+def load_trace(cfg: dict, base_dir: str = ".") -> list:
+    """The request list a run configuration names: a seeded synthetic trace
+    (workloads.serving_trace) or a file of request lines."""
+    tr = cfg.get("trace", {"rate_per_s": 200.0, "count": 2000})
+    if isinstance(tr, dict):
+        from . import workloads
+        kw = {"count": int(tr.get("count", 2000)), "rate_per_s": float(tr.get("rate_per_s", 200.0))}
+        if "seed" in tr:
+            kw["seed"] = int(tr["seed"])
+        return workloads.serving_trace(**kw)
+    path = tr if os.path.isabs(tr) else os.path.join(base_dir, tr)
+    out = []
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if line:
+                import json
+                out.append(request_from_json(json.loads(line)))
+    return out
+
+
+def main(argv=None) -> int:
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="Replay a request trace against the continuous-batching server.")
+    ap.add_argument("--config", required=True, help="JSON run configuration (see the comment above main)")
+    a = ap.parse_args(argv)
+    with open(a.config) as f:
+        cfg = json.load(f)
+    trace = load_trace(cfg, os.path.dirname(os.path.abspath(a.config)))
+    res_path = cfg.get("results")
+    out = run_trace(trace, precision=cfg.get("precision", "fp32"), device_bytes=int(cfg.get("device_bytes", 8 << 30)),
+                    streams=int(cfg.get("streams", 32)), keep_results=bool(res_path))
+    results = out.pop("results", None)
+    if res_path:
+        with open(res_path, "w") as f:
+            for i in sorted(results):
+                r = results[i]
+                f.write(json.dumps({"request": i, "pops": r["pops"].tolist(), "eta": r["eta"].tolist(),
+                                    "loss": r["loss"].tolist()}) + "\n")
+    print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

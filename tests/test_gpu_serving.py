@@ -139,3 +139,32 @@ def test_trace_replay_reports_latency():
     r = serving.run_trace(tr, "fp32", device_bytes=2 << 30, streams=8)
     assert r["completed"] == 40
     assert 0 < r["p50_latency_s"] <= r["p99_latency_s"]
+
+
+def test_json_configured_run_matches_the_oracle(tmp_path, capsys):
+    """The serving harness driven by a JSON run configuration and a file of
+    request lines: every request's populations and eta, written to the
+    results file, against the oracle."""
+    import json
+    lines = []
+    for i, (N, K) in enumerate([(2, 3), (4, 3), (3, 5)]):
+        w = workloads.random_instance(N, K, seed=2100 + i)
+        p = w["params"]
+        lines.append({"arrival_s": 0.02 * i, "N": N, "K": K,
+                      "H": [[[float(z.real), float(z.imag)] for z in row] for row in p["H"]],
+                      "lam": p["lam"].tolist(), "gam": p["gam"].tolist(), "T": float(p["T"]),
+                      "trap": p["trap"].tolist(), "recomb": p["recomb"].tolist(), "initial_site": 0,
+                      "dt": 1.0, "nsteps": 150, "out_every": 30})
+    (tmp_path / "req.jsonl").write_text("\n".join(json.dumps(x) for x in lines) + "\n")
+    cfg = {"precision": "fp32", "device_bytes": 1 << 30, "streams": 4, "trace": "req.jsonl",
+           "results": str(tmp_path / "out.jsonl")}
+    (tmp_path / "run.json").write_text(json.dumps(cfg))
+    assert serving.main(["--config", str(tmp_path / "run.json")]) == 0
+    summary = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert summary["completed"] == 3
+    got = {r["request"]: r for r in map(json.loads, (tmp_path / "out.jsonl").read_text().splitlines())}
+    for i, line in enumerate(lines):
+        e = serving.request_from_json(line)
+        o = oracle.propagate(e["params"], e["rho0"], 1.0, 150, 30)
+        assert np.abs(np.array(got[i]["pops"]) - o["pops"]).max() < 1e-5
+        assert np.abs(np.array(got[i]["eta"]) - o["eta"]).max() < 1e-4
