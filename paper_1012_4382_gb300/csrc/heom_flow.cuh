@@ -10,9 +10,8 @@
 // memory for the whole call, node-major: element p of local node l at
 // l*N*N + p.  Thread (u, l) of the CTA computes unit u (an off-diagonal pair
 // (a, b), two packed reals, or a diagonal a) of the local nodes k*S + l,
-// k = 0..NPT-1, in every stage (NPT nodes per thread, 1 by default).  The
-// part of a unit's right-hand side that involves its own node -- the
-// commutator with H_eff, the site-energy
+// k = 0..NPT-1, in every stage (NPT nodes per thread, 1 by default).  The part of a unit's right-hand side
+// that involves its own node -- the commutator with H_eff, the site-energy
 // differences, the trap/decay and low-temperature damping -- is a fixed
 // linear form in at most NRE (real part) and NIM (imaginary part) packed
 // elements of the node; the host evaluates it once per unit and the thread
