@@ -168,3 +168,22 @@ def test_json_configured_run_matches_the_oracle(tmp_path, capsys):
         o = oracle.propagate(e["params"], e["rho0"], 1.0, 150, 30)
         assert np.abs(np.array(got[i]["pops"]) - o["pops"]).max() < 1e-5
         assert np.abs(np.array(got[i]["eta"]) - o["eta"]).max() < 1e-4
+
+
+def test_benchmark_trace_prefix_full_length_sampled_against_the_oracle():
+    """The first 40 requests of the benchmark's serving trace (Poisson 200/s,
+    N 2..8, depth 3..8, 1..20 ps at full length) replayed in the benchmark's
+    server configuration (16 GB budget, 32 streams); every request completes,
+    and the four cheapest for the host (nodes x steps) are checked against the
+    oracle on every 100 fs row."""
+    tr = workloads.serving_trace()[:40]
+    r = serving.run_trace(tr, "fp32", device_bytes=16 << 30, streams=32, keep_results=True)
+    assert r["completed"] == 40
+    cost = [heom.num_nodes(w["params"]["N"], w["params"]["K"]) * w["nsteps"] for w in tr]
+    for i in np.argsort(cost)[:4]:
+        w = tr[i]
+        o = oracle.propagate(w["params"], w["rho0"], w["dt"], w["nsteps"], w["out_every"])
+        g = r["results"][int(i)]
+        assert g["pops"].shape == o["pops"].shape
+        assert np.abs(g["pops"] - o["pops"]).max() < 1e-5, i
+        assert np.abs(g["eta"] - o["eta"]).max() < 1e-4, i
