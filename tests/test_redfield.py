@@ -119,3 +119,33 @@ def test_weak_coupling_agrees_with_the_heom(case):
     # rates off by pi (2 pi J in place of 2 J) are clearly seen
     wrong, _ = _relaxation_mismatch(w, 0.5, K, rate_scale=np.pi)
     assert wrong > 5 * weak and wrong > 0.2, (wrong, weak)
+
+
+def test_fmo_trapping_time_has_no_optimal_lambda():
+    """The paper's FMO setting (Table-1 Hamiltonian, trapping from BChl 3 and 4
+    at 1/(2.5 ps), radiative decay 1/(250 ps), 300 K, 1/gamma = 166 fs): it
+    states that secular Redfield gives no local minimum of the trapping time
+    in lambda, only a plateau (Sec. "Trapping time for different
+    reorganization energies").  From BChl 1, <t> = int t d(eta) up to the
+    paper's t_max (site population below 1e-5) decreases with lambda at every
+    step of the grid, by less and less."""
+    import os
+    H = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "fmo_table1.txt"), comments="#")
+    N = 7
+    trap = np.zeros(N)
+    trap[2] = trap[3] = 1.0 / 2.5
+    rho0 = np.zeros((N, N), complex)
+    rho0[0, 0] = 1.0
+    tmean = []
+    for lam in (10.0, 20.0, 55.0, 150.0, 300.0):
+        p = dict(N=N, H=H.astype(complex), lam=np.full(N, lam), gam=np.full(N, 1.0 / (166.0 * CM)), T=300.0,
+                 trap=trap, recomb=np.full(N, 1.0 / 250.0))
+        r = redfield.propagate(p, rho0, 2.5, 40000, 4)  # the paper's 2.5 fs steps, rows every 10 fs
+        site = r["pops"].sum(axis=1)
+        end = int(np.argmax(site < 1e-5)) if (site < 1e-5).any() else len(site) - 1
+        t = np.arange(end + 1) * 10.0
+        eta = r["eta"][: end + 1]
+        tmean.append(np.sum(0.5 * (t[1:] + t[:-1]) * np.diff(eta)) / 1000.0)
+    d = np.diff(tmean)
+    assert np.all(d < 0), tmean
+    assert np.all(np.diff(-d) < 0), tmean  # the decrease flattens towards a plateau
