@@ -1,4 +1,4 @@
-"""The paper's FMO results for the trapping time (Sec. "Trapping time for
+"""The paper's FMO results from the CUDA path.  The trapping time (Sec. "Trapping time for
 different reorganization energies", Eq. trappingtime, lower panel of Fig.
 "reorg") from the CUDA path: the Table-1 Hamiltonian, trapping from BChl 3
 and 4 at 1/(2.5 ps), radiative decay at 1/(250 ps), 300 K, 1/gamma = 166 fs,
@@ -69,3 +69,29 @@ def test_optimal_reorganisation_energy_and_trapping_time(row):
     assert best == lam_opt, t
     assert abs(t[best] - t_opt) < 0.3, t
     assert t[20.0] > t[35.0] > t[55.0]  # below 50 cm^-1 the bath assists the transfer
+
+
+def test_single_precision_populations_within_the_papers_bound():
+    """The paper's precision statement (App. B): populations from single and
+    double precision differ by less than 5e-7 for N_max = 12, dt = 10 fs over
+    10 ps, lambda = 35 cm^-1, 1/gamma = 166 fs, 300 K.  Here the mixed path
+    (float right-hand side, float-float accumulation of rho_0) against the
+    FP64 path on the Table-1 FMO model with the trap of BChl 3 and 4, from
+    BChl 1, every 100 fs (50 388 nodes; the grid engine's default shape)."""
+    H = np.array(_load("fmo_table1.txt"))
+    N = 7
+    trap = np.zeros(N)
+    trap[2] = trap[3] = 1.0 / 2.5
+    gam = 1.0 / (166.0 * 2.0 * math.pi * 2.99792458e-5)
+    p = dict(N=N, K=12, H=H.astype(complex), lam=np.full(N, 35.0), gam=np.full(N, gam), T=300.0, trap=trap,
+             recomb=np.full(N, 1.0 / 250.0))
+    rho0 = np.zeros((N, N), complex)
+    rho0[0, 0] = 1.0
+    pops = {}
+    for prec in ("fp64", "fp32"):
+        with heom.Context(p, prec) as c:
+            c.set_rho0(rho0)
+            pops[prec] = c.propagate(10.0, 1000, 10)["pops"]
+    assert np.all(np.isfinite(pops["fp64"])) and abs(pops["fp64"][0, 0] - 1.0) < 1e-15
+    assert pops["fp64"][-1, 0] < 0.5  # the population has moved
+    assert np.abs(pops["fp32"] - pops["fp64"]).max() < 5e-7
